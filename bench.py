@@ -1,0 +1,392 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 radiative-transfer solver (one JSON line on rank 0).
+
+Step = one batched mixed-precision solve of the ragged column batch (256
+columns, N_z ~ U{64..512}, N_nu ~ U{32..128}, 16 directions, dipole x R_II-A,
+4 right-hand sides: the physical b and three seeded N(0,1) vectors) to a
+relative residual of 1e-11 per instance (float64 iterative refinement around
+float32 GMRES(m) with float64 Arnoldi).  Inputs are resident in HBM when the
+timed region starts; every vector (~0.7 GB per rhs) is larger than L2.
+
+Reported beside the step: the float64 path's time-to-solution on the same
+batch, operator-apply throughput (mixed and float64), the end-to-end time
+through the C ABI with host buffers, the roofline of the solve kernel from its
+own algorithmic byte count, the clocks seen during the timed region, and the
+CPU oracle timed on a bounded sample (``--impl reference`` times only that).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "RT operator applies/s and GMRES time-to-1e-10, mixed vs FP64 on one GB300"
+N_RHS = 4
+TOL = 1e-12          # relative residual target; the error against the oracle is checked
+TOL_INNER = 1e-5     # reduction asked of each float32 inner solve
+RESTART = 512        # upper bound; each instance uses what its slot holds
+MAX_OUTER = 60
+
+
+# ------------------------------------------------------------------ inputs
+def workload(rank: int = 0):
+    from paper_2602_21958_gb300 import workloads as W
+
+    seed = None if rank == 0 else W.SEED_BASE + 5 + 1000 * rank
+    cols = W.config_c5(seed=seed)
+    return cols
+
+
+def build_rhs(cols, E: int, rank: int = 0) -> np.ndarray:
+    """Host [N_RHS-1, E] block of the seeded N(0,1) right-hand sides 1..3,
+    drawn per (column, rhs) instance."""
+    from paper_2602_21958_gb300 import workloads as W
+
+    seed = None if rank == 0 else W.SEED_BASE + 55 + 1000 * rank
+    out = np.empty((N_RHS - 1, E))
+    off = 0
+    for ci, c in enumerate(cols):
+        for r in range(1, N_RHS):
+            out[r - 1, off:off + c.n] = W.c5_random_rhs(ci, r, c.n, seed)
+        off += c.n
+    return out
+
+
+# ------------------------------------------------------------- clocks sampler
+class Clocks:
+    def __init__(self):
+        self.samples = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                                         text=True)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+            return
+
+        def reader():
+            for line in self.proc.stdout:
+                self.samples.append([v.strip() for v in line.split(",")])
+
+        self.thread = threading.Thread(target=reader, daemon=True)
+        self.thread.start()
+
+    def stop(self, device_index: int = 0) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = [s for s in self.samples if len(s) >= 9 and s[0] == str(device_index)]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if "Active" in r[5 + i]
+                          and "Not" not in r[5 + i]})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ------------------------------------------------------------ CPU oracle leg
+def _oracle_instance(args):
+    """Solve one (column, rhs) instance with the CPU oracle (its own GMRES,
+    as it stands); returns (seconds, iterations, n, solution)."""
+    import oracle as O
+    from paper_2602_21958_gb300 import workloads as W
+
+    ci, rhs = args
+    p = W.config_c5_column(ci)
+    b = O.rhs(p) if rhs == 0 else W.c5_random_rhs(ci, rhs, p.n)
+    t0 = time.perf_counter()
+    r = O.gmres(lambda v: O.apply_A(p, v), b, tol=TOL, restart=RESTART, max_iter=RESTART * 8)
+    dt = time.perf_counter() - t0
+    return dt, r.iterations, p.n, r.x
+
+
+def cpu_baseline(n_inst_total: int, cores: int | None = None, keep_solutions: bool = False,
+                 q_hi: float = 0.5) -> dict:
+    """Time the oracle (as it stands) on a bounded sample of instances: one
+    single-threaded spawned process per core, instance sizes spread over the
+    lower ``q_hi`` quantiles of the batch (the largest would take minutes).
+    Batch time = sum over all instances of a power-law fit t(n) = a n^p to the
+    sample, divided by the cores."""
+    cores = cores or os.cpu_count() or 1
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[k] = "1"
+    ctx = mp.get_context("spawn")
+    from paper_2602_21958_gb300 import workloads as W
+
+    nzs, nnus, _ = W._c5_params(None, 256, (64, 512), (32, 128))
+    sizes = np.array([int(nzs[c]) * 16 * int(nnus[c]) for c in range(256)])
+    order = np.argsort(sizes)
+    qs = np.linspace(0.0, q_hi, cores)
+    pick = [int(order[int(q * (len(sizes) - 1))]) for q in qs]
+    jobs = [(ci, k % N_RHS) for k, ci in enumerate(pick)]
+    t0 = time.perf_counter()
+    with ctx.Pool(cores) as pool:
+        res = pool.map(_oracle_instance, jobs)
+    wall = time.perf_counter() - t0
+    secs = np.array([r[0] for r in res])
+    ns = np.array([r[2] for r in res], dtype=float)
+    pw, la = np.polyfit(np.log(ns), np.log(secs), 1)
+    batch_secs = N_RHS * float(np.sum(np.exp(la) * sizes.astype(float) ** pw))
+    value = cores / batch_secs
+    out = {"value": value, "unit": "batched solves/s", "cores": cores, "kind": "oracle",
+           "sample": f"{len(jobs)} of {n_inst_total} (column, rhs) instances, sizes at quantiles "
+                     f"0..{q_hi} of the batch ({int(ns.min())}..{int(ns.max())} dofs), one numpy oracle "
+                     f"GMRES({RESTART}) per core to rel. residual {TOL:g}; wall {wall:.1f}s; batch time "
+                     f"= sum over the 1024 instances of the fit t(n) = {np.exp(la):.3g} n^{pw:.2f} s, "
+                     f"divided by {cores} cores",
+           "iterations": [int(r[1]) for r in res]}
+    if keep_solutions:
+        out["_solutions"] = {job: r[3] for job, r in zip(jobs, res)}
+    return out
+
+
+# ---------------------------------------------------------------- GPU leg
+def run_ours(args, rank: int, world: int):
+    import torch
+
+    from paper_2602_21958_gb300 import rt
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    cols = workload(rank)
+    E = sum(c.n for c in cols)
+    n_inst = len(cols) * N_RHS
+    hm = rt.Handle(cols, n_rhs=N_RHS, precision=rt.RT_P_MIXED, max_restart=RESTART)
+    b = torch.empty(N_RHS * E, dtype=torch.float64, device=dev)
+    hm.rt_apply(rt.RT_OP_RHS, None, b, fp64=True)       # every rhs slot = physical b
+    b[E:] = torch.from_numpy(build_rhs(cols, E, rank).reshape(-1)).to(dev)
+    x = torch.zeros_like(b)
+    stream = torch.cuda.current_stream()
+
+    def solve(h, xx):
+        return h.rt_solve(b, xx, tol=TOL, tol_inner=TOL_INNER, restart=RESTART, max_outer=MAX_OUTER)
+
+    for _ in range(args.warmup):
+        info = solve(hm, x)
+    dist_barrier(world)
+    torch.cuda.synchronize()
+    clocks = Clocks()
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    infos = []
+    kern_ms = []
+    for _ in range(args.steps):
+        info = solve(hm, x)
+        infos.append(info)
+        kern_ms.append(info["ms"])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    dist_barrier(world)
+    clk = clocks.stop(dev.index)
+    ms = e0.elapsed_time(e1) / args.steps
+    ms_all = dist_max(ms, world)
+    # float64 path: same batch, same tolerance (one solve)
+    h64 = rt.Handle(cols, n_rhs=N_RHS, precision=rt.RT_P_FP64, max_restart=RESTART)
+    x64 = torch.zeros_like(b)
+    info64 = h64.rt_solve(b, x64, tol=TOL, restart=RESTART, max_outer=MAX_OUTER)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    info64 = h64.rt_solve(b, x64, tol=TOL, restart=RESTART, max_outer=MAX_OUTER)
+    torch.cuda.synchronize()
+    fp64_ms = (time.perf_counter() - t0) * 1e3
+    diff = (torch.linalg.vector_norm(x64 - x) / torch.linalg.vector_norm(x64)).item()
+    del h64, x64
+    # operator applies/s
+    y = torch.empty_like(b)
+    applies = {}
+    for label, fp64 in (("mixed", False), ("fp64", True)):
+        for _ in range(3):
+            hm.rt_apply(rt.RT_OP_A, x, y, fp64=fp64)
+        torch.cuda.synchronize()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        k = 10
+        a0.record(stream)
+        for _ in range(k):
+            hm.rt_apply(rt.RT_OP_A, x, y, fp64=fp64)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        ams = a0.elapsed_time(a1) / k
+        bpd = 40.0 if fp64 else 32.0
+        applies[label] = {"ms": ams, "applies_per_s": 1e3 / ams,
+                          "GB_per_s": bpd * N_RHS * E / (ams * 1e-3) / 1e9}
+    # end to end through the C ABI with host (pinned) buffers
+    bh = b.cpu().pin_memory()
+    xh = torch.zeros_like(bh).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(max(1, args.steps // 2)):
+        hm.rt_solve(bh, xh, tol=TOL, tol_inner=TOL_INNER, restart=RESTART, max_outer=MAX_OUTER)
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / max(1, args.steps // 2)
+    e2e_ms = dist_max(e2e_ms, world)
+    # roofline of the solve kernel (dominant kernel): algorithmic bytes / kernel time
+    peaks = load_peaks()
+    kern_avg = statistics.mean(kern_ms)
+    bytes_avg = statistics.mean(i["bytes"] for i in infos)
+    achieved = bytes_avg / (kern_avg * 1e-3) / 1e9
+    offs = np.concatenate([[0], np.cumsum([c.n for c in cols])])
+    return {
+        "x_mixed": lambda ci, r: x[r * E + offs[ci]: r * E + offs[ci + 1]].cpu().numpy(),
+        "ms": ms_all, "E": E, "n_inst": n_inst, "info": infos[-1], "clk": clk,
+        "fp64": {"time_to_solution_ms": fp64_ms, "max_outer": info64["max_outer"],
+                 "max_inner": info64["max_inner"], "total_inner": info64["total_inner"],
+                 "max_relres": info64["max_relres"], "status": info64["status"],
+                 "rel_diff_vs_mixed": diff},
+        "applies": applies, "e2e_ms": e2e_ms,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks[0], "unit": "GB/s",
+                     "frac": achieved / peaks[0], "traffic": None,
+                     "kernel": "k_solve<float>", "peak_source": peaks[1],
+                     "bytes_per_launch": bytes_avg, "kernel_ms": kern_avg},
+    }
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
+    except Exception:
+        return 6800.0, "fallback 6.8 TB/s"
+
+
+# ------------------------------------------------------------- distributed
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+
+        backend = os.environ.get("RT_BENCH_BACKEND", "nccl")
+        if backend == "nccl":
+            import torch
+
+            torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        dist.init_process_group(backend=backend)
+    return rank, world
+
+
+def dist_barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def dist_max(v: float, world: int) -> float:
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# -------------------------------------------------------------------- main
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank, world = dist_setup()
+    n_inst = 256 * N_RHS
+    config = {"workload": "C5 ragged batch: 256 1D columns (N_z~U{64..512}, N_nu~U{32..128}, "
+                          "16 dirs, dipole x R_II-A, eps log-uniform 1e-6..1e-2), 4 rhs; solve to "
+                          f"rel. residual {TOL:g}",
+              "inputs_vs_l2": "inputs larger than L2 (each rhs vector ~0.7 GB)",
+              "restart": RESTART, "tol_inner": TOL_INNER, "parallelism": f"replicas x{world}"}
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        steps = []
+        cb = None
+        for _ in range(args.warmup + args.steps):
+            cb = cpu_baseline(n_inst, cores=os.cpu_count(), q_hi=0.3)
+            cb.pop("_solutions", None)
+            steps.append(1.0 / cb["value"])
+        val = 1.0 / statistics.mean(steps[args.warmup:])
+        line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "batched solves/s",
+                "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": 1e3 / val, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config,
+                "cpu_baseline": {k: cb[k] for k in ("kind", "cores", "sample")} | {"value": val,
+                                                                                "unit": cb["unit"]},
+                "e2e": {"value": val, "unit": "batched solves/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+    # spawn the oracle pool before the first GPU call
+    cb = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cb = cpu_baseline(n_inst, cores=os.cpu_count(), keep_solutions=True)
+    res = run_ours(args, rank, world)
+    if rank != 0:
+        return
+    accuracy = None
+    if cb is not None:
+        sols = cb.pop("_solutions")
+        errs = []
+        for (ci, r), xo in sols.items():
+            xg = res["x_mixed"](ci, r)
+            errs.append(float(np.linalg.norm(xg - xo) / np.linalg.norm(xo)))
+        accuracy = {"max_rel_err_vs_oracle": max(errs), "instances": len(errs),
+                    "oracle_tol": TOL}
+    value = world * 1e3 / res["ms"]
+    E = res["E"]
+    line = {
+        "metric": METRIC, "value": value, "unit": "batched solves/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["ms"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+        "data": "synthetic (seeded columns shaped like the paper's 1D slabs)", "config": config,
+        "time_to_1e-10_ms": {"mixed": res["ms"], "fp64": res["fp64"]["time_to_solution_ms"]},
+        "solve": {"max_outer": res["info"]["max_outer"], "max_inner": res["info"]["max_inner"],
+                  "total_inner": res["info"]["total_inner"], "max_relres": res["info"]["max_relres"],
+                  "status": res["info"]["status"]},
+        "fp64_solve": res["fp64"],
+        "applies": res["applies"],
+        "e2e": {"value": world * 1e3 / res["e2e_ms"], "unit": "batched solves/s",
+                "h2d_bytes_per_step": 8 * N_RHS * E, "d2h_bytes_per_step": 8 * N_RHS * E},
+        "gpu_launches": args.steps,
+        "roofline": res["roofline"],
+        "clocks": res["clk"],
+        "cpu_baseline": cb,
+        "accuracy": accuracy,
+    }
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

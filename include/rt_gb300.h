@@ -1,0 +1,170 @@
+/*
+ * rt_gb300.h -- C ABI of the GB300 (sm_103a) matrix-free S_N radiative-transfer
+ * operator and its Krylov solve.
+ *
+ * The operator is the discretised linear polychromatic RT system of
+ * Benedusi, Riva, Belluzzi, Serra-Capizzano, "Analysis of eigenvalue clustering
+ * leads to optimal scaling in numerical radiative transfer" (arXiv 2602.21958):
+ *
+ *     A_N I = b,   A_N = Id - Lambda_N Sigma_N,   b = Lambda_N t + I_in
+ *                                         (Sec. 3.1, eq. RT_sys_algebraic)
+ *
+ * Lambda_N is the formal solution along every ray (Sec. 3.2, eqs. ie_1, ie_2,
+ * lambda_block; Sec. 3.4 for 3D); Sigma_N = Gamma_N Psi_N W_N is the scattering
+ * contraction, block diagonal over spatial points (Sec. 3.3, eqs. S, Sigma).
+ *
+ * Vector layout (every x, y, b below).  Space-based lexicographic ordering of
+ * Sec. 3.1: point-major, then direction, then frequency fastest.  A batch of
+ * columns stores, for each right-hand side, the columns one after another; the
+ * n_rhs vectors follow each other:  index = ((rhs * E) + off[col]) + (p*n_dir + d)*n_nu + f
+ * with E = sum of the columns' sizes nz*n_dir*n_nu.  All values are float64.
+ *
+ * Memory and ownership.  Descriptor arrays (rt_desc) are HOST pointers that
+ * rt_create copies; the caller may free them when it returns.  Vector arguments
+ * of rt_apply / rt_solve may be device pointers (used in place, stream-ordered)
+ * or host pointers (staged through handle-owned device buffers; the call then
+ * synchronises the stream before returning).  The handle owns every workspace;
+ * no call frees caller memory.
+ *
+ * Errors.  Every int-returning call returns RT_OK (0) or an RT_ERR_* code and
+ * records a message retrievable by rt_last_error() (thread-local).  On error
+ * the output buffers are unspecified; the handle stays valid unless rt_create
+ * failed (then *out is NULL).
+ */
+#ifndef RT_GB300_H
+#define RT_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+enum {
+  RT_OK = 0,
+  RT_ERR_ARG = 1,        /* invalid argument (shape, pointer, option)          */
+  RT_ERR_CUDA = 2,       /* a CUDA runtime call or kernel launch failed         */
+  RT_ERR_OOM = 3,        /* device allocation failed                            */
+  RT_ERR_NOCONV = 4,     /* solve stopped before the tolerance; info is filled  */
+  RT_ERR_BREAKDOWN = 5,  /* Arnoldi breakdown before convergence                */
+  RT_ERR_NONFINITE = 6,  /* NaN or Inf met in inputs or residuals               */
+  RT_ERR_TIMEOUT = 7     /* a bounded device wait gave up                       */
+};
+
+/* ---- enumerations ---------------------------------------------------- */
+enum { RT_FS_SCL = 0,    /* linear short-characteristics exponential step       */
+       RT_FS_IE = 1 };   /* implicit Euler, eqs. ie_1, ie_2                      */
+enum { RT_P_FP64 = 0,    /* every stage in float64                              */
+       RT_P_MIXED = 1 }; /* Sigma and sweep in float32 (bf16 tensor cores for the
+                            dense kernel), Krylov and refinement in float64     */
+enum { RT_OP_A = 0,      /* y = x - Lambda Sigma x          (eq. RT_sys_algebraic) */
+       RT_OP_LAMBDA = 1, /* y = Lambda x, zero inflow       (eq. lambda_block)     */
+       RT_OP_SIGMA = 2,  /* y = Sigma x, no thermal term    (eq. Sigma)            */
+       RT_OP_RHS = 3 };  /* y = Lambda t + I_in; x unused   (eq. RT_sys_algebraic) */
+
+/* ---- one problem: a 1D column or a 3D box ----------------------------- */
+typedef struct rt_desc {
+  int32_t dims;          /* 1 (plane-parallel column, Sec. 3.1) or 3 (box, Sec. 3.4)   */
+  int32_t nx, ny, nz;    /* points; 1D: nx = ny = 1.  3D: nz planes of ny*nx cells,
+                            point p = (k*ny + j)*nx + i, plane 0 at the top; periodic
+                            in x and y, inflow through the top and bottom planes       */
+  int32_t n_dir, n_nu;   /* directions and frequencies; n_r = n_dir*n_nu rays         */
+  const double *z;       /* 1D: depth coordinate [nz], strictly increasing from the
+                            surface; 3D: spacings {dx, dy, dz}                         */
+  const double *dir;     /* [n_dir*3] unit vectors; component 2 is mu = Omega_z,
+                            mu > 0 points to the surface (Sec. 3)                    */
+  const double *w_dir;   /* [n_dir] direction weights (Sigma uses them as given)      */
+  const double *w_nu;    /* [n_nu] frequency weights                                  */
+  const double *chi;     /* [n_pts*n_nu] opacity per unit of z; the optical depth of a
+                            step is 0.5*(chi_upwind + chi_current)*|dz|/|mu|          */
+  const double *gamma;   /* [n_pts*n_nu] Gamma_N diagonal (Sec. 3.3), direction-free   */
+  const double *P;       /* [n_dir*n_dir] angular kernel of a separable Phi = P (x) R,
+                            or NULL when Psi is given                                 */
+  const double *R;       /* [n_nu*n_nu] frequency kernel of a separable Phi           */
+  const double *Psi;     /* [n_r*n_r] dense kernel over rays (Psi of eq. Sigma), or
+                            NULL.  Sigma_p = Gamma_p Psi diag(w_dir (x) w_nu)         */
+  const double *t_src;   /* [n_pts*n_nu] thermal term t = eps_t/chi, or NULL (= 0)    */
+  const double *I_top;   /* [n_nu] inflow for mu < 0 at the top, or NULL (= 0)        */
+  const double *I_bot;   /* [n_nu] inflow for mu > 0 at the bottom, or NULL (= 0)     */
+  int32_t formal_solver; /* RT_FS_SCL or RT_FS_IE                                     */
+} rt_desc;
+
+/* ---- solve options and report ----------------------------------------- */
+typedef struct rt_solve_opts {
+  double tol;          /* target ||b - A x||_2 / ||b||_2 per instance (e.g. 1e-11)      */
+  double tol_inner;    /* RT_P_MIXED: relative reduction asked of each inner solve    */
+  int32_t restart;     /* Krylov basis length m of GMRES(m); <= handle's max_restart  */
+  int32_t max_outer;   /* outer steps: refinement steps (mixed) or restarts (fp64)    */
+  int32_t use_x0;      /* 1: x holds the initial guess on entry; 0: start from x = 0  */
+} rt_solve_opts;
+
+typedef struct rt_info {
+  int32_t status;          /* RT_OK, RT_ERR_NOCONV or RT_ERR_BREAKDOWN (worst over batch) */
+  int32_t n_instances;     /* n_cols * n_rhs                                          */
+  int32_t max_outer;       /* largest number of outer steps over the instances        */
+  int32_t max_inner;       /* largest total inner (Arnoldi) iterations                */
+  int64_t total_inner;     /* sum of inner iterations over the instances              */
+  double max_relres;       /* largest final true relative residual                    */
+  double ms;               /* device time of the solve kernel (CUDA events)           */
+  double bytes;            /* algorithmic HBM bytes the solve moved: every vector read
+                              or written once per operation it takes part in         */
+  int32_t *inst_outer;     /* optional host arrays [n_instances] filled when non-NULL */
+  int32_t *inst_inner;
+  double *inst_relres;
+} rt_info;
+
+typedef struct rt_handle rt_handle;
+
+/* Create a handle for one problem (1D column or 3D box).  Copies the
+ * descriptor, precomputes the per-layer step coefficients in float64 (e^-dtau
+ * via exp, 1 - e^-dtau via expm1, w1/dtau by its alternating series below
+ * dtau = 0.1), factors the separable kernel, and allocates workspaces for up
+ * to max_restart Krylov vectors.  precision: RT_P_FP64 or RT_P_MIXED.
+ * Returns RT_ERR_ARG on an invalid descriptor, RT_ERR_OOM / RT_ERR_CUDA on
+ * device failures.  Cites: Sec. 3.1-3.4. */
+int rt_create(const rt_desc *desc, int32_t n_rhs, int32_t precision,
+              int32_t max_restart, rt_handle **out);
+
+/* Create a handle for a batch of independent 1D columns (each desc->dims ==
+ * 1) of uneven nz, n_dir, n_nu, solved together (one persistent launch).
+ * Workspace scales with the number of concurrently resident instances, not
+ * with the batch.  Same errors as rt_create. */
+int rt_create_batch(const rt_desc *cols, int32_t n_cols, int32_t n_rhs,
+                    int32_t precision, int32_t max_restart, rt_handle **out);
+
+/* Number of float64 values of one x / y / b argument (all columns, all rhs). */
+int64_t rt_vector_length(const rt_handle *h);
+
+/* Apply one operator (RT_OP_*) to all n_rhs vectors: y = op(x).  x and y must
+ * not overlap.  In RT_P_MIXED handles the operator is applied in the mixed
+ * precision (float32 Sigma and sweep; float64 x and y); pass fp64 = 1 to force
+ * the float64 operator.  Asynchronous on `stream` (a cudaStream_t, NULL = the
+ * legacy default stream) unless x or y is host memory. */
+int rt_apply(rt_handle *h, int32_t op, int32_t fp64, const double *x, double *y,
+             void *stream);
+
+/* Solve A_N x = b for all instances (eq. RT_sys_algebraic).  b == NULL uses
+ * the internal right-hand side Lambda t + I_in for every rhs.  RT_P_FP64:
+ * restarted GMRES(m) in float64 (classical Gram-Schmidt with one
+ * re-orthogonalisation, Givens rotations).  RT_P_MIXED: float64 iterative
+ * refinement, r = b - A x in float64, inner GMRES(m) on the mixed operator with
+ * float64 Arnoldi and Givens.  x0 = 0 unless opts->use_x0.  Synchronises the
+ * stream and fills *info (may be NULL).  Returns RT_ERR_NOCONV if any instance
+ * missed opts->tol (x still holds the best iterate). */
+int rt_solve(rt_handle *h, const double *b, double *x, const rt_solve_opts *opts,
+             rt_info *info, void *stream);
+
+/* Release every device and host resource of the handle (NULL is a no-op). */
+void rt_destroy(rt_handle *h);
+
+/* Message of the last error raised on this thread ("" if none). */
+const char *rt_last_error(void);
+
+/* Library version string. */
+const char *rt_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RT_GB300_H */

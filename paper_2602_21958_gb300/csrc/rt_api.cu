@@ -1,0 +1,663 @@
+// rt_api.cu -- C ABI entry points (include/rt_gb300.h): validation, host-side
+// factorisation of the separable scattering kernel, device tables, workspaces.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/rt_gb300.h"
+#include "rt_host.h"
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string &msg) {
+  g_err = msg;
+  return code;
+}
+
+#define RT_CUDA(call)                                                                        \
+  do {                                                                                       \
+    cudaError_t e_ = (call);                                                                 \
+    if (e_ != cudaSuccess) {                                                                 \
+      g_err = std::string(#call) + ": " + cudaGetErrorString(e_);                            \
+      return e_ == cudaErrorMemoryAllocation ? RT_ERR_OOM : RT_ERR_CUDA;                     \
+    }                                                                                        \
+  } while (0)
+
+template <typename T>
+int dev_upload(T **dst, const std::vector<T> &src) {
+  *dst = nullptr;
+  if (src.empty()) return RT_OK;
+  RT_CUDA(cudaMalloc((void **)dst, src.size() * sizeof(T)));
+  RT_CUDA(cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return RT_OK;
+}
+
+template <typename T>
+std::vector<float> to_f32(const std::vector<T> &v) {
+  std::vector<float> o(v.size());
+  for (size_t i = 0; i < v.size(); ++i) o[i] = (float)v[i];
+  return o;
+}
+
+// Cyclic Jacobi eigen-decomposition of a symmetric n x n matrix (row-major).
+// Returns eigenvalues in w and eigenvectors as columns of Q.
+void jacobi_eig(int n, std::vector<double> a, std::vector<double> &w, std::vector<double> &Q) {
+  Q.assign((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i) Q[(size_t)i * n + i] = 1.0;
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    double off = 0.0, tot = 0.0;
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j) {
+        const double v = a[(size_t)i * n + j] * a[(size_t)i * n + j];
+        tot += v;
+        if (i != j) off += v;
+      }
+    if (off <= 1e-34 * tot || off == 0.0) break;
+    for (int p = 0; p < n; ++p)
+      for (int q = p + 1; q < n; ++q) {
+        const double apq = a[(size_t)p * n + q];
+        if (apq == 0.0) continue;
+        const double app = a[(size_t)p * n + p], aqq = a[(size_t)q * n + q];
+        const double theta = (aqq - app) / (2.0 * apq);
+        const double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+        const double c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
+        for (int k = 0; k < n; ++k) {  // rotate columns p, q
+          const double akp = a[(size_t)k * n + p], akq = a[(size_t)k * n + q];
+          a[(size_t)k * n + p] = c * akp - s * akq;
+          a[(size_t)k * n + q] = s * akp + c * akq;
+        }
+        for (int k = 0; k < n; ++k) {  // rotate rows p, q
+          const double apk = a[(size_t)p * n + k], aqk = a[(size_t)q * n + k];
+          a[(size_t)p * n + k] = c * apk - s * aqk;
+          a[(size_t)q * n + k] = s * apk + c * aqk;
+        }
+        for (int k = 0; k < n; ++k) {
+          const double qkp = Q[(size_t)k * n + p], qkq = Q[(size_t)k * n + q];
+          Q[(size_t)k * n + p] = c * qkp - s * qkq;
+          Q[(size_t)k * n + q] = s * qkp + c * qkq;
+        }
+      }
+  }
+  w.resize(n);
+  for (int i = 0; i < n; ++i) w[i] = a[(size_t)i * n + i];
+}
+
+bool finite_all(const double *v, size_t n) {
+  for (size_t i = 0; i < n; ++i)
+    if (!std::isfinite(v[i])) return false;
+  return true;
+}
+
+bool is_device_ptr(const void *p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+void free_handle(rt_handle *h) {
+  if (!h) return;
+  void *ptrs[] = {h->d_cols, h->d_dir_cls, h->d_dir_up, h->d_tsrc, h->d_Itop, h->d_Ibot,
+                  h->E64, h->A64, h->B64, h->Uw64, h->Ul64, h->Rw64, h->Psi64, h->gam64,
+                  h->E32, h->A32, h->B32, h->Uw32, h->Ul32, h->Rw32, h->Psi32, h->gam32,
+                  h->b_int, h->d_order, h->d_queue, h->ws.V, h->ws.S, h->ws.H,
+                  h->so.outer, h->so.inner, h->so.status, h->so.relres, h->so.bytes,
+                  h->stage_x, h->stage_y, h->d_sig_tiles, h->d_sw_tiles, h->apply_S,
+                  h->d_tc_jobs, h->d_tc_off, h->d_tc_tiles, h->d_err};
+  for (void *p : ptrs)
+    if (p) cudaFree(p);
+  delete h;
+}
+
+struct ColumnHost {
+  rt::ColDev c;
+  std::vector<double> mu_cls;
+  std::vector<int32_t> dir_cls, dir_up;
+  std::vector<double> Uw, Ul, Rw, Psi;
+};
+
+int check_desc(const rt_desc *d, int idx) {
+  char pre[64];
+  std::snprintf(pre, sizeof pre, "column %d: ", idx);
+  if (!d) return fail(RT_ERR_ARG, std::string(pre) + "null descriptor");
+  if (d->dims != 1) return fail(RT_ERR_ARG, std::string(pre) + "only dims == 1 is supported by this entry point");
+  if (d->nx != 1 || d->ny != 1) return fail(RT_ERR_ARG, std::string(pre) + "1D columns need nx = ny = 1");
+  if (d->nz < 2 || d->n_dir < 1 || d->n_nu < 1)
+    return fail(RT_ERR_ARG, std::string(pre) + "need nz >= 2, n_dir >= 1, n_nu >= 1");
+  if ((int64_t)d->n_dir * d->n_nu > 8192) return fail(RT_ERR_ARG, std::string(pre) + "n_dir*n_nu > 8192");
+  if (!d->z || !d->dir || !d->w_dir || !d->w_nu || !d->chi || !d->gamma)
+    return fail(RT_ERR_ARG, std::string(pre) + "missing z, dir, w_dir, w_nu, chi or gamma");
+  if (!d->Psi && (!d->P || !d->R)) return fail(RT_ERR_ARG, std::string(pre) + "need Psi or both P and R");
+  if (d->formal_solver != RT_FS_SCL && d->formal_solver != RT_FS_IE)
+    return fail(RT_ERR_ARG, std::string(pre) + "unknown formal_solver");
+  for (int i = 0; i + 1 < d->nz; ++i)
+    if (!(d->z[i + 1] > d->z[i])) return fail(RT_ERR_ARG, std::string(pre) + "z must increase strictly");
+  for (int k = 0; k < d->n_dir; ++k)
+    if (!(std::fabs(d->dir[3 * k + 2]) > 0.0)) return fail(RT_ERR_ARG, std::string(pre) + "mu = 0 direction");
+  const size_t np = (size_t)d->nz * d->n_nu;
+  if (!finite_all(d->chi, np) || !finite_all(d->gamma, np) || !finite_all(d->z, d->nz))
+    return fail(RT_ERR_NONFINITE, std::string(pre) + "non-finite chi, gamma or z");
+  for (size_t i = 0; i < np; ++i)
+    if (d->chi[i] < 0.0) return fail(RT_ERR_ARG, std::string(pre) + "negative opacity");
+  return RT_OK;
+}
+
+// Factor the separable kernel: P = Q diag(lam) Q^T (symmetric) truncated at
+// |lam| <= 1e-13 max|lam|; otherwise the full-rank identity factor.
+void factor_angular(const rt_desc *d, ColumnHost &ch) {
+  const int nd = d->n_dir;
+  bool sym = true;
+  double pmax = 0.0;
+  for (int i = 0; i < nd * nd; ++i) pmax = std::max(pmax, std::fabs(d->P[i]));
+  for (int i = 0; i < nd && sym; ++i)
+    for (int j = 0; j < nd; ++j)
+      if (std::fabs(d->P[i * nd + j] - d->P[j * nd + i]) > 1e-14 * pmax) { sym = false; break; }
+  ch.Uw.clear();
+  ch.Ul.clear();
+  if (sym) {
+    std::vector<double> w, Q;
+    jacobi_eig(nd, std::vector<double>(d->P, d->P + nd * nd), w, Q);
+    double wmax = 0.0;
+    for (double v : w) wmax = std::max(wmax, std::fabs(v));
+    std::vector<int> keep;
+    for (int k = 0; k < nd; ++k)
+      if (std::fabs(w[k]) > 1e-13 * wmax) keep.push_back(k);
+    if (keep.empty()) keep.push_back(0);
+    const int rp = (int)keep.size();
+    ch.c.rp = rp;
+    ch.Uw.resize((size_t)nd * rp);
+    ch.Ul.resize((size_t)nd * rp);
+    for (int dd = 0; dd < nd; ++dd)
+      for (int k = 0; k < rp; ++k) {
+        const double q = Q[(size_t)dd * nd + keep[k]];
+        ch.Uw[(size_t)dd * rp + k] = q * d->w_dir[dd];
+        ch.Ul[(size_t)dd * rp + k] = q * w[keep[k]];
+      }
+  } else {
+    ch.c.rp = nd;
+    ch.Uw.assign((size_t)nd * nd, 0.0);
+    ch.Ul.assign(d->P, d->P + nd * nd);
+    for (int dd = 0; dd < nd; ++dd) ch.Uw[(size_t)dd * nd + dd] = d->w_dir[dd];
+  }
+}
+
+int build_column(const rt_desc *d, ColumnHost &ch) {
+  const int nd = d->n_dir, nn = d->n_nu;
+  ch.c.nz = d->nz;
+  ch.c.nd = nd;
+  ch.c.nn = nn;
+  ch.c.nr = nd * nn;
+  // |mu| classes
+  ch.mu_cls.clear();
+  ch.dir_cls.assign(nd, 0);
+  ch.dir_up.assign(nd, 0);
+  for (int k = 0; k < nd; ++k) {
+    const double mu = d->dir[3 * k + 2], am = std::fabs(mu);
+    ch.dir_up[k] = mu > 0.0 ? 1 : 0;
+    int found = -1;
+    for (size_t c = 0; c < ch.mu_cls.size(); ++c)
+      if (std::fabs(ch.mu_cls[c] - am) <= 1e-15 * am) { found = (int)c; break; }
+    if (found < 0) {
+      found = (int)ch.mu_cls.size();
+      ch.mu_cls.push_back(am);
+    }
+    ch.dir_cls[k] = found;
+  }
+  ch.c.ncls = (int)ch.mu_cls.size();
+  ch.c.rdiag = 0;
+  ch.Rw.clear();
+  ch.Psi.clear();
+  if (d->Psi) {
+    const int nr = nd * nn;
+    ch.c.rp = 1;
+    ch.Uw.assign(nd, 0.0);
+    ch.Ul.assign(nd, 0.0);
+    ch.Psi.resize((size_t)nr * nr);
+    for (int r = 0; r < nr; ++r)
+      for (int q = 0; q < nr; ++q)
+        ch.Psi[(size_t)q * nr + r] = d->Psi[(size_t)r * nr + q] * d->w_dir[q / nn] * d->w_nu[q % nn];
+    if (!finite_all(ch.Psi.data(), ch.Psi.size())) return fail(RT_ERR_NONFINITE, "non-finite Psi");
+    ch.Rw.assign(1, 0.0);
+    if (nr > rt::kSigBuf) return fail(RT_ERR_ARG, "dense kernel needs n_dir*n_nu <= 2048");
+  } else {
+    if (!finite_all(d->P, (size_t)nd * nd) || !finite_all(d->R, (size_t)nn * nn))
+      return fail(RT_ERR_NONFINITE, "non-finite P or R");
+    factor_angular(d, ch);
+    if ((int64_t)ch.c.rp * nn > rt::kSigBuf)
+      return fail(RT_ERR_ARG, "rank(P) * n_nu must not exceed 2048");
+    bool diag = true;
+    for (int i = 0; i < nn && diag; ++i)
+      for (int j = 0; j < nn; ++j)
+        if (i != j && d->R[i * nn + j] != 0.0) { diag = false; break; }
+    ch.c.rdiag = diag ? 1 : 0;
+    if (diag) {
+      ch.Rw.resize(nn);
+      for (int i = 0; i < nn; ++i) ch.Rw[i] = d->R[i * nn + i] * d->w_nu[i];
+    } else {
+      ch.Rw.resize((size_t)nn * nn);
+      for (int f = 0; f < nn; ++f)
+        for (int q = 0; q < nn; ++q) ch.Rw[(size_t)q * nn + f] = d->R[(size_t)f * nn + q] * d->w_nu[q];
+    }
+  }
+  return RT_OK;
+}
+
+// Workspace: one slot per resident CTA of the solve kernel.  A slot's basis
+// bytes are shared by whatever instance runs there, so the restart length of an
+// instance is (slot bytes / instance bytes) - 1, capped by the request.
+int alloc_workspace(rt_handle *h, int max_restart) {
+  const int m = std::max(1, std::min(max_restart, rt::max_krylov()));
+  int dev = 0;
+  RT_CUDA(cudaGetDevice(&dev));
+  RT_CUDA(cudaDeviceGetAttribute(&h->n_sm, cudaDevAttrMultiProcessorCount, dev));
+  const int n_inst = h->n_cols * h->n_rhs;
+  const int64_t ld = (h->nmax + 31) / 32 * 32;
+  const int64_t elt = h->precision == RT_P_FP64 ? 8 : 4;
+  size_t free_b = 0, total_b = 0;
+  RT_CUDA(cudaMemGetInfo(&free_b, &total_b));
+  const int64_t hld = (int64_t)(m + 1) * m + 3 * (m + 1);
+  // the largest instance must fit with at least min(m, 8) vectors
+  const int64_t min_cap = (int64_t)(std::min(m, 8) + 1) * ld * elt;
+  const int64_t want_cap = (int64_t)(m + 1) * ld * elt;
+  const double fixed = (double)(ld * 8 + hld * 8);
+  const double budget = 0.6 * (double)free_b;
+  int slots = std::min(n_inst, 2 * h->n_sm);
+  while (slots > 1 && budget / slots < fixed + (double)min_cap) --slots;
+  if (budget < fixed + (double)min_cap) return fail(RT_ERR_OOM, "not enough device memory for one Krylov workspace");
+  int64_t cap = (int64_t)std::min<double>((double)want_cap, budget / slots - fixed);
+  cap = cap / 256 * 256;
+  h->ws.slots = slots;
+  h->ws.m = m;
+  h->ws.ld = ld;
+  h->ws.cap_bytes = cap;
+  h->ws.hld = hld;
+  RT_CUDA(cudaMalloc(&h->ws.V, (size_t)slots * cap));
+  RT_CUDA(cudaMalloc(&h->ws.S, (size_t)slots * ld * sizeof(double)));
+  RT_CUDA(cudaMalloc(&h->ws.H, (size_t)slots * hld * sizeof(double)));
+  RT_CUDA(cudaMalloc(&h->so.outer, n_inst * sizeof(int32_t)));
+  RT_CUDA(cudaMalloc(&h->so.inner, n_inst * sizeof(int32_t)));
+  RT_CUDA(cudaMalloc(&h->so.status, n_inst * sizeof(int32_t)));
+  RT_CUDA(cudaMalloc(&h->so.relres, n_inst * sizeof(double)));
+  RT_CUDA(cudaMalloc(&h->so.bytes, n_inst * sizeof(double)));
+  return RT_OK;
+}
+
+int create_columns(const rt_desc *descs, int n_cols, int n_rhs, int precision, int max_restart,
+                   rt_handle **out) {
+  if (!out) return fail(RT_ERR_ARG, "out is null");
+  *out = nullptr;
+  if (n_cols < 1 || n_rhs < 1) return fail(RT_ERR_ARG, "need n_cols >= 1 and n_rhs >= 1");
+  if (n_cols > 65535) return fail(RT_ERR_ARG, "at most 65535 columns per batch");
+  if ((int64_t)n_cols * n_rhs > (1 << 30)) return fail(RT_ERR_ARG, "too many instances");
+  if (precision != RT_P_FP64 && precision != RT_P_MIXED) return fail(RT_ERR_ARG, "unknown precision");
+  if (max_restart < 1 || max_restart > rt::max_krylov())
+    return fail(RT_ERR_ARG, "max_restart must be in [1, 512]");
+  for (int i = 0; i < n_cols; ++i) {
+    const int rc = check_desc(&descs[i], i);
+    if (rc != RT_OK) return rc;
+  }
+  rt_handle *h = new rt_handle();
+  h->dims = 1;
+  h->n_cols = n_cols;
+  h->n_rhs = n_rhs;
+  h->precision = precision;
+  h->max_restart = max_restart;
+  std::vector<rt::ColDev> cols(n_cols);
+  std::vector<int32_t> dir_cls, dir_up, cls_off, fs;
+  std::vector<double> z, mu_cls, chi, gam, tsrc, itop, ibot, Uw, Ul, Rw, Psi;
+  std::vector<int64_t> zoff;
+  bool any_t = false;
+  for (int i = 0; i < n_cols; ++i) any_t = any_t || descs[i].t_src;
+  int64_t x_off = 0, g_off = 0, c_off = 0, r_off = 0, psi_off = 0;
+  int32_t u_off = 0, d_off = 0, in_off = 0;
+  for (int i = 0; i < n_cols; ++i) {
+    const rt_desc *d = &descs[i];
+    ColumnHost ch{};
+    int rc = build_column(d, ch);
+    if (rc != RT_OK) {
+      free_handle(h);
+      return rc;
+    }
+    rt::ColDev &c = ch.c;
+    c.x_off = x_off;
+    c.g_off = g_off;
+    c.c_off = c_off;
+    c.r_off = r_off;
+    c.psi_off = d->Psi ? psi_off : -1;
+    c.u_off = u_off;
+    c.d_off = d_off;
+    c.in_off = in_off;
+    cols[i] = c;
+    const int64_t ncol = (int64_t)c.nz * c.nr;
+    h->nmax = std::max(h->nmax, ncol);
+    x_off += ncol;
+    zoff.push_back((int64_t)z.size());
+    z.insert(z.end(), d->z, d->z + d->nz);
+    cls_off.push_back((int32_t)mu_cls.size());
+    mu_cls.insert(mu_cls.end(), ch.mu_cls.begin(), ch.mu_cls.end());
+    fs.push_back(d->formal_solver);
+    const size_t np = (size_t)d->nz * d->n_nu;
+    chi.insert(chi.end(), d->chi, d->chi + np);
+    gam.insert(gam.end(), d->gamma, d->gamma + np);
+    if (any_t) {
+      if (d->t_src) tsrc.insert(tsrc.end(), d->t_src, d->t_src + np);
+      else tsrc.insert(tsrc.end(), np, 0.0);
+    }
+    for (int f = 0; f < d->n_nu; ++f) {
+      itop.push_back(d->I_top ? d->I_top[f] : 0.0);
+      ibot.push_back(d->I_bot ? d->I_bot[f] : 0.0);
+    }
+    dir_cls.insert(dir_cls.end(), ch.dir_cls.begin(), ch.dir_cls.end());
+    dir_up.insert(dir_up.end(), ch.dir_up.begin(), ch.dir_up.end());
+    Uw.insert(Uw.end(), ch.Uw.begin(), ch.Uw.end());
+    Ul.insert(Ul.end(), ch.Ul.begin(), ch.Ul.end());
+    Rw.insert(Rw.end(), ch.Rw.begin(), ch.Rw.end());
+    Psi.insert(Psi.end(), ch.Psi.begin(), ch.Psi.end());
+    if (d->Psi) h->has_dense = true;
+    g_off += np;
+    c_off += (int64_t)(c.nz - 1) * c.ncls * c.nn;
+    r_off += (int64_t)ch.Rw.size();
+    psi_off += (int64_t)ch.Psi.size();
+    u_off += (int32_t)ch.Uw.size();
+    d_off += c.nd;
+    in_off += c.nn;
+  }
+  h->E = x_off;
+  h->h_cols = cols;
+  int rc = RT_OK;
+#define UP(dst, src)                          \
+  if ((rc = dev_upload(&(dst), src)) != RT_OK) { \
+    free_handle(h);                           \
+    return rc;                                \
+  }
+  UP(h->d_cols, cols);
+  UP(h->d_dir_cls, dir_cls);
+  UP(h->d_dir_up, dir_up);
+  if (any_t) UP(h->d_tsrc, tsrc);
+  UP(h->d_Itop, itop);
+  UP(h->d_Ibot, ibot);
+  UP(h->Uw64, Uw);
+  UP(h->Ul64, Ul);
+  UP(h->Rw64, Rw);
+  UP(h->gam64, gam);
+  std::vector<float> Uwf = to_f32(Uw), Ulf = to_f32(Ul), Rwf = to_f32(Rw), gamf = to_f32(gam);
+  UP(h->Uw32, Uwf);
+  UP(h->Ul32, Ulf);
+  UP(h->Rw32, Rwf);
+  UP(h->gam32, gamf);
+  if (!Psi.empty()) {
+    UP(h->Psi64, Psi);
+    std::vector<float> Psif = to_f32(Psi);
+    UP(h->Psi32, Psif);
+  }
+  {
+    cudaError_t e2 = cudaMalloc(&h->d_err, sizeof(int));
+    if (e2 == cudaSuccess) e2 = cudaMemset(h->d_err, 0, sizeof(int));
+    if (e2 == cudaSuccess && precision == RT_P_MIXED && !Psi.empty()) e2 = (cudaError_t)rt::tc_prepare(h, Psi);
+    if (e2 != cudaSuccess) {
+      free_handle(h);
+      return fail(RT_ERR_CUDA, std::string("tensor-core tables: ") + cudaGetErrorString(e2));
+    }
+  }
+  // step coefficients on the device (float64 exp / expm1)
+  double *d_z = nullptr, *d_chi = nullptr, *d_mu = nullptr;
+  int64_t *d_zoff = nullptr;
+  int32_t *d_clsoff = nullptr, *d_fs = nullptr;
+  auto cleanup_tmp = [&]() {
+    cudaFree(d_z); cudaFree(d_chi); cudaFree(d_mu); cudaFree(d_zoff); cudaFree(d_clsoff); cudaFree(d_fs);
+  };
+  if ((rc = dev_upload(&d_z, z)) || (rc = dev_upload(&d_chi, chi)) || (rc = dev_upload(&d_mu, mu_cls)) ||
+      (rc = dev_upload(&d_zoff, zoff)) || (rc = dev_upload(&d_clsoff, cls_off)) || (rc = dev_upload(&d_fs, fs))) {
+    cleanup_tmp();
+    free_handle(h);
+    return rc;
+  }
+  const size_t nc = (size_t)std::max<int64_t>(c_off, 1);
+  cudaError_t ce = cudaSuccess;
+  if (ce == cudaSuccess) ce = cudaMalloc(&h->E64, nc * 8);
+  if (ce == cudaSuccess) ce = cudaMalloc(&h->A64, nc * 8);
+  if (ce == cudaSuccess) ce = cudaMalloc(&h->B64, nc * 8);
+  if (ce == cudaSuccess) ce = cudaMalloc(&h->E32, nc * 4);
+  if (ce == cudaSuccess) ce = cudaMalloc(&h->A32, nc * 4);
+  if (ce == cudaSuccess) ce = cudaMalloc(&h->B32, nc * 4);
+  if (ce == cudaSuccess) ce = (cudaError_t)rt::launch_coefficients(h, d_z, d_zoff, d_chi, d_mu, d_clsoff, d_fs, 0);
+  if (ce == cudaSuccess) ce = cudaDeviceSynchronize();
+  cleanup_tmp();
+  if (ce != cudaSuccess) {
+    free_handle(h);
+    return fail(ce == cudaErrorMemoryAllocation ? RT_ERR_OOM : RT_ERR_CUDA,
+                std::string("coefficients: ") + cudaGetErrorString(ce));
+  }
+  // instance order: largest columns first (dynamic queue balances the tail)
+  const int n_inst = n_cols * n_rhs;
+  std::vector<int32_t> order(n_inst);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    const auto &ca = cols[a % n_cols], &cb = cols[b % n_cols];
+    return (int64_t)ca.nz * ca.nr > (int64_t)cb.nz * cb.nr;
+  });
+  UP(h->d_order, order);
+#undef UP
+  ce = cudaMalloc(&h->d_queue, 4 * sizeof(int));
+  if (ce != cudaSuccess) {
+    free_handle(h);
+    return fail(RT_ERR_OOM, "queue allocation failed");
+  }
+  if ((rc = alloc_workspace(h, max_restart)) != RT_OK) {
+    free_handle(h);
+    return rc;
+  }
+  // apply tiles (rhs 0 first) and the source-function scratch of rt_apply
+  {
+    std::vector<int3> sig;
+    std::vector<int2> sw;
+    for (int r = 0; r < n_rhs; ++r) {
+      for (int ci = 0; ci < n_cols; ++ci) {
+        const rt::ColDev &c = cols[ci];
+        const int inst = r * n_cols + ci;
+        const int pb = rt::sigma_points_per_block(c);
+        for (int p0 = 0; p0 < c.nz; p0 += pb) sig.push_back(make_int3(inst, p0, std::min(pb, c.nz - p0)));
+        for (int r0 = 0; r0 < c.nr; r0 += rt::kRayBlock) sw.push_back(make_int2(inst, r0));
+      }
+      if (r == 0) {
+        h->n_sig_tiles_rhs0 = (int)sig.size();
+        h->n_sw_tiles_rhs0 = (int)sw.size();
+      }
+    }
+    if (sig.size() > 0x7fffffff || sw.size() > 0x7fffffff) {
+      free_handle(h);
+      return fail(RT_ERR_ARG, "batch too large for the apply tiling");
+    }
+    h->n_sig_tiles = (int)sig.size();
+    h->n_sw_tiles = (int)sw.size();
+    if ((rc = dev_upload(&h->d_sig_tiles, sig)) != RT_OK || (rc = dev_upload(&h->d_sw_tiles, sw)) != RT_OK) {
+      free_handle(h);
+      return rc;
+    }
+    ce = cudaMalloc(&h->apply_S, (size_t)h->E * n_rhs * sizeof(double));
+    if (ce != cudaSuccess) {
+      free_handle(h);
+      return fail(RT_ERR_OOM, "apply scratch allocation failed");
+    }
+  }
+  ce = cudaMalloc(&h->b_int, (size_t)h->E * sizeof(double));
+  if (ce == cudaSuccess) ce = (cudaError_t)rt::launch_apply(h, RT_OP_RHS, true, h->b_int, h->b_int, 0, true);
+  if (ce == cudaSuccess) ce = cudaDeviceSynchronize();
+  if (ce != cudaSuccess) {
+    free_handle(h);
+    return fail(RT_ERR_CUDA, std::string("internal rhs: ") + cudaGetErrorString(ce));
+  }
+  *out = h;
+  return RT_OK;
+}
+
+int ensure_stage(rt_handle *h, int64_t len) {
+  if (h->stage_len >= len) return RT_OK;
+  if (h->stage_x) cudaFree(h->stage_x);
+  if (h->stage_y) cudaFree(h->stage_y);
+  h->stage_x = h->stage_y = nullptr;
+  h->stage_len = 0;
+  RT_CUDA(cudaMalloc(&h->stage_x, len * sizeof(double)));
+  RT_CUDA(cudaMalloc(&h->stage_y, len * sizeof(double)));
+  h->stage_len = len;
+  return RT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *rt_last_error(void) { return g_err.c_str(); }
+
+const char *rt_version(void) { return "rt_gb300 0.1 (sm_103a)"; }
+
+int rt_create(const rt_desc *desc, int32_t n_rhs, int32_t precision, int32_t max_restart,
+              rt_handle **out) {
+  if (!desc) return fail(RT_ERR_ARG, "null descriptor");
+  if (desc->dims == 3) return fail(RT_ERR_ARG, "3D boxes are not available in this build");
+  return create_columns(desc, 1, n_rhs, precision, max_restart, out);
+}
+
+int rt_create_batch(const rt_desc *cols, int32_t n_cols, int32_t n_rhs, int32_t precision,
+                    int32_t max_restart, rt_handle **out) {
+  if (!cols) return fail(RT_ERR_ARG, "null descriptor array");
+  return create_columns(cols, n_cols, n_rhs, precision, max_restart, out);
+}
+
+int64_t rt_vector_length(const rt_handle *h) { return h ? h->E * h->n_rhs : 0; }
+
+int rt_apply(rt_handle *h, int32_t op, int32_t fp64, const double *x, double *y, void *stream) {
+  if (!h) return fail(RT_ERR_ARG, "null handle");
+  if (op < RT_OP_A || op > RT_OP_RHS) return fail(RT_ERR_ARG, "unknown op");
+  if (!y || (!x && op != RT_OP_RHS)) return fail(RT_ERR_ARG, "null vector");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t len = h->E * h->n_rhs;
+  const bool xd = x ? is_device_ptr(x) : true, yd = is_device_ptr(y);
+  const double *xin = x;
+  double *yout = y;
+  if (!xd || !yd) {
+    int rc = ensure_stage(h, len);
+    if (rc != RT_OK) return rc;
+    if (x && !xd) {
+      RT_CUDA(cudaMemcpyAsync(h->stage_x, x, len * sizeof(double), cudaMemcpyHostToDevice, s));
+      xin = h->stage_x;
+    }
+    if (!yd) yout = h->stage_y;
+  }
+  if (!xin) xin = yout;  // RT_OP_RHS ignores x
+  const int e = rt::launch_apply(h, op, fp64 != 0, xin, yout, s);
+  if (e != 0) return fail(RT_ERR_CUDA, std::string("apply launch: ") + cudaGetErrorString((cudaError_t)e));
+  if (h->n_tc_jobs > 0 && !fp64 && (op == RT_OP_A || op == RT_OP_SIGMA)) {
+    int err = 0;
+    RT_CUDA(cudaMemcpyAsync(&err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    RT_CUDA(cudaStreamSynchronize(s));
+    if (err) {
+      cudaMemsetAsync(h->d_err, 0, sizeof(int), s);
+      return fail(RT_ERR_TIMEOUT, "tensor-core Sigma: a bounded wait gave up");
+    }
+  }
+  if (!yd) {
+    RT_CUDA(cudaMemcpyAsync(y, yout, len * sizeof(double), cudaMemcpyDeviceToHost, s));
+    RT_CUDA(cudaStreamSynchronize(s));
+  } else if (!xd) {
+    RT_CUDA(cudaStreamSynchronize(s));
+  }
+  return RT_OK;
+}
+
+int rt_solve(rt_handle *h, const double *b, double *x, const rt_solve_opts *o, rt_info *info,
+             void *stream) {
+  if (!h || !x || !o) return fail(RT_ERR_ARG, "null handle, x or options");
+  if (o->restart < 1 || o->restart > h->ws.m) return fail(RT_ERR_ARG, "restart outside [1, max_restart]");
+  if (!(o->tol > 0.0) || o->max_outer < 1) return fail(RT_ERR_ARG, "need tol > 0 and max_outer >= 1");
+  if (h->precision == RT_P_MIXED && !(o->tol_inner > 0.0 && o->tol_inner < 1.0))
+    return fail(RT_ERR_ARG, "mixed precision needs 0 < tol_inner < 1");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t len = h->E * h->n_rhs;
+  const bool bd = b ? is_device_ptr(b) : true, xd = is_device_ptr(x);
+  const double *bin = b;
+  double *xio = x;
+  if (!bd || !xd) {
+    int rc = ensure_stage(h, len);
+    if (rc != RT_OK) return rc;
+    if (b && !bd) {
+      RT_CUDA(cudaMemcpyAsync(h->stage_y, b, len * sizeof(double), cudaMemcpyHostToDevice, s));
+      bin = h->stage_y;
+    }
+    if (!xd) {
+      if (o->use_x0) RT_CUDA(cudaMemcpyAsync(h->stage_x, x, len * sizeof(double), cudaMemcpyHostToDevice, s));
+      xio = h->stage_x;
+    }
+  }
+  cudaEvent_t e0, e1;
+  RT_CUDA(cudaEventCreate(&e0));
+  RT_CUDA(cudaEventCreate(&e1));
+  RT_CUDA(cudaEventRecord(e0, s));
+  int e = rt::launch_solve(h, bin, xio, o->tol, o->tol_inner, o->restart, o->max_outer, o->use_x0, s);
+  if (e != 0) {
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return fail(RT_ERR_CUDA, std::string("solve launch: ") + cudaGetErrorString((cudaError_t)e));
+  }
+  RT_CUDA(cudaEventRecord(e1, s));
+  if (!xd) RT_CUDA(cudaMemcpyAsync(x, xio, len * sizeof(double), cudaMemcpyDeviceToHost, s));
+  RT_CUDA(cudaStreamSynchronize(s));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  const int n_inst = h->n_cols * h->n_rhs;
+  std::vector<int32_t> outer(n_inst), inner(n_inst), status(n_inst);
+  std::vector<double> relres(n_inst), bytes(n_inst);
+  RT_CUDA(cudaMemcpy(bytes.data(), h->so.bytes, n_inst * 8, cudaMemcpyDeviceToHost));
+  h->last_bytes = 0.0;
+  for (double v : bytes) h->last_bytes += v;
+  RT_CUDA(cudaMemcpy(outer.data(), h->so.outer, n_inst * 4, cudaMemcpyDeviceToHost));
+  RT_CUDA(cudaMemcpy(inner.data(), h->so.inner, n_inst * 4, cudaMemcpyDeviceToHost));
+  RT_CUDA(cudaMemcpy(status.data(), h->so.status, n_inst * 4, cudaMemcpyDeviceToHost));
+  RT_CUDA(cudaMemcpy(relres.data(), h->so.relres, n_inst * 8, cudaMemcpyDeviceToHost));
+  int worst = RT_OK;
+  rt_info loc{};
+  loc.n_instances = n_inst;
+  for (int i = 0; i < n_inst; ++i) {
+    loc.max_outer = std::max(loc.max_outer, outer[i]);
+    loc.max_inner = std::max(loc.max_inner, inner[i]);
+    loc.total_inner += inner[i];
+    loc.max_relres = std::max(loc.max_relres, relres[i]);
+    if (status[i] != RT_OK && (worst == RT_OK || status[i] == RT_ERR_NONFINITE)) worst = status[i];
+  }
+  loc.status = worst;
+  loc.ms = ms;
+  loc.bytes = h->last_bytes;
+  if (info) {
+    int32_t *po = info->inst_outer, *pi = info->inst_inner;
+    double *pr = info->inst_relres;
+    if (po) std::copy(outer.begin(), outer.end(), po);
+    if (pi) std::copy(inner.begin(), inner.end(), pi);
+    if (pr) std::copy(relres.begin(), relres.end(), pr);
+    loc.inst_outer = po;
+    loc.inst_inner = pi;
+    loc.inst_relres = pr;
+    *info = loc;
+  }
+  if (worst != RT_OK) {
+    char msg[160];
+    std::snprintf(msg, sizeof msg, "solve: status %d, largest relative residual %.3e", worst, loc.max_relres);
+    g_err = msg;
+  }
+  return worst;
+}
+
+void rt_destroy(rt_handle *h) { free_handle(h); }
+
+}  // extern "C"

@@ -1,0 +1,110 @@
+// rt_apply.cu -- the operators of rt_apply over a batch of 1D columns, as two
+// fully parallel kernels:
+//   k_sigma_tiles : Sigma on (instance, block of points) tiles      (eq. Sigma)
+//   k_sweep_tiles : one thread per ray on (instance, block of rays)  (eqs. ie_1, ie_2)
+// The source function makes one round trip through HBM between them.
+#include <cuda_runtime.h>
+
+#include "rt_host.h"
+#include "rt_internal.cuh"
+
+namespace rt {
+
+constexpr int kSigNT = 256;
+
+// skip_tc: columns handled by the tensor-core kernel are left to it
+template <typename T, typename TX>
+__global__ void __launch_bounds__(kSigNT) k_sigma_tiles(Common cm, Tables<T> tb, const int3 *tiles,
+                                                        int n_cols, int64_t E, const TX *X, T *S,
+                                                        int skip_tc) {
+  __shared__ T sm[2 * kSigBuf];
+  const int3 t = tiles[blockIdx.x];
+  const int ci = t.x % n_cols, rhs = t.x / n_cols;
+  const ColDev c = cm.cols[ci];
+  if (skip_tc && c.psi_off >= 0 && c.nr % 16 == 0) return;
+  const int64_t base = rhs * E + c.x_off;
+  sigma_block<T, TX>(c, tb, X + base, S + base, t.y, t.z, sm, sm + kSigBuf);
+}
+
+// out: kOutAminus (y = x - Lambda S), kOutI (y = Lambda S, or Lambda t + I_in
+// when tsrc is set and inflow is on)
+template <typename T>
+__global__ void __launch_bounds__(kRayBlock) k_sweep_tiles(Common cm, Tables<T> tb, const int2 *tiles,
+                                                           int n_cols, int64_t E, const T *S,
+                                                           const double *x, double *y, int out,
+                                                           int use_tsrc, int inflow) {
+  const int2 t = tiles[blockIdx.x];
+  const int ci = t.x % n_cols, rhs = t.x / n_cols;
+  const ColDev c = cm.cols[ci];
+  const int r = t.y + threadIdx.x;
+  if (r >= c.nr) return;
+  const int64_t base = rhs * E + c.x_off;
+  const double *ts = use_tsrc ? cm.tsrc + c.g_off : nullptr;
+  sweep_ray<T, double, double>(c, tb, cm, S ? S + base : nullptr, ts, x ? x + base : nullptr, nullptr,
+                               y + base, out, inflow != 0, r);
+}
+
+template <typename T>
+__global__ void k_convert(const double *a, T *b, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = (T)a[i];
+}
+
+template <typename T>
+__global__ void k_widen(const T *a, double *b, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = (double)a[i];
+}
+
+template <typename T>
+static int run_apply(rt_handle *h, const Tables<T> &tb, int op, const double *x, double *y, cudaStream_t s,
+                     bool first_rhs_only) {
+  const Common cm{h->d_cols, h->d_dir_cls, h->d_dir_up, h->d_tsrc, h->d_Itop, h->d_Ibot};
+  const int nsig = first_rhs_only ? h->n_sig_tiles_rhs0 : h->n_sig_tiles;
+  const int nsw = first_rhs_only ? h->n_sw_tiles_rhs0 : h->n_sw_tiles;
+  const int64_t len = (first_rhs_only ? 1 : h->n_rhs) * h->E;
+  T *S = reinterpret_cast<T *>(h->apply_S);
+  const bool tc = sizeof(T) == 4 && h->n_tc_jobs > 0 && !first_rhs_only;
+  auto sigma = [&]() -> int {
+    k_sigma_tiles<T, double><<<nsig, kSigNT, 0, s>>>(cm, tb, h->d_sig_tiles, h->n_cols, h->E, x, S, tc ? 1 : 0);
+    if (tc) return launch_sigma_dense_tc(h, false, x, reinterpret_cast<float *>(S), s);
+    return 0;
+  };
+  const int cgrid = (int)std::min<int64_t>((len + 255) / 256, 16 * 152);
+  switch (op) {
+    case 0:  // y = x - Lambda Sigma x
+      sigma();
+      k_sweep_tiles<T><<<nsw, kRayBlock, 0, s>>>(cm, tb, h->d_sw_tiles, h->n_cols, h->E, S, x, y, kOutAminus, 0, 0);
+      break;
+    case 1:  // y = Lambda x
+      k_convert<T><<<cgrid, 256, 0, s>>>(x, S, len);
+      k_sweep_tiles<T><<<nsw, kRayBlock, 0, s>>>(cm, tb, h->d_sw_tiles, h->n_cols, h->E, S, nullptr, y, kOutI, 0, 0);
+      break;
+    case 2:  // y = Sigma x
+      sigma();
+      k_widen<T><<<cgrid, 256, 0, s>>>(S, y, len);
+      break;
+    default:  // y = Lambda t + I_in
+      if (h->d_tsrc) {
+        k_sweep_tiles<T><<<nsw, kRayBlock, 0, s>>>(cm, tb, h->d_sw_tiles, h->n_cols, h->E, nullptr, nullptr, y,
+                                                   kOutI, 1, 1);
+      } else {
+        cudaMemsetAsync(S, 0, len * sizeof(T), s);
+        k_sweep_tiles<T><<<nsw, kRayBlock, 0, s>>>(cm, tb, h->d_sw_tiles, h->n_cols, h->E, S, nullptr, y, kOutI,
+                                                   0, 1);
+      }
+  }
+  return (int)cudaGetLastError();
+}
+
+int launch_apply(rt_handle *h, int op, bool fp64, const double *x, double *y, cudaStream_t s,
+                 bool first_rhs_only) {
+  if (fp64 || h->precision == 0) {
+    const Tables<double> tb{h->E64, h->A64, h->B64, h->Uw64, h->Ul64, h->Rw64, h->Psi64, h->gam64};
+    return run_apply<double>(h, tb, op, x, y, s, first_rhs_only);
+  }
+  const Tables<float> tb{h->E32, h->A32, h->B32, h->Uw32, h->Ul32, h->Rw32, h->Psi32, h->gam32};
+  return run_apply<float>(h, tb, op, x, y, s, first_rhs_only);
+}
+
+}  // namespace rt

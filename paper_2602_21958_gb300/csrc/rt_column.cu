@@ -1,0 +1,474 @@
+// rt_column.cu -- kernels for batches of 1D columns (Sec. 3.1-3.3):
+//   k_coefficients : per-layer step coefficients in float64 (exp / expm1)
+//   k_solve        : persistent per-instance solver: float64 iterative
+//                    refinement around GMRES(m) (CGS2 Arnoldi, Givens rotations)
+//
+// Every kernel walks a work queue of (column, rhs) instances with one CTA per
+// instance at a time; all synchronisation is inside the CTA, no CTA ever waits
+// for another.
+#include <algorithm>
+
+#include <cuda_runtime.h>
+
+#include "rt_host.h"
+#include "rt_internal.cuh"
+
+namespace rt {
+
+constexpr int kNT = 256;      // threads per CTA of the apply / solve kernels
+constexpr int kDots = 8;      // basis vectors per block reduction in Gram-Schmidt
+
+int solve_block_threads() { return kNT; }
+
+// ------------------------------------------------------------ coefficients
+// One thread per (layer, |mu| class, nu) of one column (blockIdx.y).  The
+// optical depth of layer l is 0.5 (chi_l + chi_{l+1}) (z_{l+1} - z_l) / |mu|.
+// SC-L step: e = e^-d, w0 = -expm1(-d), beta = w1/d (series below d = 0.1),
+// alpha = w0 - beta.  Implicit Euler: e = 1/(1+d), alpha = 0, beta = d/(1+d).
+__global__ void k_coefficients(const ColDev *__restrict__ cols, const double *__restrict__ z,
+                               const int64_t *__restrict__ zoff, const double *__restrict__ chi,
+                               const double *__restrict__ mu_cls, const int32_t *__restrict__ cls_off,
+                               const int32_t *__restrict__ fs, double *E, double *A, double *B,
+                               float *Ef, float *Af, float *Bf) {
+  const int col = blockIdx.y;
+  const ColDev c = cols[col];
+  const int64_t count = (int64_t)(c.nz - 1) * c.ncls * c.nn;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int f = (int)(i % c.nn);
+    const int cl = (int)((i / c.nn) % c.ncls);
+    const int layer = (int)(i / ((int64_t)c.nn * c.ncls));
+    const double dz = z[zoff[col] + layer + 1] - z[zoff[col] + layer];
+    const double cbar = 0.5 * (chi[c.g_off + (int64_t)layer * c.nn + f] +
+                               chi[c.g_off + (int64_t)(layer + 1) * c.nn + f]);
+    const double d = cbar * dz / mu_cls[cls_off[col] + cl];
+    double e, a, b;
+    if (fs[col] == 1) {
+      e = 1.0 / (1.0 + d);
+      a = 0.0;
+      b = d * e;
+    } else {
+      e = exp(-d);
+      const double w0 = -expm1(-d);
+      double beta;
+      if (d < 0.1) {
+        // w1/d = sum_{k>=1} (-1)^(k+1) d^k/(k+1)! = (d/2)(1 - (d/3)(1 - (d/4)(1 - ...)))
+        // 16 terms, nested from the innermost factor d/17
+        double s = 1.0;
+        for (int j = 17; j >= 3; --j) s = 1.0 - (d / j) * s;
+        beta = 0.5 * d * s;
+      } else {
+        beta = (d - w0) / d;
+      }
+      b = beta;
+      a = w0 - beta;
+    }
+    const int64_t o = c.c_off + i;
+    E[o] = e;
+    A[o] = a;
+    B[o] = b;
+    Ef[o] = (float)e;
+    Af[o] = (float)a;
+    Bf[o] = (float)b;
+  }
+}
+
+
+int launch_coefficients(rt_handle *h, const double *d_z, const int64_t *d_zoff,
+                        const double *d_chi, const double *d_mu_cls, const int32_t *d_cls_off,
+                        const int32_t *d_fs, cudaStream_t s) {
+  int64_t most = 1;
+  for (const ColDev &c : h->h_cols) most = std::max<int64_t>(most, (int64_t)(c.nz - 1) * c.ncls * c.nn);
+  const int bx = (int)std::min<int64_t>((most + 255) / 256, 4096);
+  dim3 grid(bx, h->n_cols);
+  k_coefficients<<<grid, 256, 0, s>>>(h->d_cols, d_z, d_zoff, d_chi, d_mu_cls, d_cls_off, d_fs, h->E64,
+                                      h->A64, h->B64, h->E32, h->A32, h->B32);
+  return (int)cudaGetLastError();
+}
+
+__device__ __forceinline__ int next_instance(int *queue, int *s_q) {
+  if (threadIdx.x == 0) *s_q = atomicAdd(queue, 1);
+  __syncthreads();
+  const int q = *s_q;
+  __syncthreads();
+  return q;
+}
+
+// ------------------------------------------------------------------ solve
+struct SolveParams {
+  Common cm;
+  Tables<double> t64;
+  Tables<float> t32;
+  const int32_t *order;
+  int n_cols, n_inst;
+  int64_t E;
+  const double *b;      // [n_rhs][E]
+  int b_shared;         // 1: b has one rhs vector shared by every rhs
+  double *x;            // [n_rhs][E]
+  double tol, tol_inner;
+  int m, max_outer, use_x0;
+  void *V;              // [slots][cap] Krylov basis, element type of the inner solve
+  int64_t cap;          // basis capacity of one slot (elements)
+  double *S;            // [slots][ld] float64 scratch: source function / residual
+  int64_t ld;
+  double *H;            // [slots][hld] Hessenberg (column-major), cs, sn, g
+  int64_t hld;
+  int *queue;
+  SolveOut out;
+};
+
+constexpr int kU = 4;  // independent elements per thread in the vector loops
+
+__device__ __forceinline__ double cta_norm2(const double *v, int64_t n, double *red, double *outb) {
+  double a[1] = {0.0};
+  for (int64_t k = threadIdx.x; k < n; k += blockDim.x) a[0] += v[k] * v[k];
+  block_sum<1>(a, red, outb);
+  return a[0];
+}
+
+// h[0..j] = V[0..j]^T w and ||w||^2 (returned).  Products and the running sums
+// over 8 consecutive elements of a thread are taken in TL, then accumulated
+// in float64, then summed over the block in float64.
+template <typename TL>
+__device__ double cta_dots(const TL *V, int64_t ldv, int j, const TL *w, int64_t n, double *h,
+                           double *red, double *outb) {
+  double nrm = 0.0;
+  constexpr int kWiden = 8;  // loop iterations summed in TL before one float64 add
+  for (int i0 = 0; i0 <= j; i0 += kDots) {
+    const int cnt = min(kDots, j + 1 - i0);
+    double acc[kDots + 1];
+#pragma unroll
+    for (int u = 0; u <= kDots; ++u) acc[u] = 0.0;
+    TL part[kDots + 1];
+#pragma unroll
+    for (int u = 0; u <= kDots; ++u) part[u] = 0;
+    int it = 0;
+    for (int64_t k0 = threadIdx.x; k0 < n; k0 += (int64_t)kU * blockDim.x) {
+      TL wv[kU];
+#pragma unroll
+      for (int e = 0; e < kU; ++e) {
+        const int64_t k = k0 + (int64_t)e * blockDim.x;
+        wv[e] = k < n ? w[k] : (TL)0;
+      }
+#pragma unroll
+      for (int u = 0; u < kDots; ++u) {
+        if (u < cnt) {
+          const TL *vi = V + (int64_t)(i0 + u) * ldv;
+          TL vv[kU];
+#pragma unroll
+          for (int e = 0; e < kU; ++e) {
+            const int64_t k = k0 + (int64_t)e * blockDim.x;
+            vv[e] = k < n ? vi[k] : (TL)0;
+          }
+#pragma unroll
+          for (int e = 0; e < kU; ++e) part[u] = fma(vv[e], wv[e], part[u]);
+        }
+      }
+      if (i0 == 0) {
+#pragma unroll
+        for (int e = 0; e < kU; ++e) part[kDots] = fma(wv[e], wv[e], part[kDots]);
+      }
+      if (++it == kWiden) {
+        it = 0;
+#pragma unroll
+        for (int u = 0; u <= kDots; ++u) {
+          acc[u] += (double)part[u];
+          part[u] = 0;
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u <= kDots; ++u) acc[u] += (double)part[u];
+    block_sum<kDots + 1>(acc, red, outb);
+    if (threadIdx.x < cnt) h[i0 + threadIdx.x] = acc[threadIdx.x];
+    if (i0 == 0) nrm = acc[kDots];
+  }
+  __syncthreads();
+  return nrm;
+}
+
+// acc[e] += sum_{i < cnt} coef[i] * V_i[k0 + e*blockDim] for kU elements; the
+// basis is walked kDots vectors at a time with all their loads issued before
+// the FMAs (kDots*kU independent loads in flight per thread).  coef is in TL.
+template <typename TL>
+__device__ __forceinline__ void axpy_block(const TL *V, int64_t ldv, int cnt, const TL *coef, int64_t k0,
+                                           int64_t n, TL (&acc)[kU]) {
+  for (int i0 = 0; i0 < cnt; i0 += kDots) {
+    TL v[kDots][kU];
+#pragma unroll
+    for (int u = 0; u < kDots; ++u) {
+      const TL *vi = V + (int64_t)(i0 + u) * ldv;
+#pragma unroll
+      for (int e = 0; e < kU; ++e) {
+        const int64_t k = k0 + (int64_t)e * blockDim.x;
+        v[u][e] = (i0 + u < cnt && k < n) ? vi[k] : (TL)0;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kDots; ++u) {
+      const TL hu = (i0 + u < cnt) ? coef[i0 + u] : (TL)0;
+#pragma unroll
+      for (int e = 0; e < kU; ++e) acc[e] = fma(hu, v[u][e], acc[e]);
+    }
+  }
+}
+
+// coefficients -> TL in shared memory (sign applied), then a barrier
+template <typename TL>
+__device__ __forceinline__ void stage_coef(const double *h, int cnt, double sgn, TL *hf) {
+  for (int i = threadIdx.x; i < cnt; i += blockDim.x) hf[i] = (TL)(sgn * h[i]);
+  __syncthreads();
+}
+
+// w = (w - V[0..j] h) * scale; returns ||result||^2 when want_norm (else 0).
+// hf: shared scratch of at least j+1 TL.
+template <typename TL>
+__device__ double cta_update(const TL *V, int64_t ldv, int j, TL *w, int64_t n, const double *h,
+                             double scale, bool want_norm, TL *hf, double *red, double *outb) {
+  stage_coef<TL>(h, j + 1, -1.0, hf);
+  const TL sc = (TL)scale;
+  double a[1] = {0.0};
+  for (int64_t k0 = threadIdx.x; k0 < n; k0 += (int64_t)kU * blockDim.x) {
+    TL wv[kU];
+#pragma unroll
+    for (int e = 0; e < kU; ++e) {
+      const int64_t k = k0 + (int64_t)e * blockDim.x;
+      wv[e] = k < n ? w[k] : (TL)0;
+    }
+    axpy_block<TL>(V, ldv, j + 1, hf, k0, n, wv);
+    TL part = 0;
+#pragma unroll
+    for (int e = 0; e < kU; ++e) {
+      const int64_t k = k0 + (int64_t)e * blockDim.x;
+      const TL v = wv[e] * sc;
+      if (k < n) w[k] = v;
+      part = fma(v, v, part);
+    }
+    if (want_norm) a[0] += (double)part;
+  }
+  if (want_norm) block_sum<1>(a, red, outb);
+  else __syncthreads();
+  return want_norm ? a[0] : 0.0;
+}
+
+enum InstStatus : int { kConverged = 0, kNoConv = 4, kBreakdown = 5, kNonFinite = 6 };
+
+constexpr int kMaxM = 512;  // largest Krylov basis per instance
+
+// One CTA solves one (column, rhs) instance at a time, to completion:
+//   outer loop (float64): r = b - A x, stop when ||r|| <= tol ||b||;
+//   inner GMRES(m) on the operator in TL (float: mixed, double: plain fp64),
+//   basis stored in TL, m = min(requested, kMaxM, slot capacity / instance size);
+//   Arnoldi: classical Gram-Schmidt with the DGKS test: when ||w - V h|| >=
+//   ||w||/sqrt(2) (known from ||w||^2 - ||h||^2 without another pass) one
+//   update pass also normalises; otherwise a second projection is made;
+//   Givens rotations and the triangular solve in float64 by thread 0;
+//   x += V y with the correction summed in TL.
+template <typename TL>
+__global__ void __launch_bounds__(kNT) k_solve(SolveParams p) {
+  __shared__ double sm[2 * kSigBuf];
+  __shared__ double red[(kNT / 32) * (kDots + 1)];
+  __shared__ double outb[kDots + 1];
+  __shared__ double hbuf[2 * (kMaxM + 8)];
+  __shared__ TL hf[kMaxM + 8];
+  __shared__ int s_q;
+  __shared__ double s_val[4];
+  TL *Vslot = reinterpret_cast<TL *>(p.V) + (int64_t)blockIdx.x * p.cap;
+  double *S64 = p.S + (int64_t)blockIdx.x * p.ld;
+  TL *SL = reinterpret_cast<TL *>(S64);
+  double *Hc = p.H + (int64_t)blockIdx.x * p.hld;
+  double *h = hbuf;
+  double *h2 = hbuf + kMaxM + 8;
+  const Tables<TL> &tl = *reinterpret_cast<const Tables<TL> *>(
+      sizeof(TL) == 8 ? (const void *)&p.t64 : (const void *)&p.t32);
+  const bool mixed = sizeof(TL) == 4;
+  const double sz = (double)sizeof(TL);
+  for (;;) {
+    const int q = next_instance(p.queue, &s_q);
+    if (q >= p.n_inst) break;
+    const int inst = p.order[q];
+    const int ci = inst % p.n_cols, rhs = inst / p.n_cols;
+    const ColDev c = p.cm.cols[ci];
+    const int64_t n = (int64_t)c.nz * c.nr;
+    const int64_t ldv = (n + 31) / 32 * 32;
+    const int64_t fit = p.cap / ldv - 1;
+    const int m = (int)(fit < (int64_t)min(p.m, kMaxM) ? fit : (int64_t)min(p.m, kMaxM));
+    double *cs = Hc + (int64_t)(m + 1) * m;
+    double *sn = cs + (m + 1);
+    double *g = sn + (m + 1);
+    const double *bv = p.b + (p.b_shared ? 0 : rhs * p.E) + c.x_off;
+    double *x = p.x + rhs * p.E + c.x_off;
+    const double bn = sqrt(cta_norm2(bv, n, red, outb));
+    if (!p.use_x0) {
+      for (int64_t k = threadIdx.x; k < n; k += blockDim.x) x[k] = 0.0;
+      __syncthreads();
+    }
+    int status = kNoConv, outer = 0, inner_total = 0;
+    double relres = 1.0;
+    double bpe = p.use_x0 ? 8.0 : 16.0;  // algorithmic bytes per element: ||b||, x = 0
+    const bool bad_b = !(bn == bn) || bn > 1e300;
+    if (bad_b) {
+      status = kNonFinite;
+    } else if (bn == 0.0) {
+      for (int64_t k = threadIdx.x; k < n; k += blockDim.x) x[k] = 0.0;
+      status = kConverged;
+      relres = 0.0;
+    }
+    for (; bn > 0.0 && !bad_b; ++outer) {
+      // ---- r = b - A x in float64, then V_0 = r / ||r|| in TL ----------------
+      double rn;
+      const double *rsrc;
+      if (outer == 0 && !p.use_x0) {
+        rn = bn;
+        rsrc = bv;
+        bpe += 0.0;
+      } else {
+        sigma_column<double, double>(c, p.t64, x, S64, sm, sm + kSigBuf);
+        double a[1] = {sweep_column<double, double, double>(c, p.t64, p.cm, S64, nullptr, x, bv, S64,
+                                                            kOutResid, false)};
+        block_sum<1>(a, red, outb);
+        rn = sqrt(a[0]);
+        rsrc = S64;
+        bpe += 48.0;  // x, S, S, x, b, r
+      }
+      relres = rn / bn;
+      if (!(rn == rn) || rn > 1e300) { status = kNonFinite; break; }
+      if (relres <= p.tol) { status = kConverged; break; }
+      if (outer >= p.max_outer) { status = kNoConv; break; }
+      for (int64_t k = threadIdx.x; k < n; k += blockDim.x) Vslot[k] = (TL)(rsrc[k] / rn);
+      __syncthreads();
+      bpe += 8.0 + sz;
+      if (threadIdx.x == 0) g[0] = rn;
+      const double target = mixed ? fmax(p.tol_inner * rn, 0.5 * p.tol * bn) : 0.5 * p.tol * bn;
+      int jdone = 0;
+      bool breakdown = false;
+      for (int j = 0; j < m; ++j) {
+        TL *vj = Vslot + (int64_t)j * ldv;
+        TL *w = Vslot + (int64_t)(j + 1) * ldv;
+        sigma_column<TL, TL>(c, tl, vj, SL, reinterpret_cast<TL *>(sm), reinterpret_cast<TL *>(sm) + kSigBuf);
+        sweep_column<TL, TL, TL>(c, tl, p.cm, SL, nullptr, vj, nullptr, w, kOutAminus, false);
+        __syncthreads();
+        bpe += 5.0 * sz;  // v, S, S, v, w
+        const double ww = cta_dots<TL>(Vslot, ldv, j, w, n, h, red, outb);
+        double hh = 0.0;
+        for (int i = 0; i <= j; ++i) hh += h[i] * h[i];
+        double hn;
+        bpe += sz * (j + 2);
+        if (ww - hh > 0.5 * ww) {
+          hn = sqrt(ww - hh);
+          cta_update<TL>(Vslot, ldv, j, w, n, h, hn > 0.0 ? 1.0 / hn : 0.0, false, hf, red, outb);
+          bpe += sz * (j + 3);
+          for (int i = threadIdx.x; i <= j; i += blockDim.x) h2[i] = 0.0;
+        } else {
+          // second projection: w' = w - V h, h2 = V^T w', w'' = w' - V h2
+          cta_update<TL>(Vslot, ldv, j, w, n, h, 1.0, false, hf, red, outb);
+          cta_dots<TL>(Vslot, ldv, j, w, n, h2, red, outb);
+          const double hn2 = cta_update<TL>(Vslot, ldv, j, w, n, h2, 1.0, true, hf, red, outb);
+          hn = sqrt(hn2);
+          for (int64_t k = threadIdx.x; k < n; k += blockDim.x) w[k] = (TL)((double)w[k] / hn);
+          __syncthreads();
+          bpe += sz * (3.0 * j + 10.0);
+        }
+        if (threadIdx.x == 0) {
+          double *col = Hc + (int64_t)j * (m + 1);
+          for (int i = 0; i <= j; ++i) col[i] = h[i] + h2[i];
+          col[j + 1] = hn;
+          for (int i = 0; i < j; ++i) {
+            const double t0 = cs[i] * col[i] + sn[i] * col[i + 1];
+            col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
+            col[i] = t0;
+          }
+          const double den = hypot(col[j], col[j + 1]);
+          double cj = 1.0, sj = 0.0;
+          if (den > 0.0) { cj = col[j] / den; sj = col[j + 1] / den; }
+          cs[j] = cj;
+          sn[j] = sj;
+          col[j] = den;
+          col[j + 1] = 0.0;
+          g[j + 1] = -sj * g[j];
+          g[j] = cj * g[j];
+          s_val[0] = fabs(g[j + 1]);
+          s_val[1] = den;
+        }
+        __syncthreads();
+        const double est = s_val[0];
+        const double den = s_val[1];
+        jdone = j + 1;
+        if (den == 0.0) { breakdown = true; jdone = j; break; }
+        if (!(hn > 1e-300 * fmax(1.0, rn))) break;  // invariant subspace: exact in it
+        if (!(est == est)) break;
+        if (est <= target) break;
+      }
+      inner_total += jdone;
+      // ---- y = R^-1 g (float64), x += V y -------------------------------------
+      if (threadIdx.x == 0) {
+        for (int i = jdone - 1; i >= 0; --i) {
+          double acc = g[i];
+          for (int k = i + 1; k < jdone; ++k) acc -= Hc[(int64_t)k * (m + 1) + i] * h[k];
+          h[i] = acc / Hc[(int64_t)i * (m + 1) + i];
+        }
+      }
+      __syncthreads();
+      stage_coef<TL>(h, jdone, 1.0, hf);
+      for (int64_t k0 = threadIdx.x; k0 < n; k0 += (int64_t)kU * blockDim.x) {
+        TL d[kU];
+#pragma unroll
+        for (int e = 0; e < kU; ++e) d[e] = 0;
+        axpy_block<TL>(Vslot, ldv, jdone, hf, k0, n, d);
+#pragma unroll
+        for (int e = 0; e < kU; ++e) {
+          const int64_t k = k0 + (int64_t)e * blockDim.x;
+          if (k < n) x[k] += (double)d[e];
+        }
+      }
+      bpe += sz * jdone + 16.0;
+      __syncthreads();
+      if (breakdown && jdone == 0) { status = kBreakdown; break; }
+    }
+    if (threadIdx.x == 0) {
+      p.out.outer[inst] = outer;
+      p.out.inner[inst] = inner_total;
+      p.out.status[inst] = status;
+      p.out.relres[inst] = relres;
+      p.out.bytes[inst] = bpe * (double)n;
+    }
+    __syncthreads();
+  }
+}
+
+int launch_solve(rt_handle *h, const double *b, double *x, double tol, double tol_inner, int m,
+                 int max_outer, int use_x0, cudaStream_t s) {
+  SolveParams p;
+  p.cm = Common{h->d_cols, h->d_dir_cls, h->d_dir_up, h->d_tsrc, h->d_Itop, h->d_Ibot};
+  p.t64 = Tables<double>{h->E64, h->A64, h->B64, h->Uw64, h->Ul64, h->Rw64, h->Psi64, h->gam64};
+  p.t32 = Tables<float>{h->E32, h->A32, h->B32, h->Uw32, h->Ul32, h->Rw32, h->Psi32, h->gam32};
+  p.order = h->d_order;
+  p.n_cols = h->n_cols;
+  p.n_inst = h->n_cols * h->n_rhs;
+  p.E = h->E;
+  p.b = b ? b : h->b_int;
+  p.b_shared = b ? 0 : 1;
+  p.x = x;
+  p.tol = tol;
+  p.tol_inner = tol_inner;
+  p.m = m;
+  p.max_outer = max_outer;
+  p.use_x0 = use_x0;
+  p.V = h->ws.V;
+  p.cap = h->ws.cap_bytes / (h->precision == 0 ? 8 : 4);
+  p.S = h->ws.S;
+  p.ld = h->ws.ld;
+  p.H = h->ws.H;
+  p.hld = h->ws.hld;
+  p.queue = h->d_queue + 1;
+  p.out = h->so;
+  cudaError_t e = cudaMemsetAsync(h->d_queue + 1, 0, sizeof(int), s);
+  if (e != cudaSuccess) return (int)e;
+  if (h->precision == 0) k_solve<double><<<h->ws.slots, kNT, 0, s>>>(p);
+  else k_solve<float><<<h->ws.slots, kNT, 0, s>>>(p);
+  return (int)cudaGetLastError();
+}
+
+int max_krylov() { return kMaxM; }
+
+}  // namespace rt

@@ -1,0 +1,86 @@
+// rt_host.h -- host-side handle and launch interface shared by the C-ABI
+// translation unit and the kernel translation units.
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "rt_internal.cuh"
+
+namespace rt {
+
+struct SolveOut {
+  int32_t *outer, *inner, *status;  // device [n_inst]
+  double *relres;                   // device [n_inst]
+  double *bytes;                    // device [n_inst] algorithmic HBM bytes of the solve
+};
+
+struct Workspace {
+  int slots = 0;           // concurrently resident instances (persistent CTAs)
+  int m = 0;               // largest Krylov basis length a solve may ask for
+  int64_t ld = 0;          // float64 scratch length per slot (>= largest column)
+  int64_t cap_bytes = 0;   // Krylov basis bytes per slot (shared by whatever instance runs there)
+  int64_t hld = 0;         // doubles per slot of Hessenberg + Givens storage
+  void *V = nullptr;       // [slots][cap_bytes]
+  double *S = nullptr;     // [slots][ld] source-function / residual scratch
+  double *H = nullptr;     // [slots][hld]
+};
+
+}  // namespace rt
+
+struct rt_handle {
+  int dims = 1;
+  int n_cols = 0, n_rhs = 1, precision = 0, max_restart = 0;
+  int64_t E = 0;       // length of one right-hand side (all columns)
+  int64_t nmax = 0;    // largest column length
+  int n_sm = 0;
+  std::vector<rt::ColDev> h_cols;
+  rt::ColDev *d_cols = nullptr;
+  int32_t *d_dir_cls = nullptr, *d_dir_up = nullptr;
+  double *d_tsrc = nullptr, *d_Itop = nullptr, *d_Ibot = nullptr;
+  // float64 tables
+  double *E64 = nullptr, *A64 = nullptr, *B64 = nullptr, *Uw64 = nullptr, *Ul64 = nullptr,
+         *Rw64 = nullptr, *Psi64 = nullptr, *gam64 = nullptr;
+  // float32 tables (mixed precision)
+  float *E32 = nullptr, *A32 = nullptr, *B32 = nullptr, *Uw32 = nullptr, *Ul32 = nullptr,
+        *Rw32 = nullptr, *Psi32 = nullptr, *gam32 = nullptr;
+  double *b_int = nullptr;       // internal right-hand side [E]
+  int32_t *d_order = nullptr;    // instance order, largest first
+  int *d_queue = nullptr;        // work-queue counters (2 ints)
+  rt::Workspace ws;
+  rt::SolveOut so{};
+  double last_bytes = 0.0;           // algorithmic bytes of the last solve (all instances)
+  double *stage_x = nullptr, *stage_y = nullptr;  // device staging for host vectors
+  // tiled apply: Sigma tiles (instance, first point, points) and sweep tiles
+  // (instance, first ray), rhs 0 first; scratch for the source function
+  int3 *d_sig_tiles = nullptr;
+  int2 *d_sw_tiles = nullptr;
+  int n_sig_tiles = 0, n_sig_tiles_rhs0 = 0, n_sw_tiles = 0, n_sw_tiles_rhs0 = 0;
+  void *apply_S = nullptr;
+  // dense-kernel Sigma on tcgen05 (mixed precision, columns with n_r % 16 == 0)
+  int n_tc_jobs = 0;
+  void *d_tc_jobs = nullptr;          // TcJob[n_tc_jobs]
+  int64_t *d_tc_off = nullptr;        // per column offset into the bf16 tiles
+  uint16_t *d_tc_tiles = nullptr;     // pre-tiled bf16 PsiW
+  int *d_err = nullptr;               // device error word (bounded waits)
+  int64_t stage_len = 0;
+  bool has_dense = false;
+};
+
+namespace rt {
+// launchers (defined in rt_column.cu); all return a cudaError_t as int
+int launch_coefficients(rt_handle *h, const double *d_z, const int64_t *d_zoff,
+                        const double *d_chi, const double *d_mu_cls, const int32_t *d_cls_off,
+                        const int32_t *d_fs, cudaStream_t s);
+int launch_apply(rt_handle *h, int op, bool fp64, const double *x, double *y, cudaStream_t s,
+                 bool first_rhs_only = false);
+int launch_solve(rt_handle *h, const double *b, double *x, double tol, double tol_inner, int m,
+                 int max_outer, int use_x0, cudaStream_t s);
+int solve_block_threads();
+int launch_sigma_dense_tc(rt_handle *h, bool x_is_float, const void *x, float *S, cudaStream_t s);
+struct TcJob;
+int tc_prepare(rt_handle *h, const std::vector<double> &psiwT);
+constexpr int kRayBlock = 128;  // rays (threads) per sweep tile
+int max_krylov();
+int apply_slots(rt_handle *h);
+}  // namespace rt

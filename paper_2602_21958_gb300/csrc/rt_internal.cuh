@@ -1,0 +1,298 @@
+// rt_internal.cuh -- device data layout and per-column device routines shared by
+// the 1D apply and solve kernels.
+//
+// A handle holds a batch of 1D columns (Sec. 3.1) in concatenated device arrays.
+// Per column: step coefficients per (layer, |mu| class, nu), the factored
+// scattering kernel, Gamma, the thermal term and the inflow.  Vectors follow the
+// space-based ordering of Sec. 3.1 (point, direction, frequency fastest).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace rt {
+
+constexpr int kMaxRank = 16;   // largest rank of the angular factor kept in registers
+constexpr int kSigBuf = 2048;  // elements of each shared buffer of the Sigma stage
+
+// Per-column metadata (device resident, one entry per column).
+struct ColDev {
+  int64_t x_off;    // offset of the column inside one right-hand-side vector
+  int64_t g_off;    // offset in per-(point, nu) arrays: gamma, t_src, chi
+  int64_t c_off;    // offset in step-coefficient arrays [nz-1][ncls][nn]
+  int64_t r_off;    // offset in the frequency-kernel storage
+  int64_t psi_off;  // offset in the dense-kernel storage, -1 when separable
+  int32_t u_off;    // offset in angular-factor arrays [nd][rp]
+  int32_t d_off;    // offset in per-direction arrays [nd]
+  int32_t in_off;   // offset in inflow arrays [nn]
+  int32_t nz, nd, nn, nr;
+  int32_t ncls;     // number of distinct |mu|
+  int32_t rp;       // rank of the angular factor
+  int32_t rdiag;    // 1: frequency kernel is diagonal (coherent scattering)
+};
+
+// Arrays in one arithmetic precision T (double: fp64 path; float: mixed path).
+template <typename T>
+struct Tables {
+  const T *E, *A, *B;   // step coefficients: I_c = E I_u + A S_u + B S_c
+  const T *Uw;          // [nd][rp] moment weights  (eigvecs of P times w_dir)
+  const T *Ul;          // [nd][rp] expansion       (eigvecs of P times eigvals)
+  const T *RwT;         // [nn'][nn] (R w_nu)^T, or [nn] diagonal when rdiag
+  const T *PsiwT;       // [nr'][nr] (Psi diag(w_r))^T for dense kernels
+  const T *gamma;       // [nz][nn]
+};
+
+struct Common {
+  const ColDev *cols;
+  const int32_t *dir_cls;   // [sum nd] |mu| class of each direction
+  const int32_t *dir_up;    // [sum nd] 1 if mu > 0 (sweeps towards the surface)
+  const double *tsrc;       // [sum nz*nn] thermal term, or nullptr
+  const double *I_top;      // [sum nn]
+  const double *I_bot;      // [sum nn]
+};
+
+template <typename T> struct Vec2;
+template <> struct Vec2<double> { using type = double2; };
+template <> struct Vec2<float> { using type = float2; };
+
+// ------------------------------------------------------------ block reductions
+// Sum NV per-thread values over the block; every thread receives the totals.
+// `red` must hold (blockDim/32)*NV doubles; `out` NV doubles (shared).
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV], double *red, double *out) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    double s = v[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    v[k] = s;
+  }
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) red[warp * NV + k] = v[k];
+  }
+  __syncthreads();
+  if (threadIdx.x < NV) {
+    double s = 0.0;
+    for (int w = 0; w < nw; ++w) s += red[w * NV + threadIdx.x];
+    out[threadIdx.x] = s;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < NV; ++k) v[k] = out[k];
+  __syncthreads();
+}
+
+template <typename T> __device__ __forceinline__ T to(double v) { return (T)v; }
+
+// ------------------------------------------------------------------ Sigma
+// S_p = Gamma_p Psi W X_p for every point of one column (eq. Sigma), the
+// separable kernel Phi = P (x) R taken in factored form:
+//   m_k(nu')  = sum_d Uw[d][k] X(d, nu')                (angular moments)
+//   z_k(nu)   = sum_nu' RwT[nu'][nu] m_k(nu')           (frequency kernel)
+//   S(d, nu)  = gamma(nu) sum_k Ul[d][k] z_k(nu)        (+ t(nu) if tsrc)
+// X is read in its own type and rounded to T; S is written in T.  Shared buffers:
+// sm0, sm1 each kSigBuf elements of T.
+// Points [p0, p0+np) of one column; np * rp * nn (separable) or np * nr
+// (dense) must not exceed kSigBuf.  Ends with __syncthreads().
+template <typename T, typename TX>
+__device__ void sigma_block(const ColDev &c, const Tables<T> &tb, const TX *__restrict__ X,
+                            T *__restrict__ S, int p0, int np, T *sm0, T *sm1) {
+  const int nd = c.nd, nn = c.nn, nr = c.nr, rp = c.rp;
+  const T *gam = tb.gamma + c.g_off;
+  if (c.psi_off >= 0) {
+    // Dense kernel: S = gamma * (PsiwT^T X_p); X_p staged in shared memory.
+    const T *Pw = tb.PsiwT + c.psi_off;
+    for (int i = threadIdx.x; i < np * nr; i += blockDim.x) sm0[i] = to<T>(X[(int64_t)p0 * nr + i]);
+    __syncthreads();
+    for (int i = threadIdx.x; i < np * nr; i += blockDim.x) {
+      const int b = i / nr, r = i - b * nr;
+      const T *xp = sm0 + b * nr;
+      T acc = 0;
+      for (int q = 0; q < nr; ++q) acc = fma(Pw[(int64_t)q * nr + r], xp[q], acc);
+      S[(int64_t)(p0 + b) * nr + r] = gam[(int64_t)(p0 + b) * nn + (r % nn)] * acc;
+    }
+    __syncthreads();
+    return;
+  }
+  const T *Uw = tb.Uw + c.u_off;
+  const T *Ul = tb.Ul + c.u_off;
+  const T *Rw = tb.RwT + c.r_off;
+  const int per_pt = rp * nn;
+  // 1. angular moments, one thread per (point, nu'), up to kMaxRank ranks in registers
+  for (int i = threadIdx.x; i < np * nn; i += blockDim.x) {
+    const int b = i / nn, f = i - b * nn;
+    const TX *xp = X + (int64_t)(p0 + b) * nr + f;
+    for (int k0 = 0; k0 < rp; k0 += kMaxRank) {
+      const int kn = min(kMaxRank, rp - k0);
+      T m[kMaxRank];
+#pragma unroll
+      for (int k = 0; k < kMaxRank; ++k) m[k] = 0;
+      int d = 0;
+      for (; d + 4 <= nd; d += 4) {  // four independent loads in flight
+        T xv[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) xv[e] = to<T>(xp[(d + e) * nn]);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const T *u = Uw + (d + e) * rp + k0;
+#pragma unroll
+          for (int k = 0; k < kMaxRank; ++k)
+            if (k < kn) m[k] = fma(u[k], xv[e], m[k]);
+        }
+      }
+      for (; d < nd; ++d) {
+        const T xv = to<T>(xp[d * nn]);
+        const T *u = Uw + d * rp + k0;
+#pragma unroll
+        for (int k = 0; k < kMaxRank; ++k)
+          if (k < kn) m[k] = fma(u[k], xv, m[k]);
+      }
+#pragma unroll
+      for (int k = 0; k < kMaxRank; ++k)
+        if (k < kn) sm0[(b * rp + k0 + k) * nn + f] = m[k];
+    }
+  }
+  __syncthreads();
+  // 2. frequency kernel, one thread per (point, rank, nu)
+  for (int i = threadIdx.x; i < np * per_pt; i += blockDim.x) {
+    const int f = i % nn;
+    const T *mrow = sm0 + (i - f);
+    T acc;
+    if (c.rdiag) {
+      acc = Rw[f] * mrow[f];
+    } else {
+      acc = 0;
+      for (int q = 0; q < nn; ++q) acc = fma(Rw[q * nn + f], mrow[q], acc);
+    }
+    sm1[i] = acc;
+  }
+  __syncthreads();
+  // 3. expansion over directions, scaled by Gamma
+  for (int i = threadIdx.x; i < np * nr; i += blockDim.x) {
+    const int b = i / nr, r = i - b * nr, d = r / nn, f = r - d * nn;
+    const T *zb = sm1 + b * per_pt + f;
+    const T *u = Ul + d * rp;
+    T acc = 0;
+    for (int k = 0; k < rp; ++k) acc = fma(u[k], zb[k * nn], acc);
+    S[(int64_t)(p0 + b) * nr + r] = gam[(int64_t)(p0 + b) * nn + f] * acc;
+  }
+  __syncthreads();
+}
+
+// Points per Sigma block for one column (fits the two shared buffers).
+__host__ __device__ inline int sigma_points_per_block(const ColDev &c) {
+  const int per_pt = c.psi_off >= 0 ? c.nr : c.rp * c.nn;
+  const int pb = kSigBuf / per_pt;
+  return pb < 1 ? 1 : pb;
+}
+
+// Every point of one column, block by block (one CTA).
+template <typename T, typename TX>
+__device__ void sigma_column(const ColDev &c, const Tables<T> &tb, const TX *__restrict__ X,
+                             T *__restrict__ S, T *sm0, T *sm1) {
+  const int pb = sigma_points_per_block(c);
+  for (int p0 = 0; p0 < c.nz; p0 += pb) sigma_block<T, TX>(c, tb, X, S, p0, min(pb, c.nz - p0), sm0, sm1);
+}
+
+// ------------------------------------------------------------------ sweep
+enum SweepOut : int {
+  kOutAminus = 0,  // y = x - I            (A x with I = Lambda Sigma x)
+  kOutI = 1,       // y = I                (Lambda S, or the right-hand side)
+  kOutResid = 2    // y = b - x + I        (b - A x), returns the squared norm
+};
+
+// Formal solution along every ray of one column (eqs. ie_1, ie_2 with the
+// coefficients of the chosen step): mu < 0 from the surface down, mu > 0 from
+// the deep boundary up.  The source is S[p][r] (T), or the thermal term
+// broadcast over directions when `tsrc` is non-null.  With `inflow` the first
+// point of each ray holds I_top / I_bot, else 0.  Loads run ahead of the
+// recurrence by kAhead depth points.  Returns this thread's partial sum of y^2
+// for kOutResid (0 otherwise).  y may alias S: each thread reads S and writes y
+// only at the points of its own rays, the source value is read before the
+// output at the same point is written.
+template <typename T, typename TX, typename TY, int kAhead = 4>
+__device__ double sweep_ray(const ColDev &c, const Tables<T> &tb, const Common &cm, const T *S,
+                            const double *__restrict__ tsrc, const TX *__restrict__ x,
+                            const double *__restrict__ bv, TY *y, int out, bool inflow, int r) {
+  const int nz = c.nz, nn = c.nn, nr = c.nr, ncls = c.ncls;
+  const T *E = tb.E + c.c_off, *A = tb.A + c.c_off, *B = tb.B + c.c_off;
+  double ss = 0.0;
+  const int d = r / nn, f = r - d * nn;
+  const int up = cm.dir_up[c.d_off + d];
+  const int cls = cm.dir_cls[c.d_off + d];
+  const int step = up ? -1 : 1;
+  const int i0 = up ? nz - 1 : 0;
+  T Iu = 0;
+  if (inflow) Iu = (T)(up ? cm.I_bot[c.in_off + f] : cm.I_top[c.in_off + f]);
+  auto src = [&](int i) -> T {
+    return tsrc ? (T)tsrc[(int64_t)i * nn + f] : S[(int64_t)i * nr + r];
+  };
+  auto emit = [&](int i, T I) {
+    const int64_t k = (int64_t)i * nr + r;
+    if (out == kOutResid) {
+      const double v = bv[k] - (double)x[k] + (double)I;
+      y[k] = (TY)v;
+      ss += v * v;
+    } else if (out == kOutI) {
+      y[k] = (TY)I;
+    } else if (sizeof(TY) == 4 && sizeof(TX) == 4) {
+      y[k] = (TY)((float)x[k] - (float)I);   // float pipeline: no float64 op
+    } else {
+      y[k] = (TY)((double)x[k] - (double)I);
+    }
+  };
+  T Su = src(i0);
+  emit(i0, Iu);
+  // march the remaining nz-1 points in chunks with loads issued ahead
+  int i = i0;
+  for (int done = 1; done < nz; done += kAhead) {
+    const int cnt = min(kAhead, nz - done);
+    T e[kAhead], a[kAhead], b[kAhead], sc[kAhead];
+#pragma unroll
+    for (int u = 0; u < kAhead; ++u) {
+      if (u < cnt) {
+        const int ic = i + (u + 1) * step;
+        const int layer = up ? ic : ic - 1;  // layer between ic and its upwind point
+        const int64_t ci = ((int64_t)layer * ncls + cls) * nn + f;
+        e[u] = E[ci];
+        a[u] = A[ci];
+        b[u] = B[ci];
+        sc[u] = src(ic);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kAhead; ++u) {
+      if (u < cnt) {
+        const T Ic = fma(e[u], Iu, fma(a[u], Su, b[u] * sc[u]));
+        emit(i + (u + 1) * step, Ic);
+        Iu = Ic;
+        Su = sc[u];
+      }
+    }
+    i += cnt * step;
+  }
+  return out == kOutResid ? ss : 0.0;
+}
+
+// Formal solution along every ray of one column (eqs. ie_1, ie_2 with the
+// coefficients of the chosen step): mu < 0 from the surface down, mu > 0 from
+// the deep boundary up.  The source is S[p][r] (T), or the thermal term
+// broadcast over directions when `tsrc` is non-null.  With `inflow` the first
+// point of each ray holds I_top / I_bot, else 0.  Loads run ahead of the
+// recurrence by kAhead depth points.  Returns this thread's partial sum of y^2
+// for kOutResid (0 otherwise).  y may alias S: each thread reads S and writes y
+// only at the points of its own rays, the source value is read before the
+// output at the same point is written.
+template <typename T, typename TX, typename TY, int kAhead = 4>
+__device__ double sweep_column(const ColDev &c, const Tables<T> &tb, const Common &cm,
+                               const T *S, const double *__restrict__ tsrc,
+                               const TX *__restrict__ x, const double *__restrict__ bv,
+                               TY *y, int out, bool inflow) {
+  double ss = 0.0;
+  for (int r = threadIdx.x; r < c.nr; r += blockDim.x)
+    ss += sweep_ray<T, TX, TY, kAhead>(c, tb, cm, S, tsrc, x, bv, y, out, inflow, r);
+  return ss;
+}
+
+}  // namespace rt

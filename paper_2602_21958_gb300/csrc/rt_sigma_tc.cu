@@ -1,0 +1,362 @@
+// rt_sigma_tc.cu -- Sigma with a dense kernel Psi on the 5th-generation tensor
+// cores (tcgen05, sm_103a):  S_p = Gamma_p Psi W X_p  (eq. Sigma), i.e. for one
+// column the GEMM  C[rows, r] = sum_q X[rows, q] PsiW[r, q]  with the rows the
+// points of every right-hand side stacked, then S = gamma * C.
+//
+//   operands  : bf16.  A = X rows, converted in registers by all threads and
+//               stored in the canonical no-swizzle K-major layout; B = PsiW,
+//               pre-tiled in global memory as the exact shared-memory image of
+//               each (256-ray, 64-q) block and fetched with one cp.async.bulk
+//               completing on an mbarrier.
+//   accumulate: fp32 in tensor memory (128 lanes x 256 columns), read back
+//               with tcgen05.ld and scaled by Gamma in the epilogue.
+//   pipeline  : two stages; thread 0 issues tcgen05.mma (M=128, N<=256, K=16,
+//               four per 64-wide chunk) and commits each stage to an mbarrier
+//               that gates the overwrite of that stage two chunks later.
+// Every wait is bounded; on timeout the CTA raises an error flag, drains what
+// it issued (bounded), frees its tensor memory and returns.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "rt_host.h"
+#include "rt_internal.cuh"
+
+namespace rt {
+
+constexpr int kTcBM = 128;               // rows per tile (MMA M, TMEM lanes)
+constexpr int kTcBN = 256;               // rays per tile (MMA N max, TMEM columns)
+constexpr int kTcBK = 64;                // q per stage: four MMAs of K = 16
+constexpr int kTcThreads = 256;
+constexpr int kTcABytes = kTcBM * kTcBK * 2;   // 16 KB
+constexpr int kTcBBytes = kTcBN * kTcBK * 2;   // 32 KB
+constexpr int kTcSmem = 2 * (kTcABytes + kTcBBytes) + 1024;
+constexpr long long kSpinLimit = 1ll << 26;
+
+struct TcJob {
+  int32_t col;  // column index
+  int32_t m0;   // first stacked row (rhs * nz + point)
+  int32_t n0;   // first ray
+  int32_t pad;
+};
+
+// ----------------------------------------------------------- PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+// Bounded wait for the phase with parity `par`; false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t par) {
+  const uint32_t a = smem_u32(bar);
+  for (long long it = 0; it < kSpinLimit; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(a), "r"(par)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: no swizzle, K-major canonical layout of
+// 8-row x 16-byte core matrices; lbo = byte distance of K-adjacent core
+// matrices, sbo = byte distance of 8-row groups.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor, kind::f16: bf16 x bf16 -> f32, both K-major.
+__host__ __device__ constexpr uint32_t tc_idesc(int m, int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc,
+                                       uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(uint64_t *bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+        "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
+  __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<uint32_t *>(&h);
+}
+
+// ----------------------------------------------------------------- kernel
+template <typename TX>
+__global__ void __launch_bounds__(kTcThreads, 1)
+    k_sigma_dense_tc(const ColDev *__restrict__ cols, const TcJob *__restrict__ jobs,
+                     const int64_t *__restrict__ btile_off, const uint16_t *__restrict__ btiles,
+                     const float *__restrict__ gamma, int n_rhs, int64_t E, const TX *__restrict__ X,
+                     float *__restrict__ S, int *err) {
+  extern __shared__ __align__(1024) uint8_t tc_smem[];
+  uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(tc_smem) + 1023) & ~uintptr_t(1023));
+  uint8_t *sA[2] = {base, base + kTcABytes};
+  uint8_t *sB[2] = {base + 2 * kTcABytes, base + 2 * kTcABytes + kTcBBytes};
+  __shared__ __align__(8) uint64_t bar_b[2], bar_mma[2];
+  __shared__ uint32_t tmem_base;
+  __shared__ int s_fail;
+
+  const TcJob job = jobs[blockIdx.x];
+  const ColDev c = cols[job.col];
+  const int nr = c.nr, nn = c.nn, nz = c.nz;
+  const int M = n_rhs * nz;
+  const int n_valid = min(kTcBN, nr - job.n0);      // multiple of 16 (nr is)
+  const int nk = nr / 16;                            // MMA K-steps in total
+  const int nchunk = (nr + kTcBK - 1) / kTcBK;
+  const int ntile_n = (nr + kTcBN - 1) / kTcBN;
+  const uint16_t *Bcol = btiles + btile_off[job.col];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+  if (tid == 0) {
+    mbar_init(&bar_b[0], 1);
+    mbar_init(&bar_b[1], 1);
+    mbar_init(&bar_mma[0], 1);
+    mbar_init(&bar_mma[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    s_fail = 0;
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                 "r"(kTcBN)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_base;
+  const uint32_t idesc = tc_idesc(kTcBM, (n_valid + 15) / 16 * 16);
+
+  // rows handled by this thread in the A conversion: item = tid + 256*j,
+  // row = item % 128, 8-wide K group = item / 128 (j = 0..3)
+  int issued_chunks = 0;
+  bool ok = true;
+  for (int kc = 0; kc < nchunk && ok; ++kc) {
+    const int s = kc & 1;
+    if (kc >= 2) {  // stage s was read by the MMAs of chunk kc-2
+      if (!mbar_wait(&bar_mma[s], ((kc - 2) >> 1) & 1)) ok = false;
+    }
+    if (!ok) break;
+    if (tid == 0) {
+      mbar_expect_tx(&bar_b[s], kTcBBytes);
+      const int nt = job.n0 / kTcBN;
+      bulk_g2s(sB[s], Bcol + ((int64_t)nt * nchunk + kc) * (kTcBN * kTcBK), kTcBBytes, &bar_b[s]);
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int item = tid + kTcThreads * j;
+      const int row = item & (kTcBM - 1), kq = item >> 7;
+      const int grow = job.m0 + row;
+      const int q0 = kc * kTcBK + kq * 8;
+      uint4 pk = make_uint4(0, 0, 0, 0);
+      if (grow < M && q0 < nr) {
+        const int rhs = grow / nz, p = grow - rhs * nz;
+        const TX *xr = X + rhs * E + c.x_off + (int64_t)p * nr + q0;
+        float f[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) f[e] = (q0 + e < nr) ? (float)xr[e] : 0.f;
+        pk.x = pack_bf16(f[0], f[1]);
+        pk.y = pack_bf16(f[2], f[3]);
+        pk.z = pack_bf16(f[4], f[5]);
+        pk.w = pack_bf16(f[6], f[7]);
+      }
+      *reinterpret_cast<uint4 *>(sA[s] + kq * (kTcBM / 8) * 128 + (row >> 3) * 128 + (row & 7) * 16) = pk;
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      if (!mbar_wait(&bar_b[s], (kc >> 1) & 1)) {
+        s_fail = 1;
+      } else {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t a0 = smem_u32(sA[s]), b0 = smem_u32(sB[s]);
+#pragma unroll
+        for (int ks = 0; ks < 4; ++ks) {
+          if (kc * 4 + ks < nk) {
+            const uint64_t ad = smem_desc(a0 + ks * 2 * (kTcBM / 8) * 128, (kTcBM / 8) * 128, 128);
+            const uint64_t bd = smem_desc(b0 + ks * 2 * (kTcBN / 8) * 128, (kTcBN / 8) * 128, 128);
+            tc_mma(tmem, ad, bd, idesc, (kc | ks) ? 1u : 0u);
+          }
+        }
+        tc_commit(&bar_mma[s]);
+      }
+    }
+    __syncthreads();
+    if (s_fail) ok = false;
+    issued_chunks = kc + 1;
+  }
+  // drain: the last commit completes after every earlier MMA of this thread
+  bool drained = true;
+  if (issued_chunks > 0) {
+    const int kl = issued_chunks - 1;
+    drained = mbar_wait(&bar_mma[kl & 1], (kl >> 1) & 1);
+  }
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (ok && drained) {
+    // epilogue: warp w reads TMEM lanes 32*(w%4).. and columns 128*(w/4)..
+    const int quarter = warp & 3, half = warp >> 2;
+    const int row = quarter * 32 + lane;
+    const int grow = job.m0 + row;
+    const bool valid_row = grow < M;
+    const int rhs = valid_row ? grow / nz : 0, p = valid_row ? grow - rhs * nz : 0;
+    float *srow = S + rhs * E + c.x_off + (int64_t)p * nr;
+    const float *grow_g = gamma + c.g_off + (int64_t)p * nn;
+    for (int cc = 0; cc < kTcBN / 2; cc += 16) {
+      const int col0 = half * (kTcBN / 2) + cc;
+      if (col0 >= n_valid) break;  // uniform across the warp
+      float v[16];
+      tc_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)col0, v);
+      if (valid_row) {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const int r = job.n0 + col0 + i;
+          if (col0 + i < n_valid) srow[r] = grow_g[r % nn] * v[i];
+        }
+      }
+    }
+  } else if (tid == 0) {
+    atomicOr(err, 1);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcBN) : "memory");
+  (void)ntile_n;
+}
+
+// ------------------------------------------------------------ host side
+static uint16_t bf16_bits(float f) {
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  if ((u & 0x7f800000u) == 0x7f800000u) return (uint16_t)(u >> 16);  // inf / nan
+  u += 0x7FFFu + ((u >> 16) & 1u);                                    // round to nearest even
+  return (uint16_t)(u >> 16);
+}
+
+// PsiW (row r, column q) = PsiwT[q][r] arranged per (256-ray tile, 64-q chunk)
+// as [q/8][r/8][r%8][q%8] bf16, zero padded beyond nr.
+void tc_build_tiles(const std::vector<ColDev> &cols, const std::vector<double> &psiwT,
+                    std::vector<uint16_t> &tiles, std::vector<int64_t> &offs) {
+  offs.assign(cols.size(), 0);
+  tiles.clear();
+  for (size_t ci = 0; ci < cols.size(); ++ci) {
+    const ColDev &c = cols[ci];
+    if (c.psi_off < 0 || c.nr % 16) continue;
+    const int nr = c.nr;
+    const int nt = (nr + kTcBN - 1) / kTcBN, nch = (nr + kTcBK - 1) / kTcBK;
+    offs[ci] = (int64_t)tiles.size();
+    tiles.resize(tiles.size() + (size_t)nt * nch * kTcBN * kTcBK, 0);
+    uint16_t *dst = tiles.data() + offs[ci];
+    const double *P = psiwT.data() + c.psi_off;
+    for (int t = 0; t < nt; ++t)
+      for (int ch = 0; ch < nch; ++ch) {
+        uint16_t *blk = dst + ((size_t)t * nch + ch) * kTcBN * kTcBK;
+        for (int rr = 0; rr < kTcBN; ++rr)
+          for (int qq = 0; qq < kTcBK; ++qq) {
+            const int r = t * kTcBN + rr, q = ch * kTcBK + qq;
+            const float v = (r < nr && q < nr) ? (float)P[(size_t)q * nr + r] : 0.f;
+            blk[(qq >> 3) * (kTcBN / 8) * 64 + (rr >> 3) * 64 + (rr & 7) * 8 + (qq & 7)] = bf16_bits(v);
+          }
+      }
+  }
+}
+
+void tc_build_jobs(const std::vector<ColDev> &cols, int n_rhs, std::vector<TcJob> &jobs) {
+  jobs.clear();
+  for (size_t ci = 0; ci < cols.size(); ++ci) {
+    const ColDev &c = cols[ci];
+    if (c.psi_off < 0 || c.nr % 16) continue;
+    const int M = n_rhs * c.nz;
+    for (int m0 = 0; m0 < M; m0 += kTcBM)
+      for (int n0 = 0; n0 < c.nr; n0 += kTcBN) jobs.push_back(TcJob{(int32_t)ci, m0, n0, 0});
+  }
+}
+
+// Builds the bf16 tiles and the job list of the tensor-core Sigma (mixed
+// precision handles with dense columns).  Returns a cudaError_t as int.
+int tc_prepare(rt_handle *h, const std::vector<double> &psiwT) {
+  std::vector<uint16_t> tiles;
+  std::vector<int64_t> offs;
+  std::vector<TcJob> jobs;
+  tc_build_tiles(h->h_cols, psiwT, tiles, offs);
+  tc_build_jobs(h->h_cols, h->n_rhs, jobs);
+  h->n_tc_jobs = (int)jobs.size();
+  if (jobs.empty()) return 0;
+  cudaError_t e = cudaMalloc(&h->d_tc_tiles, tiles.size() * 2);
+  if (e == cudaSuccess) e = cudaMemcpy(h->d_tc_tiles, tiles.data(), tiles.size() * 2, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMalloc(&h->d_tc_off, offs.size() * 8);
+  if (e == cudaSuccess) e = cudaMemcpy(h->d_tc_off, offs.data(), offs.size() * 8, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMalloc(&h->d_tc_jobs, jobs.size() * sizeof(TcJob));
+  if (e == cudaSuccess) e = cudaMemcpy(h->d_tc_jobs, jobs.data(), jobs.size() * sizeof(TcJob), cudaMemcpyHostToDevice);
+  return (int)e;
+}
+
+int launch_sigma_dense_tc(rt_handle *h, bool x_is_float, const void *x, float *S, cudaStream_t s) {
+  if (h->n_tc_jobs == 0) return 0;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(k_sigma_dense_tc<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
+    cudaFuncSetAttribute(k_sigma_dense_tc<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
+    attr_set = true;
+  }
+  if (x_is_float)
+    k_sigma_dense_tc<float><<<h->n_tc_jobs, kTcThreads, kTcSmem, s>>>(
+        h->d_cols, static_cast<const TcJob *>(h->d_tc_jobs), h->d_tc_off, h->d_tc_tiles, h->gam32, h->n_rhs,
+        h->E, static_cast<const float *>(x), S, h->d_err);
+  else
+    k_sigma_dense_tc<double><<<h->n_tc_jobs, kTcThreads, kTcSmem, s>>>(
+        h->d_cols, static_cast<const TcJob *>(h->d_tc_jobs), h->d_tc_off, h->d_tc_tiles, h->gam32, h->n_rhs,
+        h->E, static_cast<const double *>(x), S, h->d_err);
+  return (int)cudaGetLastError();
+}
+
+}  // namespace rt

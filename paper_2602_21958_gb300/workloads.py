@@ -431,22 +431,38 @@ def config_c2(seed: Optional[int] = None) -> Problem:
     return two_level_column(t, 8, 2, 64, "r2", eps, _b_linear_log(t), name="C2")
 
 
+def _c5_params(seed: Optional[int], n_col: int, nz_range, nnu_range):
+    rng = np.random.Generator(np.random.PCG64(SEED_BASE + 5 if seed is None else seed))
+    nzs = rng.integers(nz_range[0], nz_range[1] + 1, size=n_col)
+    nnus = rng.integers(nnu_range[0], nnu_range[1] + 1, size=n_col)
+    epss = 10.0 ** rng.uniform(-6, -2, size=n_col)
+    return nzs, nnus, epss
+
+
+def config_c5_column(ci: int, seed: Optional[int] = None, n_col: int = 256,
+                     nz_range=(64, 512), nnu_range=(32, 128)) -> Problem:
+    """Column ``ci`` of :func:`config_c5` (same seed stream), built alone."""
+    nzs, nnus, epss = _c5_params(seed, n_col, nz_range, nnu_range)
+    t = np.logspace(-4, 4, int(nzs[ci]))
+    return two_level_column(t, 8, 2, int(nnus[ci]), "r2", float(epss[ci]),
+                            _b_linear_log(t), name=f"C5[{ci}]")
+
+
 def config_c5(seed: Optional[int] = None, n_col: int = 256,
               nz_range=(64, 512), nnu_range=(32, 128)) -> list[Problem]:
     """Ragged batch of slabs: N_z ~ U{64..512} log-spaced points over t in
     [1e-4, 1e4] (the slab range of the CRD test column), N_nu ~ U{32..128},
     16 dirs, dipole x R_II-A, one log-uniform eps in [1e-6, 1e-2] per column,
     B linear in log t."""
-    rng = np.random.Generator(np.random.PCG64(SEED_BASE + 5 if seed is None else seed))
-    nzs = rng.integers(nz_range[0], nz_range[1] + 1, size=n_col)
-    nnus = rng.integers(nnu_range[0], nnu_range[1] + 1, size=n_col)
-    epss = 10.0 ** rng.uniform(-6, -2, size=n_col)
-    cols = []
-    for c in range(n_col):
-        t = np.logspace(-4, 4, int(nzs[c]))
-        cols.append(two_level_column(t, 8, 2, int(nnus[c]), "r2", float(epss[c]),
-                                     _b_linear_log(t), name=f"C5[{c}]"))
-    return cols
+    return [config_c5_column(c, seed, n_col, nz_range, nnu_range) for c in range(n_col)]
+
+
+def c5_random_rhs(ci: int, rhs: int, n: int, seed: Optional[int] = None) -> np.ndarray:
+    """Seeded N(0,1) right-hand side of instance (column ci, rhs >= 1) of the
+    ragged batch, drawn per instance so any instance can be rebuilt alone."""
+    base = SEED_BASE + 55 if seed is None else seed
+    rng = np.random.Generator(np.random.PCG64([base, ci, rhs]))
+    return rng.standard_normal(n)
 
 
 def box_3d(n: int, order: int, n_nu: int, kernel: str, eps: float, seed: int,

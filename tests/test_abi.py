@@ -1,0 +1,55 @@
+"""Host-side checks of the C ABI: the library builds, loads and exports every
+function declared in include/*.h (no compute calls without a GPU)."""
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    inc = os.path.join(ROOT, "include")
+    for f in os.listdir(inc):
+        if f.endswith(".h"):
+            txt = open(os.path.join(inc, f)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names |= set(re.findall(r"\b(rt_\w+)\s*\(", txt))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2602_21958_gb300 import build_lib, rt
+
+    build_lib.build()
+    return rt.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert {"rt_create", "rt_create_batch", "rt_apply", "rt_solve", "rt_destroy"} <= names
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_version_and_error_string(lib):
+    from paper_2602_21958_gb300 import rt
+
+    assert "sm_103a" in rt.version()
+    assert isinstance(lib.rt_last_error(), bytes)
+
+
+def test_binding_names_match_abi():
+    from paper_2602_21958_gb300 import rt
+
+    assert set(rt.EXPORTS) == _declared()
+    assert hasattr(rt.Handle, "rt_apply") and hasattr(rt.Handle, "rt_solve")
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    from paper_2602_21958_gb300 import rt
+
+    with pytest.raises(RuntimeError):
+        rt.load(str(tmp_path / "nope.so"))
