@@ -36,8 +36,10 @@ sys.path.insert(0, ROOT)
 METRIC = "RT operator applies/s and GMRES time-to-1e-10, mixed vs FP64 on one GB300"
 N_RHS = 4
 TOL = 1e-12          # relative residual target; the error against the oracle is checked
-TOL_INNER = 1e-5     # reduction asked of each float32 inner solve
-RESTART = 512        # upper bound; each instance uses what its slot holds
+RESTART = 512        # float64 GMRES(m): upper bound, each instance uses what its slot holds
+RESTART_MIXED = 32   # mixed: float64 flexible outer basis
+INNER = 20           # mixed: float32 inner GMRES cycle
+TOL_INNER = 0.1      # mixed: reduction asked of each inner cycle
 MAX_OUTER = 60
 
 
@@ -179,7 +181,7 @@ def run_ours(args, rank: int, world: int):
     cols = workload(rank)
     E = sum(c.n for c in cols)
     n_inst = len(cols) * N_RHS
-    hm = rt.Handle(cols, n_rhs=N_RHS, precision=rt.RT_P_MIXED, max_restart=RESTART)
+    hm = rt.Handle(cols, n_rhs=N_RHS, precision=rt.RT_P_MIXED, max_restart=RESTART_MIXED)
     b = torch.empty(N_RHS * E, dtype=torch.float64, device=dev)
     hm.rt_apply(rt.RT_OP_RHS, None, b, fp64=True)       # every rhs slot = physical b
     b[E:] = torch.from_numpy(build_rhs(cols, E, rank).reshape(-1)).to(dev)
@@ -187,7 +189,8 @@ def run_ours(args, rank: int, world: int):
     stream = torch.cuda.current_stream()
 
     def solve(h, xx):
-        return h.rt_solve(b, xx, tol=TOL, tol_inner=TOL_INNER, restart=RESTART, max_outer=MAX_OUTER)
+        return h.rt_solve(b, xx, tol=TOL, tol_inner=TOL_INNER, restart=RESTART_MIXED, max_outer=MAX_OUTER,
+                          inner_restart=INNER)
 
     for _ in range(args.warmup):
         info = solve(hm, x)
@@ -212,7 +215,6 @@ def run_ours(args, rank: int, world: int):
     # float64 path: same batch, same tolerance (one solve)
     h64 = rt.Handle(cols, n_rhs=N_RHS, precision=rt.RT_P_FP64, max_restart=RESTART)
     x64 = torch.zeros_like(b)
-    info64 = h64.rt_solve(b, x64, tol=TOL, restart=RESTART, max_outer=MAX_OUTER)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     info64 = h64.rt_solve(b, x64, tol=TOL, restart=RESTART, max_outer=MAX_OUTER)
@@ -244,7 +246,8 @@ def run_ours(args, rank: int, world: int):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(max(1, args.steps // 2)):
-        hm.rt_solve(bh, xh, tol=TOL, tol_inner=TOL_INNER, restart=RESTART, max_outer=MAX_OUTER)
+        hm.rt_solve(bh, xh, tol=TOL, tol_inner=TOL_INNER, restart=RESTART_MIXED, max_outer=MAX_OUTER,
+                    inner_restart=INNER)
     e2e_ms = (time.perf_counter() - t0) * 1e3 / max(1, args.steps // 2)
     e2e_ms = dist_max(e2e_ms, world)
     # roofline of the solve kernel (dominant kernel): algorithmic bytes / kernel time
@@ -275,6 +278,45 @@ def load_peaks():
         return float(d["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
     except Exception:
         return 6800.0, "fallback 6.8 TB/s"
+
+
+# ------------------------------------------------------------ ncu cases
+def profile_case(kind: str):
+    """Bounded workloads for ncu captures (a few GB on the device at most)."""
+    import torch
+
+    from paper_2602_21958_gb300 import rt, workloads as W
+
+    dev = torch.device("cuda", 0)
+    if kind == "solve-small":
+        cols = [W.config_c5_column(ci) for ci in range(16)]
+        h = rt.Handle(cols, n_rhs=1, precision=rt.RT_P_MIXED, max_restart=32)
+        E = sum(c.n for c in cols)
+        b = torch.empty(E, dtype=torch.float64, device=dev)
+        h.rt_apply(rt.RT_OP_RHS, None, b, fp64=True)
+        x = torch.zeros_like(b)
+        info = h.rt_solve(b, x, tol=1e-12, tol_inner=0.1, restart=32, max_outer=4, inner_restart=20)
+        print("solve-small", info)
+    elif kind == "apply":
+        cols = W.config_c5()
+        h = rt.Handle(cols, n_rhs=1, precision=rt.RT_P_MIXED, max_restart=4)
+        E = sum(c.n for c in cols)
+        x = torch.randn(E, dtype=torch.float64, device=dev)
+        y = torch.empty_like(x)
+        for _ in range(3):
+            h.rt_apply(rt.RT_OP_A, x, y)
+        torch.cuda.synchronize()
+        print("apply", E)
+    else:
+        cols = [W.config_c5_column(ci).with_dense_kernel() for ci in range(8)]
+        h = rt.Handle(cols, n_rhs=4, precision=rt.RT_P_MIXED, max_restart=4)
+        E = sum(c.n for c in cols)
+        x = torch.randn(4 * E, dtype=torch.float64, device=dev)
+        y = torch.empty_like(x)
+        for _ in range(3):
+            h.rt_apply(rt.RT_OP_SIGMA, x, y)
+        torch.cuda.synchronize()
+        print("sigma-tc", E)
 
 
 # ------------------------------------------------------------- distributed
@@ -320,14 +362,21 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", choices=["solve-small", "apply", "sigma-tc"], default=None,
+                    help="run one bounded case for an ncu capture and exit (no JSON line)")
     args = ap.parse_args()
+    if args.profile:
+        profile_case(args.profile)
+        return
     rank, world = dist_setup()
     n_inst = 256 * N_RHS
     config = {"workload": "C5 ragged batch: 256 1D columns (N_z~U{64..512}, N_nu~U{32..128}, "
                           "16 dirs, dipole x R_II-A, eps log-uniform 1e-6..1e-2), 4 rhs; solve to "
                           f"rel. residual {TOL:g}",
               "inputs_vs_l2": "inputs larger than L2 (each rhs vector ~0.7 GB)",
-              "restart": RESTART, "tol_inner": TOL_INNER, "parallelism": f"replicas x{world}"}
+              "solver": f"mixed: float64 FGMRES({RESTART_MIXED}) + float32 GMRES({INNER}) cycles "
+                        f"(tol_inner {TOL_INNER}); fp64: GMRES(<= {RESTART})",
+              "parallelism": f"replicas x{world}"}
     if args.impl == "reference":
         if rank != 0:
             return

@@ -92,11 +92,15 @@ typedef struct rt_desc {
 
 /* ---- solve options and report ----------------------------------------- */
 typedef struct rt_solve_opts {
-  double tol;          /* target ||b - A x||_2 / ||b||_2 per instance (e.g. 1e-11)      */
-  double tol_inner;    /* RT_P_MIXED: relative reduction asked of each inner solve    */
-  int32_t restart;     /* Krylov basis length m of GMRES(m); <= handle's max_restart  */
-  int32_t max_outer;   /* outer steps: refinement steps (mixed) or restarts (fp64)    */
-  int32_t use_x0;      /* 1: x holds the initial guess on entry; 0: start from x = 0  */
+  double tol;            /* target ||b - A x||_2 / ||b||_2 per instance (e.g. 1e-12)    */
+  double tol_inner;      /* RT_P_MIXED: relative reduction asked of each inner float32
+                            GMRES cycle (e.g. 0.1); it stops earlier if reached        */
+  int32_t restart;       /* basis length m: GMRES(m) (fp64) or the float64 flexible
+                            outer basis (mixed); <= max_restart; clipped per instance to
+                            what its workspace slot holds                             */
+  int32_t max_outer;     /* restart cycles allowed                                      */
+  int32_t use_x0;        /* 1: x holds the initial guess on entry; 0: start from x = 0  */
+  int32_t inner_restart; /* RT_P_MIXED: inner float32 GMRES cycle length (0 -> 20)      */
 } rt_solve_opts;
 
 typedef struct rt_info {
@@ -144,14 +148,18 @@ int64_t rt_vector_length(const rt_handle *h);
 int rt_apply(rt_handle *h, int32_t op, int32_t fp64, const double *x, double *y,
              void *stream);
 
-/* Solve A_N x = b for all instances (eq. RT_sys_algebraic).  b == NULL uses
- * the internal right-hand side Lambda t + I_in for every rhs.  RT_P_FP64:
- * restarted GMRES(m) in float64 (classical Gram-Schmidt with one
- * re-orthogonalisation, Givens rotations).  RT_P_MIXED: float64 iterative
- * refinement, r = b - A x in float64, inner GMRES(m) on the mixed operator with
- * float64 Arnoldi and Givens.  x0 = 0 unless opts->use_x0.  Synchronises the
- * stream and fills *info (may be NULL).  Returns RT_ERR_NOCONV if any instance
- * missed opts->tol (x still holds the best iterate). */
+/* Solve A_N x = b for all instances (eq. RT_sys_algebraic; the Krylov solvers
+ * of Sec. 5, unpreconditioned).  b == NULL uses the internal right-hand side
+ * Lambda t + I_in for every rhs.  RT_P_FP64: restarted GMRES(m) in float64
+ * (classical Gram-Schmidt with the DGKS re-orthogonalisation test, Givens
+ * rotations).  RT_P_MIXED: flexible GMRES(m) in float64 (Arnoldi,
+ * Givens, the residual b - A x and x all float64) whose directions are refined
+ * by one float32 GMRES(inner_restart) cycle on the float32 operator -- mixed
+ * precision iterative refinement with a float64 Krylov outer loop.  Batches:
+ * one persistent launch, a CTA per (column, rhs) instance; boxes: grid-wide
+ * kernels.  x0 = 0 unless opts->use_x0.  Synchronises the stream and fills
+ * *info (may be NULL).  Returns RT_ERR_NOCONV if any instance missed opts->tol
+ * (x still holds the last iterate). */
 int rt_solve(rt_handle *h, const double *b, double *x, const rt_solve_opts *opts,
              rt_info *info, void *stream);
 

@@ -113,9 +113,12 @@ void free_handle(rt_handle *h) {
                   h->b_int, h->d_order, h->d_queue, h->ws.V, h->ws.S, h->ws.H,
                   h->so.outer, h->so.inner, h->so.status, h->so.relres, h->so.bytes,
                   h->stage_x, h->stage_y, h->d_sig_tiles, h->d_sw_tiles, h->apply_S,
-                  h->d_tc_jobs, h->d_tc_off, h->d_tc_tiles, h->d_err};
+                  h->d_tc_jobs, h->d_tc_off, h->d_tc_tiles, h->d_err, h->d_geo,
+                  h->chi64, h->chi32, h->g_part, h->g_red, h->g_coef, h->g_r};
   for (void *p : ptrs)
     if (p) cudaFree(p);
+  if (h->solve_graph) cudaGraphExecDestroy(h->solve_graph);
+  if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
   delete h;
 }
 
@@ -265,13 +268,20 @@ int alloc_workspace(rt_handle *h, int max_restart) {
   const int64_t elt = h->precision == RT_P_FP64 ? 8 : 4;
   size_t free_b = 0, total_b = 0;
   RT_CUDA(cudaMemGetInfo(&free_b, &total_b));
-  const int64_t hld = (int64_t)(m + 1) * m + 3 * (m + 1);
-  // the largest instance must fit with at least min(m, 8) vectors
-  const int64_t min_cap = (int64_t)(std::min(m, 8) + 1) * ld * elt;
-  const int64_t want_cap = (int64_t)(m + 1) * ld * elt;
+  // Hessenberg + Givens storage for an outer and an inner basis of up to m
+  const int64_t hld = 2 * ((int64_t)(m + 1) * m + 3 * (m + 2));
+  // fp64: basis of m+1 float64 vectors.  mixed: outer float64 basis (m+1), its
+  // float32 preconditioned vectors (m), the inner float32 basis (m+1).  The
+  // largest instance must fit with at least min(m, 8) vectors of each.
+  auto bytes_per_elt = [&](int mm) -> int64_t {
+    return elt == 8 ? (int64_t)(mm + 1) * 8 : (int64_t)(mm + 1) * 8 + (int64_t)mm * 4 + (int64_t)(mm + 1) * 4;
+  };
+  const int64_t min_cap = bytes_per_elt(std::min(m, 8)) * ld;
+  const int64_t want_cap = bytes_per_elt(m) * ld;
   const double fixed = (double)(ld * 8 + hld * 8);
   const double budget = 0.6 * (double)free_b;
-  int slots = std::min(n_inst, 2 * h->n_sm);
+  // one 512-thread CTA per SM: a heavy instance gets a whole SM's bandwidth
+  int slots = std::min(n_inst, h->n_sm);
   while (slots > 1 && budget / slots < fixed + (double)min_cap) --slots;
   if (budget < fixed + (double)min_cap) return fail(RT_ERR_OOM, "not enough device memory for one Krylov workspace");
   int64_t cap = (int64_t)std::min<double>((double)want_cap, budget / slots - fixed);
@@ -461,8 +471,12 @@ int create_columns(const rt_desc *descs, int n_cols, int n_rhs, int precision, i
   {
     std::vector<int3> sig;
     std::vector<int2> sw;
+    // longest columns first: their sweeps are the longest sequential chains
+    std::vector<int> by_depth(n_cols);
+    std::iota(by_depth.begin(), by_depth.end(), 0);
+    std::stable_sort(by_depth.begin(), by_depth.end(), [&](int a, int b) { return cols[a].nz > cols[b].nz; });
     for (int r = 0; r < n_rhs; ++r) {
-      for (int ci = 0; ci < n_cols; ++ci) {
+      for (int ci : by_depth) {
         const rt::ColDev &c = cols[ci];
         const int inst = r * n_cols + ci;
         const int pb = rt::sigma_points_per_block(c);
@@ -501,6 +515,139 @@ int create_columns(const rt_desc *descs, int n_cols, int n_rhs, int precision, i
   return RT_OK;
 }
 
+
+// 3D box: Sigma tables as one "column" of n_pts points; plane-sweep geometry.
+int create_box(const rt_desc *d, int n_rhs, int precision, int max_restart, rt_handle **out) {
+  if (!out) return fail(RT_ERR_ARG, "out is null");
+  *out = nullptr;
+  if (n_rhs != 1) return fail(RT_ERR_ARG, "3D boxes take one right-hand side per handle");
+  if (precision != RT_P_FP64 && precision != RT_P_MIXED) return fail(RT_ERR_ARG, "unknown precision");
+  if (max_restart < 1 || max_restart > rt::max_krylov()) return fail(RT_ERR_ARG, "max_restart must be in [1, 512]");
+  if (d->nx < 1 || d->ny < 1 || d->nz < 2 || d->n_dir < 1 || d->n_nu < 1)
+    return fail(RT_ERR_ARG, "box: need nx, ny >= 1, nz >= 2, n_dir, n_nu >= 1");
+  if (!d->z || !d->dir || !d->w_dir || !d->w_nu || !d->chi || !d->gamma)
+    return fail(RT_ERR_ARG, "box: missing z (spacings), dir, w_dir, w_nu, chi or gamma");
+  if (!(d->z[0] > 0 && d->z[1] > 0 && d->z[2] > 0)) return fail(RT_ERR_ARG, "box: spacings must be positive");
+  if (!d->Psi && (!d->P || !d->R)) return fail(RT_ERR_ARG, "box: need Psi or both P and R");
+  if (d->formal_solver != RT_FS_SCL && d->formal_solver != RT_FS_IE) return fail(RT_ERR_ARG, "unknown formal_solver");
+  const int64_t npts = (int64_t)d->nx * d->ny * d->nz;
+  const int64_t plane = (int64_t)d->nx * d->ny;
+  if (plane * 32 > 200 * 1024) return fail(RT_ERR_ARG, "box: a z-plane must fit in shared memory (nx*ny <= 6400)");
+  for (int k = 0; k < d->n_dir; ++k)
+    if (!(std::fabs(d->dir[3 * k + 2]) > 0.0)) return fail(RT_ERR_ARG, "box: direction with Omega_z = 0");
+  const size_t np = (size_t)npts * d->n_nu;
+  if (!finite_all(d->chi, np) || !finite_all(d->gamma, np)) return fail(RT_ERR_NONFINITE, "box: non-finite chi or gamma");
+  for (size_t i = 0; i < np; ++i)
+    if (d->chi[i] < 0.0) return fail(RT_ERR_ARG, "box: negative opacity");
+  ColumnHost ch{};
+  rt_desc dd = *d;
+  int rc = build_column(&dd, ch);
+  if (rc != RT_OK) return rc;
+  rt_handle *h = new rt_handle();
+  h->dims = 3;
+  h->n_cols = 1;
+  h->n_rhs = 1;
+  h->precision = precision;
+  h->max_restart = max_restart;
+  rt::ColDev c = ch.c;
+  if (npts > 0x7fffffff) { free_handle(h); return fail(RT_ERR_ARG, "box too large"); }
+  c.nz = (int32_t)npts;
+  c.x_off = 0; c.g_off = 0; c.c_off = 0; c.r_off = 0; c.psi_off = d->Psi ? 0 : -1;
+  c.u_off = 0; c.d_off = 0; c.in_off = 0;
+  h->h_cols = {c};
+  h->E = npts * c.nr;
+  h->nmax = h->E;
+  h->box = rt::BoxDev{d->nx, d->ny, d->nz, d->n_dir, d->n_nu, d->formal_solver == RT_FS_IE ? 1 : 0};
+  std::vector<double> geo(4 * (size_t)d->n_dir);
+  for (int k = 0; k < d->n_dir; ++k) {
+    const double ox = d->dir[3 * k], oy = d->dir[3 * k + 1], oz = d->dir[3 * k + 2];
+    const double ds = d->z[2] / std::fabs(oz);
+    geo[4 * k + 0] = ox * ds / d->z[0];
+    geo[4 * k + 1] = oy * ds / d->z[1];
+    geo[4 * k + 2] = ds;
+    geo[4 * k + 3] = oz > 0 ? 1.0 : 0.0;
+  }
+  std::vector<double> chi(d->chi, d->chi + np), gam(d->gamma, d->gamma + np), itop, ibot, tsrc;
+  for (int f = 0; f < d->n_nu; ++f) {
+    itop.push_back(d->I_top ? d->I_top[f] : 0.0);
+    ibot.push_back(d->I_bot ? d->I_bot[f] : 0.0);
+  }
+  if (d->t_src) tsrc.assign(d->t_src, d->t_src + np);
+  std::vector<rt::ColDev> cols = {c};
+#define UPB(dst, src)                           \
+  if ((rc = dev_upload(&(dst), src)) != RT_OK) { \
+    free_handle(h);                             \
+    return rc;                                  \
+  }
+  UPB(h->d_cols, cols);
+  UPB(h->d_dir_cls, ch.dir_cls);
+  UPB(h->d_dir_up, ch.dir_up);
+  UPB(h->d_geo, geo);
+  UPB(h->chi64, chi);
+  std::vector<float> chif = to_f32(chi), gamf = to_f32(gam);
+  UPB(h->chi32, chif);
+  UPB(h->gam64, gam);
+  UPB(h->gam32, gamf);
+  UPB(h->d_Itop, itop);
+  UPB(h->d_Ibot, ibot);
+  if (!tsrc.empty()) UPB(h->d_tsrc, tsrc);
+  UPB(h->Uw64, ch.Uw);
+  UPB(h->Ul64, ch.Ul);
+  UPB(h->Rw64, ch.Rw);
+  std::vector<float> Uwf = to_f32(ch.Uw), Ulf = to_f32(ch.Ul), Rwf = to_f32(ch.Rw);
+  UPB(h->Uw32, Uwf);
+  UPB(h->Ul32, Ulf);
+  UPB(h->Rw32, Rwf);
+  if (!ch.Psi.empty()) {
+    UPB(h->Psi64, ch.Psi);
+    std::vector<float> Psif = to_f32(ch.Psi);
+    UPB(h->Psi32, Psif);
+  }
+  std::vector<int3> sig;
+  const int pb = rt::sigma_points_per_block(c);
+  for (int64_t p0 = 0; p0 < npts; p0 += pb) sig.push_back(make_int3(0, (int)p0, (int)std::min<int64_t>(pb, npts - p0)));
+  h->n_sig_tiles = h->n_sig_tiles_rhs0 = (int)sig.size();
+  UPB(h->d_sig_tiles, sig);
+#undef UPB
+  int dev = 0;
+  cudaError_t ce = cudaGetDevice(&dev);
+  if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&h->n_sm, cudaDevAttrMultiProcessorCount, dev);
+  const int G = 2 * h->n_sm;
+  if (ce == cudaSuccess) ce = cudaMalloc(&h->apply_S, (size_t)h->E * sizeof(double));
+  if (ce == cudaSuccess) ce = cudaMalloc(&h->g_r, (size_t)h->E * sizeof(double));
+  if (ce == cudaSuccess) ce = cudaMalloc(&h->g_part, (size_t)G * 16 * sizeof(double));
+  if (ce == cudaSuccess) ce = cudaMalloc(&h->g_red, 64 * sizeof(double));
+  if (ce == cudaSuccess) ce = cudaMalloc(&h->g_coef, 1024 * sizeof(double));
+  if (ce == cudaSuccess) ce = cudaMalloc(&h->d_err, sizeof(int));
+  if (ce == cudaSuccess) ce = cudaMemset(h->d_err, 0, sizeof(int));
+  if (ce == cudaSuccess) ce = cudaMalloc(&h->b_int, (size_t)h->E * sizeof(double));
+  if (ce != cudaSuccess) {
+    free_handle(h);
+    return fail(ce == cudaErrorMemoryAllocation ? RT_ERR_OOM : RT_ERR_CUDA, std::string("box buffers: ") + cudaGetErrorString(ce));
+  }
+  // Krylov basis: as many vectors as 60% of the free memory holds, up to max_restart
+  size_t free_b = 0, total_b = 0;
+  cudaMemGetInfo(&free_b, &total_b);
+  const int64_t ldv = (h->E + 31) / 32 * 32;
+  const int64_t elt = precision == RT_P_FP64 ? 8 : 4;
+  int m = max_restart;
+  while (m > 1 && (double)(m + 1) * ldv * elt > 0.6 * (double)free_b) --m;
+  if ((double)(m + 1) * ldv * elt > 0.6 * (double)free_b) { free_handle(h); return fail(RT_ERR_OOM, "box: no room for a Krylov basis"); }
+  h->ws.slots = 1;
+  h->ws.m = m;
+  h->ws.ld = ldv;
+  h->ws.cap_bytes = (m + 1) * ldv * elt;
+  ce = cudaMalloc(&h->ws.V, (size_t)h->ws.cap_bytes);
+  if (ce == cudaSuccess) ce = (cudaError_t)rt::apply_box(h, RT_OP_RHS, true, nullptr, false, h->b_int, false, 0);
+  if (ce == cudaSuccess) ce = cudaDeviceSynchronize();
+  if (ce != cudaSuccess) {
+    free_handle(h);
+    return fail(ce == cudaErrorMemoryAllocation ? RT_ERR_OOM : RT_ERR_CUDA, std::string("box setup: ") + cudaGetErrorString(ce));
+  }
+  *out = h;
+  return RT_OK;
+}
+
 int ensure_stage(rt_handle *h, int64_t len) {
   if (h->stage_len >= len) return RT_OK;
   if (h->stage_x) cudaFree(h->stage_x);
@@ -524,7 +671,7 @@ const char *rt_version(void) { return "rt_gb300 0.1 (sm_103a)"; }
 int rt_create(const rt_desc *desc, int32_t n_rhs, int32_t precision, int32_t max_restart,
               rt_handle **out) {
   if (!desc) return fail(RT_ERR_ARG, "null descriptor");
-  if (desc->dims == 3) return fail(RT_ERR_ARG, "3D boxes are not available in this build");
+  if (desc->dims == 3) return create_box(desc, n_rhs, precision, max_restart, out);
   return create_columns(desc, 1, n_rhs, precision, max_restart, out);
 }
 
@@ -582,6 +729,8 @@ int rt_solve(rt_handle *h, const double *b, double *x, const rt_solve_opts *o, r
   if (!(o->tol > 0.0) || o->max_outer < 1) return fail(RT_ERR_ARG, "need tol > 0 and max_outer >= 1");
   if (h->precision == RT_P_MIXED && !(o->tol_inner > 0.0 && o->tol_inner < 1.0))
     return fail(RT_ERR_ARG, "mixed precision needs 0 < tol_inner < 1");
+  if (o->inner_restart < 0 || o->inner_restart > h->ws.m)
+    return fail(RT_ERR_ARG, "inner_restart outside [0, max_restart]");
   cudaStream_t s = (cudaStream_t)stream;
   const int64_t len = h->E * h->n_rhs;
   const bool bd = b ? is_device_ptr(b) : true, xd = is_device_ptr(x);
@@ -599,11 +748,91 @@ int rt_solve(rt_handle *h, const double *b, double *x, const rt_solve_opts *o, r
       xio = h->stage_x;
     }
   }
+  if (h->dims == 3) {
+    int outer = 0, inner = 0, status = 0;
+    double relres = 1.0, bytes = 0.0;
+    cudaEvent_t e0, e1;
+    RT_CUDA(cudaEventCreate(&e0));
+    RT_CUDA(cudaEventCreate(&e1));
+    RT_CUDA(cudaEventRecord(e0, s));
+    const int e = rt::launch_grid_solve(h, bin ? bin : h->b_int, xio, o->tol, o->tol_inner, o->restart,
+                                        o->max_outer, o->use_x0, s, outer, inner, relres, status, bytes);
+    RT_CUDA(cudaEventRecord(e1, s));
+    if (e != 0) {
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      return fail(RT_ERR_CUDA, std::string("grid solve: ") + cudaGetErrorString((cudaError_t)e));
+    }
+    if (!xd) RT_CUDA(cudaMemcpyAsync(x, xio, len * sizeof(double), cudaMemcpyDeviceToHost, s));
+    RT_CUDA(cudaStreamSynchronize(s));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    h->last_bytes = bytes;
+    if (info) {
+      rt_info loc{};
+      loc.status = status;
+      loc.n_instances = 1;
+      loc.max_outer = outer;
+      loc.max_inner = inner;
+      loc.total_inner = inner;
+      loc.max_relres = relres;
+      loc.ms = ms;
+      loc.bytes = bytes;
+      loc.inst_outer = info->inst_outer;
+      loc.inst_inner = info->inst_inner;
+      loc.inst_relres = info->inst_relres;
+      if (info->inst_outer) info->inst_outer[0] = outer;
+      if (info->inst_inner) info->inst_inner[0] = inner;
+      if (info->inst_relres) info->inst_relres[0] = relres;
+      *info = loc;
+    }
+    if (status != RT_OK) {
+      char msg[160];
+      std::snprintf(msg, sizeof msg, "solve: status %d, relative residual %.3e", status, relres);
+      g_err = msg;
+    }
+    return status;
+  }
   cudaEvent_t e0, e1;
   RT_CUDA(cudaEventCreate(&e0));
   RT_CUDA(cudaEventCreate(&e1));
+  // the launch (queue reset + persistent kernel) is captured once into a CUDA
+  // graph and replayed while (b, x, options) stay the same
+  const int m_in = o->inner_restart > 0 ? o->inner_restart : 20;
+  unsigned long long key[8];
+  key[0] = (unsigned long long)(uintptr_t)bin;
+  key[1] = (unsigned long long)(uintptr_t)xio;
+  std::memcpy(&key[2], &o->tol, 8);
+  std::memcpy(&key[3], &o->tol_inner, 8);
+  key[4] = (unsigned long long)o->restart;
+  key[5] = (unsigned long long)o->max_outer;
+  key[6] = (unsigned long long)o->use_x0;
+  key[7] = (unsigned long long)m_in;
+  int e = 0;
+  if (!h->solve_graph || std::memcmp(key, h->graph_key, sizeof key) != 0) {
+    if (h->solve_graph) {
+      cudaGraphExecDestroy(h->solve_graph);
+      h->solve_graph = nullptr;
+    }
+    if (!h->capture_stream) RT_CUDA(cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking));
+    cudaGraph_t graph = nullptr;
+    RT_CUDA(cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeThreadLocal));
+    e = rt::launch_solve(h, bin, xio, o->tol, o->tol_inner, o->restart, o->max_outer, o->use_x0,
+                         h->capture_stream, m_in);
+    const cudaError_t ce = cudaStreamEndCapture(h->capture_stream, &graph);
+    if (e == 0 && ce != cudaSuccess) e = (int)ce;
+    if (e == 0) e = (int)cudaGraphInstantiate(&h->solve_graph, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (e == 0) std::memcpy(h->graph_key, key, sizeof key);
+    h->graph_replays = 0;
+  }
   RT_CUDA(cudaEventRecord(e0, s));
-  int e = rt::launch_solve(h, bin, xio, o->tol, o->tol_inner, o->restart, o->max_outer, o->use_x0, s);
+  if (e == 0) {
+    e = (int)cudaGraphLaunch(h->solve_graph, s);
+    ++h->graph_replays;
+  }
   if (e != 0) {
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

@@ -40,8 +40,8 @@ __global__ void __launch_bounds__(kRayBlock) k_sweep_tiles(Common cm, Tables<T> 
   if (r >= c.nr) return;
   const int64_t base = rhs * E + c.x_off;
   const double *ts = use_tsrc ? cm.tsrc + c.g_off : nullptr;
-  sweep_ray<T, double, double>(c, tb, cm, S ? S + base : nullptr, ts, x ? x + base : nullptr, nullptr,
-                               y + base, out, inflow != 0, r);
+  sweep_ray<T, double, double, 8>(c, tb, cm, S ? S + base : nullptr, ts, x ? x + base : nullptr, nullptr,
+                                  y + base, out, inflow != 0, r);
 }
 
 template <typename T>
@@ -58,12 +58,12 @@ __global__ void k_widen(const T *a, double *b, int64_t n) {
 
 template <typename T>
 static int run_apply(rt_handle *h, const Tables<T> &tb, int op, const double *x, double *y, cudaStream_t s,
-                     bool first_rhs_only) {
+                     bool first_rhs_only, void *scratch) {
   const Common cm{h->d_cols, h->d_dir_cls, h->d_dir_up, h->d_tsrc, h->d_Itop, h->d_Ibot};
   const int nsig = first_rhs_only ? h->n_sig_tiles_rhs0 : h->n_sig_tiles;
   const int nsw = first_rhs_only ? h->n_sw_tiles_rhs0 : h->n_sw_tiles;
   const int64_t len = (first_rhs_only ? 1 : h->n_rhs) * h->E;
-  T *S = reinterpret_cast<T *>(h->apply_S);
+  T *S = reinterpret_cast<T *>(scratch ? scratch : h->apply_S);
   const bool tc = sizeof(T) == 4 && h->n_tc_jobs > 0 && !first_rhs_only;
   auto sigma = [&]() -> int {
     k_sigma_tiles<T, double><<<nsig, kSigNT, 0, s>>>(cm, tb, h->d_sig_tiles, h->n_cols, h->E, x, S, tc ? 1 : 0);
@@ -97,14 +97,68 @@ static int run_apply(rt_handle *h, const Tables<T> &tb, int op, const double *x,
   return (int)cudaGetLastError();
 }
 
-int launch_apply(rt_handle *h, int op, bool fp64, const double *x, double *y, cudaStream_t s,
-                 bool first_rhs_only) {
+template <typename T, typename TX>
+static int box_apply_t(rt_handle *h, const Tables<T> &tb, int op, const TX *x, void *y, bool yf, cudaStream_t s,
+                       void *scratch) {
+  const Common cm{h->d_cols, h->d_dir_cls, h->d_dir_up, h->d_tsrc, h->d_Itop, h->d_Ibot};
+  T *S = reinterpret_cast<T *>(scratch ? scratch : h->apply_S);
+  const bool fp64 = sizeof(T) == 8;
+  const bool xf = sizeof(TX) == 4;
+  const int64_t len = h->E;
+  const int cgrid = (int)std::min<int64_t>((len + 255) / 256, 16 * 152);
+  switch (op) {
+    case 0:
+      k_sigma_tiles<T, TX><<<h->n_sig_tiles, kSigNT, 0, s>>>(cm, tb, h->d_sig_tiles, 1, h->E, x, S, 0);
+      return launch_sweep3d(h, fp64, S, nullptr, x, xf, y, yf, kOutAminus, false, s);
+    case 1:
+      if (xf) return (int)cudaErrorInvalidValue;
+      k_convert<T><<<cgrid, 256, 0, s>>>(reinterpret_cast<const double *>(x), S, len);
+      return launch_sweep3d(h, fp64, S, nullptr, nullptr, false, y, yf, kOutI, false, s);
+    case 2:
+      if (yf) return (int)cudaErrorInvalidValue;
+      k_sigma_tiles<T, TX><<<h->n_sig_tiles, kSigNT, 0, s>>>(cm, tb, h->d_sig_tiles, 1, h->E, x, S, 0);
+      k_widen<T><<<cgrid, 256, 0, s>>>(S, static_cast<double *>(y), len);
+      return (int)cudaGetLastError();
+    default:
+      if (h->d_tsrc) return launch_sweep3d(h, fp64, S, h->d_tsrc, nullptr, false, y, yf, kOutI, true, s);
+      cudaMemsetAsync(S, 0, len * sizeof(T), s);
+      return launch_sweep3d(h, fp64, S, nullptr, nullptr, false, y, yf, kOutI, true, s);
+  }
+}
+
+// Operators of a 3D box: Sigma by point tiles, then the plane sweep.  x (and
+// y) are float32 when xf (yf), else float64; the float64 operator needs both
+// in float64.
+static int apply_box_s(rt_handle *h, int op, bool fp64, const void *x, bool xf, void *y, bool yf, cudaStream_t s,
+                       void *scratch) {
   if (fp64 || h->precision == 0) {
     const Tables<double> tb{h->E64, h->A64, h->B64, h->Uw64, h->Ul64, h->Rw64, h->Psi64, h->gam64};
-    return run_apply<double>(h, tb, op, x, y, s, first_rhs_only);
+    if (xf) return (int)cudaErrorInvalidValue;
+    return box_apply_t<double, double>(h, tb, op, static_cast<const double *>(x), y, yf, s, scratch);
   }
   const Tables<float> tb{h->E32, h->A32, h->B32, h->Uw32, h->Ul32, h->Rw32, h->Psi32, h->gam32};
-  return run_apply<float>(h, tb, op, x, y, s, first_rhs_only);
+  if (xf) return box_apply_t<float, float>(h, tb, op, static_cast<const float *>(x), y, yf, s, scratch);
+  return box_apply_t<float, double>(h, tb, op, static_cast<const double *>(x), y, yf, s, scratch);
+}
+
+int apply_box(rt_handle *h, int op, bool fp64, const void *x, bool xf, void *y, bool yf, cudaStream_t s) {
+  return apply_box_s(h, op, fp64, x, xf, y, yf, s, nullptr);
+}
+
+static int launch_apply_s(rt_handle *h, int op, bool fp64, const double *x, double *y, cudaStream_t s,
+                          bool first_rhs_only, void *scratch) {
+  if (h->dims == 3) return apply_box_s(h, op, fp64, x, false, y, false, s, scratch);
+  if (fp64 || h->precision == 0) {
+    const Tables<double> tb{h->E64, h->A64, h->B64, h->Uw64, h->Ul64, h->Rw64, h->Psi64, h->gam64};
+    return run_apply<double>(h, tb, op, x, y, s, first_rhs_only, scratch);
+  }
+  const Tables<float> tb{h->E32, h->A32, h->B32, h->Uw32, h->Ul32, h->Rw32, h->Psi32, h->gam32};
+  return run_apply<float>(h, tb, op, x, y, s, first_rhs_only, scratch);
+}
+
+int launch_apply(rt_handle *h, int op, bool fp64, const double *x, double *y, cudaStream_t s,
+                 bool first_rhs_only) {
+  return launch_apply_s(h, op, fp64, x, y, s, first_rhs_only, nullptr);
 }
 
 }  // namespace rt

@@ -15,7 +15,7 @@
 
 namespace rt {
 
-constexpr int kNT = 256;      // threads per CTA of the apply / solve kernels
+constexpr int kNT = 512;      // threads per CTA of the solve kernel (one CTA per SM)
 constexpr int kDots = 8;      // basis vectors per block reduction in Gram-Schmidt
 
 int solve_block_threads() { return kNT; }
@@ -107,8 +107,9 @@ struct SolveParams {
   double *x;            // [n_rhs][E]
   double tol, tol_inner;
   int m, max_outer, use_x0;
-  void *V;              // [slots][cap] Krylov basis, element type of the inner solve
-  int64_t cap;          // basis capacity of one slot (elements)
+  int m_in;             // mixed precision: inner float32 GMRES cycle length
+  void *V;              // [slots][cap] Krylov bases of one slot
+  int64_t cap;          // fp64 path: basis capacity of one slot in elements; mixed: bytes
   double *S;            // [slots][ld] float64 scratch: source function / residual
   int64_t ld;
   double *H;            // [slots][hld] Hessenberg (column-major), cs, sn, g
@@ -436,8 +437,251 @@ __global__ void __launch_bounds__(kNT) k_solve(SolveParams p) {
   }
 }
 
+
+// ---------------------------------------------------------------- mixed solve
+// Givens update of column j of a Hessenberg matrix stored column-major with
+// leading dimension ld (thread 0 only); returns |g_{j+1}| and den via s_val.
+__device__ __forceinline__ void givens_step(double *Hc, int ld, double *cs, double *sn, double *g, int j,
+                                            const double *h, const double *h2, double hn, double *s_val) {
+  double *col = Hc + (int64_t)j * ld;
+  for (int i = 0; i <= j; ++i) col[i] = h[i] + h2[i];
+  col[j + 1] = hn;
+  for (int i = 0; i < j; ++i) {
+    const double t0 = cs[i] * col[i] + sn[i] * col[i + 1];
+    col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
+    col[i] = t0;
+  }
+  const double den = hypot(col[j], col[j + 1]);
+  double cj = 1.0, sj = 0.0;
+  if (den > 0.0) { cj = col[j] / den; sj = col[j + 1] / den; }
+  cs[j] = cj;
+  sn[j] = sj;
+  col[j] = den;
+  col[j + 1] = 0.0;
+  g[j + 1] = -sj * g[j];
+  g[j] = cj * g[j];
+  s_val[0] = fabs(g[j + 1]);
+  s_val[1] = den;
+}
+
+// One Arnoldi step on basis V[0..j] (TL) with w = V[j+1] unnormalised:
+// classical Gram-Schmidt with the DGKS test and a fused normalisation (see
+// k_solve).  Leaves h (+ h2) and returns ||w - V h||; bytes per element in bpe.
+template <typename TL>
+__device__ double arnoldi_orth(TL *V, int64_t ldv, int j, int64_t n, double *h, double *h2, TL *hf,
+                               double *red, double *outb, double &bpe) {
+  TL *w = V + (int64_t)(j + 1) * ldv;
+  const double sz = sizeof(TL);
+  const double ww = cta_dots<TL>(V, ldv, j, w, n, h, red, outb);
+  double hh = 0.0;
+  for (int i = 0; i <= j; ++i) hh += h[i] * h[i];
+  bpe += sz * (j + 2);
+  double hn;
+  if (ww - hh > 0.5 * ww) {
+    hn = sqrt(ww - hh);
+    cta_update<TL>(V, ldv, j, w, n, h, hn > 0.0 ? 1.0 / hn : 0.0, false, hf, red, outb);
+    for (int i = threadIdx.x; i <= j; i += blockDim.x) h2[i] = 0.0;
+    bpe += sz * (j + 3);
+  } else {
+    cta_update<TL>(V, ldv, j, w, n, h, 1.0, false, hf, red, outb);
+    cta_dots<TL>(V, ldv, j, w, n, h2, red, outb);
+    hn = sqrt(cta_update<TL>(V, ldv, j, w, n, h2, 1.0, true, hf, red, outb));
+    const TL inv = (TL)(hn > 0.0 ? 1.0 / hn : 0.0);
+    for (int64_t k = threadIdx.x; k < n; k += blockDim.x) w[k] *= inv;
+    bpe += sz * (3.0 * j + 10.0);
+  }
+  __syncthreads();
+  return hn;
+}
+
+// y = R^-1 g for the leading k x k triangle of H (thread 0), result in y
+__device__ __forceinline__ void tri_solve(const double *Hc, int ld, const double *g, int k, double *y) {
+  if (threadIdx.x == 0) {
+    for (int i = k - 1; i >= 0; --i) {
+      double acc = g[i];
+      for (int q = i + 1; q < k; ++q) acc -= Hc[(int64_t)q * ld + i] * y[q];
+      y[i] = acc / Hc[(int64_t)i * ld + i];
+    }
+  }
+  __syncthreads();
+}
+
+// Mixed precision (RT_P_MIXED): flexible GMRES(kout) with the Arnoldi basis,
+// Givens rotations, residual and x in float64, preconditioned by one cycle of
+// float32 GMRES(m_in) on the float32 operator (relative tolerance tol_inner):
+//   z_i ~ A^-1 v_i (float32), w = A z_i (float64 operator), orthogonalise w,
+//   x += Z y at the end of a cycle; cycles restart from the true residual.
+// One CTA per (column, rhs) instance, as k_solve.
+__global__ void __launch_bounds__(kNT) k_solve_nested(SolveParams p) {
+  __shared__ double sm[2 * kSigBuf];
+  __shared__ double red[(kNT / 32) * (kDots + 1)];
+  __shared__ double outb[kDots + 1];
+  __shared__ double hbuf[2 * (kMaxM + 8)];
+  __shared__ double ybuf[kMaxM + 8];
+  __shared__ float hf32[kMaxM + 8];
+  __shared__ double hf64[kMaxM + 8];
+  __shared__ int s_q;
+  __shared__ double s_val[4];
+  uint8_t *slot = reinterpret_cast<uint8_t *>(p.V) + (int64_t)blockIdx.x * p.cap;
+  double *S64 = p.S + (int64_t)blockIdx.x * p.ld;
+  float *S32 = reinterpret_cast<float *>(S64);
+  double *Hbase = p.H + (int64_t)blockIdx.x * p.hld;
+  double *h = hbuf;
+  double *h2 = hbuf + kMaxM + 8;
+  for (;;) {
+    const int q = next_instance(p.queue, &s_q);
+    if (q >= p.n_inst) break;
+    const int inst = p.order[q];
+    const int ci = inst % p.n_cols, rhs = inst / p.n_cols;
+    const ColDev c = p.cm.cols[ci];
+    const int64_t n = (int64_t)c.nz * c.nr;
+    const int64_t ldv = (n + 31) / 32 * 32;
+    const int m_in = min(p.m_in, kMaxM);
+    // slot: Vout [(kout+1) ldv] double | Z [kout ldv] float | U [(m_in+1) ldv] float
+    const int64_t per = p.cap / ldv;  // bytes per vector element available
+    const int64_t kfit = (per - 8 - 4 * (int64_t)(m_in + 1)) / 12;
+    const int kout = (int)(kfit < (int64_t)min(p.m, kMaxM) ? kfit : (int64_t)min(p.m, kMaxM));
+    double *Vo = reinterpret_cast<double *>(slot);
+    float *Z = reinterpret_cast<float *>(Vo + (int64_t)(kout + 1) * ldv);
+    float *U = Z + (int64_t)kout * ldv;
+    double *Ho = Hbase;
+    double *cso = Ho + (int64_t)(kout + 1) * kout, *sno = cso + (kout + 1), *go = sno + (kout + 1);
+    double *Hi = go + (kout + 2);
+    double *csi = Hi + (int64_t)(m_in + 1) * m_in, *sni = csi + (m_in + 1), *gi = sni + (m_in + 1);
+    const double *bv = p.b + (p.b_shared ? 0 : rhs * p.E) + c.x_off;
+    double *x = p.x + rhs * p.E + c.x_off;
+    const double bn = sqrt(cta_norm2(bv, n, red, outb));
+    if (!p.use_x0) {
+      for (int64_t k = threadIdx.x; k < n; k += blockDim.x) x[k] = 0.0;
+      __syncthreads();
+    }
+    int status = kNoConv, cycles = 0, outer_total = 0, inner_total = 0;
+    double relres = 1.0;
+    double bpe = p.use_x0 ? 8.0 : 16.0;
+    const bool bad_b = !(bn == bn) || bn > 1e300;
+    if (bad_b) {
+      status = kNonFinite;
+    } else if (bn == 0.0) {
+      status = kConverged;
+      relres = 0.0;
+    }
+    for (; bn > 0.0 && !bad_b && kout >= 1; ++cycles) {
+      double rn;
+      const double *rsrc;
+      if (cycles == 0 && !p.use_x0) {
+        rn = bn;
+        rsrc = bv;
+      } else {
+        sigma_column<double, double>(c, p.t64, x, S64, sm, sm + kSigBuf);
+        double a[1] = {sweep_column<double, double, double>(c, p.t64, p.cm, S64, nullptr, x, bv, S64,
+                                                            kOutResid, false)};
+        block_sum<1>(a, red, outb);
+        rn = sqrt(a[0]);
+        rsrc = S64;
+        bpe += 48.0;
+      }
+      relres = rn / bn;
+      if (!(rn == rn) || rn > 1e300) { status = kNonFinite; break; }
+      if (relres <= p.tol) { status = kConverged; break; }
+      if (cycles >= p.max_outer) { status = kNoConv; break; }
+      for (int64_t k = threadIdx.x; k < n; k += blockDim.x) Vo[k] = rsrc[k] / rn;
+      __syncthreads();
+      bpe += 16.0;
+      if (threadIdx.x == 0) go[0] = rn;
+      int idone = 0;
+      for (int i = 0; i < kout; ++i) {
+        // ---- inner: one float32 GMRES(m_in) cycle, z_i ~ A^-1 v_i -----------
+        const double *vi = Vo + (int64_t)i * ldv;
+        float *zi = Z + (int64_t)i * ldv;
+        double a0[1] = {0.0};
+        for (int64_t k = threadIdx.x; k < n; k += blockDim.x) {
+          const float u = (float)vi[k];
+          U[k] = u;
+          a0[0] += (double)u * (double)u;
+        }
+        block_sum<1>(a0, red, outb);
+        const double beta = sqrt(a0[0]);
+        {
+          const float inv = (float)(1.0 / beta);
+          for (int64_t k = threadIdx.x; k < n; k += blockDim.x) U[k] *= inv;
+          __syncthreads();
+        }
+        bpe += 8.0 + 4.0 + 8.0;
+        if (threadIdx.x == 0) gi[0] = beta;
+        int jdone = 0;
+        for (int j = 0; j < m_in; ++j) {
+          float *uj = U + (int64_t)j * ldv;
+          float *w = U + (int64_t)(j + 1) * ldv;
+          sigma_column<float, float>(c, p.t32, uj, S32, reinterpret_cast<float *>(sm),
+                                     reinterpret_cast<float *>(sm) + kSigBuf);
+          sweep_column<float, float, float>(c, p.t32, p.cm, S32, nullptr, uj, nullptr, w, kOutAminus, false);
+          __syncthreads();
+          bpe += 20.0;
+          const double hn = arnoldi_orth<float>(U, ldv, j, n, h, h2, hf32, red, outb, bpe);
+          if (threadIdx.x == 0) givens_step(Hi, m_in + 1, csi, sni, gi, j, h, h2, hn, s_val);
+          __syncthreads();
+          const double est = s_val[0], den = s_val[1];
+          jdone = j + 1;
+          if (den == 0.0) { jdone = j; break; }
+          if (!(hn > 1e-30 * beta)) break;
+          if (!(est == est) || est <= p.tol_inner * beta) break;
+        }
+        inner_total += jdone;
+        tri_solve(Hi, m_in + 1, gi, jdone, ybuf);
+        stage_coef<float>(ybuf, jdone, 1.0, hf32);
+        for (int64_t k0 = threadIdx.x; k0 < n; k0 += (int64_t)kU * blockDim.x) {
+          float d[kU];
+#pragma unroll
+          for (int e = 0; e < kU; ++e) d[e] = 0.f;
+          axpy_block<float>(U, ldv, jdone, hf32, k0, n, d);
+#pragma unroll
+          for (int e = 0; e < kU; ++e) {
+            const int64_t k = k0 + (int64_t)e * blockDim.x;
+            if (k < n) zi[k] = d[e];
+          }
+        }
+        __syncthreads();
+        bpe += 4.0 * (jdone + 1);
+        // ---- outer: w = A z_i in float64, orthogonalise in float64 ----------
+        double *w = Vo + (int64_t)(i + 1) * ldv;
+        sigma_column<double, float>(c, p.t64, zi, S64, sm, sm + kSigBuf);
+        sweep_column<double, float, double>(c, p.t64, p.cm, S64, nullptr, zi, nullptr, w, kOutAminus, false);
+        __syncthreads();
+        bpe += 4.0 + 8.0 + 8.0 + 4.0 + 8.0;
+        const double hn = arnoldi_orth<double>(Vo, ldv, i, n, h, h2, hf64, red, outb, bpe);
+        if (threadIdx.x == 0) givens_step(Ho, kout + 1, cso, sno, go, i, h, h2, hn, s_val);
+        __syncthreads();
+        const double est = s_val[0], den = s_val[1];
+        idone = i + 1;
+        if (den == 0.0) { idone = i; break; }
+        if (!(hn > 1e-300 * rn)) break;
+        if (!(est == est) || est <= 0.3 * p.tol * bn) break;
+      }
+      outer_total += idone;
+      // ---- x += Z y ----------------------------------------------------------
+      tri_solve(Ho, kout + 1, go, idone, ybuf);
+      for (int64_t k = threadIdx.x; k < n; k += blockDim.x) {
+        double acc = x[k];
+        for (int i = 0; i < idone; ++i) acc = fma(ybuf[i], (double)Z[(int64_t)i * ldv + k], acc);
+        x[k] = acc;
+      }
+      __syncthreads();
+      bpe += 4.0 * idone + 16.0;
+      if (idone == 0) { status = kBreakdown; break; }
+    }
+    if (threadIdx.x == 0) {
+      p.out.outer[inst] = outer_total;
+      p.out.inner[inst] = inner_total;
+      p.out.status[inst] = status;
+      p.out.relres[inst] = relres;
+      p.out.bytes[inst] = bpe * (double)n;
+    }
+    __syncthreads();
+  }
+}
+
 int launch_solve(rt_handle *h, const double *b, double *x, double tol, double tol_inner, int m,
-                 int max_outer, int use_x0, cudaStream_t s) {
+                 int max_outer, int use_x0, cudaStream_t s, int m_in) {
   SolveParams p;
   p.cm = Common{h->d_cols, h->d_dir_cls, h->d_dir_up, h->d_tsrc, h->d_Itop, h->d_Ibot};
   p.t64 = Tables<double>{h->E64, h->A64, h->B64, h->Uw64, h->Ul64, h->Rw64, h->Psi64, h->gam64};
@@ -455,7 +699,8 @@ int launch_solve(rt_handle *h, const double *b, double *x, double tol, double to
   p.max_outer = max_outer;
   p.use_x0 = use_x0;
   p.V = h->ws.V;
-  p.cap = h->ws.cap_bytes / (h->precision == 0 ? 8 : 4);
+  p.cap = h->precision == 0 ? h->ws.cap_bytes / 8 : h->ws.cap_bytes;
+  p.m_in = m_in;
   p.S = h->ws.S;
   p.ld = h->ws.ld;
   p.H = h->ws.H;
@@ -465,7 +710,7 @@ int launch_solve(rt_handle *h, const double *b, double *x, double tol, double to
   cudaError_t e = cudaMemsetAsync(h->d_queue + 1, 0, sizeof(int), s);
   if (e != cudaSuccess) return (int)e;
   if (h->precision == 0) k_solve<double><<<h->ws.slots, kNT, 0, s>>>(p);
-  else k_solve<float><<<h->ws.slots, kNT, 0, s>>>(p);
+  else k_solve_nested<<<h->ws.slots, kNT, 0, s>>>(p);
   return (int)cudaGetLastError();
 }
 

@@ -1,0 +1,303 @@
+// rt_grid.cu -- Krylov building blocks spread over the whole GPU, for single
+// problems too large for one CTA (3D boxes).  The solve loop runs on the host
+// (float64 Givens rotations and least squares there); each Arnoldi step is a
+// few grid-wide kernels: operator, projections (per-CTA partial sums reduced
+// by one CTA), fused update + normalisation.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <vector>
+
+#include "rt_host.h"
+#include "rt_internal.cuh"
+
+namespace rt {
+
+constexpr int kGT = 256;     // threads per CTA
+constexpr int kGDots = 8;    // basis vectors per pass of the projection kernel
+
+int grid_ctas(const rt_handle *h) { return 2 * (h->n_sm > 0 ? h->n_sm : 152); }
+
+// partial[blockIdx][u] = sum over this CTA's elements of V_{i0+u} . w  (u < cnt),
+// partial[blockIdx][kGDots] = w . w (when with_norm)
+template <typename TL>
+__global__ void __launch_bounds__(kGT) k_gdots(const TL *V, int64_t ldv, int i0, int cnt, const TL *w,
+                                               int64_t n, int with_norm, double *partial) {
+  __shared__ double red[(kGT / 32) * (kGDots + 1)];
+  __shared__ double outb[kGDots + 1];
+  double acc[kGDots + 1];
+#pragma unroll
+  for (int u = 0; u <= kGDots; ++u) acc[u] = 0.0;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const TL wk = w[k];
+#pragma unroll
+    for (int u = 0; u < kGDots; ++u)
+      if (u < cnt) acc[u] += (double)(V[(int64_t)(i0 + u) * ldv + k] * wk);
+    if (with_norm) acc[kGDots] += (double)(wk * wk);
+  }
+  block_sum<kGDots + 1>(acc, red, outb);
+  if (threadIdx.x <= kGDots) partial[(int64_t)blockIdx.x * (kGDots + 1) + threadIdx.x] = acc[threadIdx.x];
+}
+
+__global__ void k_greduce(const double *partial, int nblk, int nv, double *out) {
+  for (int u = threadIdx.x; u < nv; u += blockDim.x) {
+    double s = 0.0;
+    for (int b = 0; b < nblk; ++b) s += partial[(int64_t)b * nv + u];
+    out[u] = s;
+  }
+}
+
+// w = (w - sum_{i<cnt} coef[i] V_i) * scale; optional squared norm partials
+template <typename TL>
+__global__ void __launch_bounds__(kGT) k_gupdate(const TL *V, int64_t ldv, int cnt, const double *coef,
+                                                 TL *w, int64_t n, double scale, double *partial) {
+  __shared__ TL cf[1024];
+  __shared__ double red[kGT / 32];
+  __shared__ double outb[1];
+  for (int i = threadIdx.x; i < cnt; i += blockDim.x) cf[i] = (TL)coef[i];
+  __syncthreads();
+  const TL sc = (TL)scale;
+  double a[1] = {0.0};
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    TL wk = w[k];
+    for (int i = 0; i < cnt; ++i) wk = fma(-cf[i], V[(int64_t)i * ldv + k], wk);
+    wk *= sc;
+    w[k] = wk;
+    a[0] += (double)(wk * wk);
+  }
+  if (partial) {
+    block_sum<1>(a, red, outb);
+    if (threadIdx.x == 0) partial[blockIdx.x] = a[0];
+  }
+}
+
+// x += sum_{i<cnt} y[i] V_i  (correction summed in TL, added in float64)
+template <typename TL>
+__global__ void __launch_bounds__(kGT) k_gxupdate(const TL *V, int64_t ldv, int cnt, const double *y,
+                                                  double *x, int64_t n) {
+  __shared__ TL cf[1024];
+  for (int i = threadIdx.x; i < cnt; i += blockDim.x) cf[i] = (TL)y[i];
+  __syncthreads();
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    TL d = 0;
+    for (int i = 0; i < cnt; ++i) d = fma(cf[i], V[(int64_t)i * ldv + k], d);
+    x[k] += (double)d;
+  }
+}
+
+// r = b - y (in place in y) and squared-norm partials
+__global__ void __launch_bounds__(kGT) k_gresid(const double *b, double *y, int64_t n, double *partial) {
+  __shared__ double red[kGT / 32];
+  __shared__ double outb[1];
+  double a[1] = {0.0};
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const double r = b[k] - y[k];
+    y[k] = r;
+    a[0] += r * r;
+  }
+  block_sum<1>(a, red, outb);
+  if (threadIdx.x == 0) partial[blockIdx.x] = a[0];
+}
+
+template <typename TL>
+__global__ void k_gscale(const double *src, TL *dst, int64_t n, double s) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+    dst[k] = (TL)(src[k] * s);
+}
+
+__global__ void k_gnorm(const double *v, int64_t n, double *partial) {
+  __shared__ double red[kGT / 32];
+  __shared__ double outb[1];
+  double a[1] = {0.0};
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+    a[0] += v[k] * v[k];
+  block_sum<1>(a, red, outb);
+  if (threadIdx.x == 0) partial[blockIdx.x] = a[0];
+}
+
+// ------------------------------------------------------------ host loop
+struct GridCtx {
+  rt_handle *h;
+  cudaStream_t s;
+  int G;
+  double *part, *red, *coef;
+  std::vector<double> host;
+};
+
+static int reduce_to_host(GridCtx &g, int nv, double *dst) {
+  k_greduce<<<1, 64, 0, g.s>>>(g.part, g.G, nv, g.red);
+  cudaError_t e = cudaMemcpyAsync(dst, g.red, nv * sizeof(double), cudaMemcpyDeviceToHost, g.s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(g.s);
+  return (int)e;
+}
+
+template <typename TL>
+static int dots(GridCtx &g, const TL *V, int64_t ldv, int j, const TL *w, int64_t n, std::vector<double> &h,
+                double *ww) {
+  h.assign(j + 1, 0.0);
+  for (int i0 = 0; i0 <= j; i0 += kGDots) {
+    const int cnt = std::min(kGDots, j + 1 - i0);
+    k_gdots<TL><<<g.G, kGT, 0, g.s>>>(V, ldv, i0, cnt, w, n, i0 == 0 ? 1 : 0, g.part);
+    double out[kGDots + 1];
+    int e = reduce_to_host(g, kGDots + 1, out);
+    if (e) return e;
+    for (int u = 0; u < cnt; ++u) h[i0 + u] = out[u];
+    if (i0 == 0 && ww) *ww = out[kGDots];
+  }
+  return 0;
+}
+
+template <typename TL>
+static int update(GridCtx &g, const TL *V, int64_t ldv, const std::vector<double> &c, TL *w, int64_t n,
+                  double scale, double *nrm2) {
+  if (!c.empty()) {
+    cudaError_t e = cudaMemcpyAsync(g.coef, c.data(), c.size() * sizeof(double), cudaMemcpyHostToDevice, g.s);
+    if (e) return (int)e;
+  }
+  k_gupdate<TL><<<g.G, kGT, 0, g.s>>>(V, ldv, (int)c.size(), g.coef, w, n, scale, nrm2 ? g.part : nullptr);
+  if (nrm2) {
+    double v;
+    int r = reduce_to_host(g, 1, &v);
+    *nrm2 = v;
+    return r;
+  }
+  return (int)cudaGetLastError();
+}
+
+// Restarted GMRES(m) with float64 refinement for one big problem (n_rhs == 1).
+// apply64(x, y) writes y = A x in float64; applyL(v, w) writes w = A v in TL.
+template <typename TL, typename F64, typename FL>
+static int grid_solve(rt_handle *h, const double *b, double *x, double tol, double tol_inner, int m,
+                      int max_outer, int use_x0, cudaStream_t s, F64 apply64, FL applyL, int &outer_out,
+                      int &inner_out, double &relres_out, int &status, double &bytes) {
+  const int64_t n = h->E;
+  const int64_t ldv = (n + 31) / 32 * 32;
+  const bool mixed = sizeof(TL) == 4;
+  GridCtx g{h, s, grid_ctas(h), h->g_part, h->g_red, h->g_coef, {}};
+  TL *V = static_cast<TL *>(h->ws.V);
+  double *r = h->g_r;  // float64 residual
+  const double sz = sizeof(TL);
+  bytes = 0.0;
+  k_gnorm<<<g.G, kGT, 0, s>>>(b, n, g.part);
+  double bn2;
+  int e = reduce_to_host(g, 1, &bn2);
+  if (e) return e;
+  const double bn = std::sqrt(bn2);
+  bytes += 8.0 * n;
+  status = 4;
+  relres_out = 1.0;
+  outer_out = 0;
+  inner_out = 0;
+  if (!std::isfinite(bn)) { status = 6; return 0; }
+  if (!use_x0) cudaMemsetAsync(x, 0, n * sizeof(double), s);
+  if (bn == 0.0) { status = 0; relres_out = 0.0; return 0; }
+  std::vector<double> H((size_t)(m + 1) * m), cs(m + 1), sn(m + 1), gv(m + 2), hv, h2;
+  for (int outer = 0;; ++outer) {
+    outer_out = outer;
+    double rn;
+    const double *rsrc;
+    if (outer == 0 && !use_x0) {
+      rsrc = b;
+      rn = bn;
+    } else {
+      if ((e = apply64(x, r))) return e;
+      k_gresid<<<g.G, kGT, 0, s>>>(b, r, n, g.part);
+      double rn2;
+      if ((e = reduce_to_host(g, 1, &rn2))) return e;
+      rn = std::sqrt(rn2);
+      rsrc = r;
+      bytes += (40.0 + 24.0) * n;
+    }
+    relres_out = rn / bn;
+    if (!std::isfinite(rn)) { status = 6; return 0; }
+    if (relres_out <= tol) { status = 0; return 0; }
+    if (outer >= max_outer) { status = 4; return 0; }
+    k_gscale<TL><<<g.G, kGT, 0, s>>>(rsrc, V, n, 1.0 / rn);
+    bytes += (8.0 + sz) * n;
+    gv.assign(m + 2, 0.0);
+    gv[0] = rn;
+    const double target = mixed ? std::max(tol_inner * rn, 0.5 * tol * bn) : 0.5 * tol * bn;
+    int jdone = 0;
+    for (int j = 0; j < m; ++j) {
+      TL *vj = V + (int64_t)j * ldv;
+      TL *w = V + (int64_t)(j + 1) * ldv;
+      if ((e = applyL(vj, w))) return e;
+      double ww = 0.0;
+      if ((e = dots<TL>(g, V, ldv, j, w, n, hv, &ww))) return e;
+      bytes += (5.0 * sz + sz * (j + 2)) * n;
+      double hh = 0.0;
+      for (double v : hv) hh += v * v;
+      double hn;
+      h2.assign(j + 1, 0.0);
+      if (ww - hh > 0.5 * ww) {
+        hn = std::sqrt(ww - hh);
+        if ((e = update<TL>(g, V, ldv, hv, w, n, hn > 0 ? 1.0 / hn : 0.0, nullptr))) return e;
+        bytes += sz * (j + 3) * n;
+      } else {
+        if ((e = update<TL>(g, V, ldv, hv, w, n, 1.0, nullptr))) return e;
+        if ((e = dots<TL>(g, V, ldv, j, w, n, h2, nullptr))) return e;
+        double n2;
+        if ((e = update<TL>(g, V, ldv, h2, w, n, 1.0, &n2))) return e;
+        hn = std::sqrt(n2);
+        std::vector<double> zero;
+        if ((e = update<TL>(g, V, ldv, zero, w, n, hn > 0 ? 1.0 / hn : 0.0, nullptr))) return e;
+        bytes += sz * (4.0 * j + 12.0) * n;
+      }
+      double *col = H.data() + (size_t)j * (m + 1);
+      for (int i = 0; i <= j; ++i) col[i] = hv[i] + h2[i];
+      col[j + 1] = hn;
+      for (int i = 0; i < j; ++i) {
+        const double t0 = cs[i] * col[i] + sn[i] * col[i + 1];
+        col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
+        col[i] = t0;
+      }
+      const double den = std::hypot(col[j], col[j + 1]);
+      double cj = 1.0, sj = 0.0;
+      if (den > 0.0) { cj = col[j] / den; sj = col[j + 1] / den; }
+      cs[j] = cj;
+      sn[j] = sj;
+      col[j] = den;
+      col[j + 1] = 0.0;
+      gv[j + 1] = -sj * gv[j];
+      gv[j] = cj * gv[j];
+      jdone = j + 1;
+      if (den == 0.0) { jdone = j; break; }
+      if (!(hn > 1e-300 * rn)) break;
+      if (std::fabs(gv[j + 1]) <= target) break;
+    }
+    inner_out += jdone;
+    std::vector<double> yv(jdone);
+    for (int i = jdone - 1; i >= 0; --i) {
+      double acc = gv[i];
+      for (int k = i + 1; k < jdone; ++k) acc -= H[(size_t)k * (m + 1) + i] * yv[k];
+      yv[i] = acc / H[(size_t)i * (m + 1) + i];
+    }
+    if (jdone > 0) {
+      cudaMemcpyAsync(g.coef, yv.data(), jdone * sizeof(double), cudaMemcpyHostToDevice, s);
+      k_gxupdate<TL><<<g.G, kGT, 0, s>>>(V, ldv, jdone, g.coef, x, n);
+      bytes += (sz * jdone + 16.0) * n;
+    }
+    if ((e = (int)cudaGetLastError())) return e;
+    if (jdone == 0) { status = 5; return 0; }
+  }
+}
+
+int launch_grid_solve(rt_handle *h, const double *b, double *x, double tol, double tol_inner, int m,
+                      int max_outer, int use_x0, cudaStream_t s, int &outer, int &inner, double &relres,
+                      int &status, double &bytes) {
+  auto apply64 = [&](const double *xx, double *yy) -> int { return apply_box(h, 0, true, xx, false, yy, false, s); };
+  if (h->precision == 0) {
+    auto applyL = [&](const double *v, double *w) -> int { return apply_box(h, 0, true, v, false, w, false, s); };
+    return grid_solve<double>(h, b, x, tol, tol_inner, m, max_outer, use_x0, s, apply64, applyL, outer, inner,
+                              relres, status, bytes);
+  }
+  auto applyL = [&](const float *v, float *w) -> int { return apply_box(h, 0, false, v, true, w, true, s); };
+  return grid_solve<float>(h, b, x, tol, tol_inner, m, max_outer, use_x0, s, apply64, applyL, outer, inner,
+                           relres, status, bytes);
+}
+
+}  // namespace rt

@@ -26,6 +26,11 @@ struct Workspace {
   double *H = nullptr;     // [slots][hld]
 };
 
+// 3D box geometry (device-side copy of the scalars)
+struct BoxDev {
+  int nx, ny, nz, nd, nn, ie;
+};
+
 }  // namespace rt
 
 struct rt_handle {
@@ -63,6 +68,18 @@ struct rt_handle {
   int64_t *d_tc_off = nullptr;        // per column offset into the bf16 tiles
   uint16_t *d_tc_tiles = nullptr;     // pre-tiled bf16 PsiW
   int *d_err = nullptr;               // device error word (bounded waits)
+  // 3D boxes: geometry, per-direction (sx, sy, ds, up), opacity, grid-solve scratch
+  // CUDA graph of the batched solve (queue reset + persistent kernel), reused
+  // while the call signature (b, x, options) repeats
+  cudaGraphExec_t solve_graph = nullptr;
+  cudaStream_t capture_stream = nullptr;
+  unsigned long long graph_key[8] = {};
+  int graph_replays = 0;
+  rt::BoxDev box{};
+  double *d_geo = nullptr;
+  double *chi64 = nullptr;
+  float *chi32 = nullptr;
+  double *g_part = nullptr, *g_red = nullptr, *g_coef = nullptr, *g_r = nullptr;
   int64_t stage_len = 0;
   bool has_dense = false;
 };
@@ -75,11 +92,19 @@ int launch_coefficients(rt_handle *h, const double *d_z, const int64_t *d_zoff,
 int launch_apply(rt_handle *h, int op, bool fp64, const double *x, double *y, cudaStream_t s,
                  bool first_rhs_only = false);
 int launch_solve(rt_handle *h, const double *b, double *x, double tol, double tol_inner, int m,
-                 int max_outer, int use_x0, cudaStream_t s);
+                 int max_outer, int use_x0, cudaStream_t s, int m_in);
 int solve_block_threads();
 int launch_sigma_dense_tc(rt_handle *h, bool x_is_float, const void *x, float *S, cudaStream_t s);
 struct TcJob;
 int tc_prepare(rt_handle *h, const std::vector<double> &psiwT);
+int launch_sweep3d(rt_handle *h, bool fp64, const void *S, const double *tsrc, const void *x, bool xf,
+                   void *y, bool yf, int out, bool inflow, cudaStream_t s);
+int apply_box(rt_handle *h, int op, bool fp64, const void *x, bool xf, void *y, bool yf, cudaStream_t s);
+int launch_grid_solve(rt_handle *h, const double *b, double *x, double tol, double tol_inner, int m,
+                      int max_outer, int use_x0, cudaStream_t s, int &outer, int &inner, double &relres,
+                      int &status, double &bytes);
+int grid_ctas(const rt_handle *h);
+
 constexpr int kRayBlock = 128;  // rays (threads) per sweep tile
 int max_krylov();
 int apply_slots(rt_handle *h);

@@ -36,7 +36,7 @@ class rt_desc(C.Structure):
 
 class rt_solve_opts(C.Structure):
     _fields_ = [("tol", C.c_double), ("tol_inner", C.c_double), ("restart", C.c_int32),
-                ("max_outer", C.c_int32), ("use_x0", C.c_int32)]
+                ("max_outer", C.c_int32), ("use_x0", C.c_int32), ("inner_restart", C.c_int32)]
 
 
 class rt_info(C.Structure):
@@ -46,8 +46,8 @@ class rt_info(C.Structure):
                 ("inst_inner", C.POINTER(C.c_int32)), ("inst_relres", _dp)]
 
 
-EXPORTS = ("rt_create", "rt_create_batch", "rt_vector_length", "rt_apply", "rt_solve",
-           "rt_destroy", "rt_last_error", "rt_version")
+EXPORTS = ("rt_create", "rt_create_batch", "rt_vector_length", "rt_apply",
+           "rt_solve", "rt_destroy", "rt_last_error", "rt_version")
 
 _lib = None
 
@@ -181,10 +181,10 @@ class Handle:
     def rt_apply(self, op: int, x, y, fp64: bool = False, stream=None):
         _check(load().rt_apply(self._h, op, int(bool(fp64)), _ptr(x), _ptr(y), _stream_ptr(stream)))
 
-    def rt_solve(self, b, x, tol: float = 1e-11, tol_inner: float = 1e-4, restart: Optional[int] = None,
+    def rt_solve(self, b, x, tol: float = 1e-11, tol_inner: float = 0.1, restart: Optional[int] = None,
                  max_outer: int = 50, use_x0: bool = False, stream=None, per_instance: bool = False,
-                 raise_on_noconv: bool = False) -> dict:
-        o = rt_solve_opts(tol, tol_inner, restart or self.max_restart, max_outer, int(use_x0))
+                 raise_on_noconv: bool = False, inner_restart: int = 0) -> dict:
+        o = rt_solve_opts(tol, tol_inner, restart or self.max_restart, max_outer, int(use_x0), inner_restart)
         info = rt_info()
         n_inst = len(self.problems) * self.n_rhs
         arrs = None

@@ -244,3 +244,22 @@ def test_iteration_count_reported_and_noconv(rt):
     x = torch.zeros(p.n, dtype=torch.float64, device="cuda:0")
     info = h.rt_solve(dev(O.rhs(p)), x, tol=1e-12, restart=4, max_outer=2)
     assert info["status"] == rt.RT_ERR_NOCONV and info["max_outer"] == 2 and info["max_inner"] == 8
+
+
+def test_repeated_solve_replays_identically(rt):
+    """The batched solve is captured once into a CUDA graph and replayed while
+    its arguments repeat; a replay must reproduce the first solve bit for bit,
+    and changing an option must re-capture."""
+    probs = [small_problems()[k] for k in ("crd", "r2_ragged")]
+    h = rt.Handle(probs, n_rhs=2, precision=rt.RT_P_MIXED, max_restart=32)
+    b = torch.tensor(np.concatenate([O.rhs_batch(probs)] * 2), device="cuda:0")
+    x = torch.zeros_like(b)
+    outs = []
+    for tol in (1e-12, 1e-12, 1e-13):
+        x.zero_()
+        info = h.rt_solve(b, x, tol=tol, tol_inner=0.1, max_outer=40)
+        torch.cuda.synchronize()
+        assert info["status"] == 0
+        outs.append(x.cpu().numpy().copy())
+    assert np.array_equal(outs[0], outs[1])
+    assert np.linalg.norm(outs[2] - outs[0]) <= 1e-10 * np.linalg.norm(outs[0])
