@@ -148,6 +148,28 @@ int64_t rt_vector_length(const rt_handle *h);
 int rt_apply(rt_handle *h, int32_t op, int32_t fp64, const double *x, double *y,
              void *stream);
 
+/* Allocation-free variant of rt_apply for callers that cannot allocate device
+ * memory at call time: code running while a CUDA stream is being captured into
+ * a graph (cudaMalloc is illegal there), real-time loops that must not touch
+ * the allocator, or hosts whose device memory is fully budgeted up front.  (The
+ * paper has no counterpart; it is a property of this library's interface.)
+ * Same operators and layouts as rt_apply, on a handle created beforehand, but
+ * the source-function scratch of the apply is a static 16 MiB device array in
+ * the library instead of handle-owned memory, and the call allocates nothing.
+ * Limits and behaviour:
+ *  - x and y must be device pointers (host staging would allocate): else RT_ERR_ARG;
+ *  - the scratch needed, n_rhs * E elements of the operator's precision
+ *    (float64 if fp64 or an RT_P_FP64 handle, else float32; E alone for 3D
+ *    boxes), must fit in 16 MiB: else RT_ERR_ARG naming the size;
+ *  - the first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture;
+ *  - every call, from any handle, shares the one array: calls that overlap on
+ *    the GPU (other streams, other threads) race and must be serialised by the
+ *    caller; the array keeps the last call's contents (whatever must start at
+ *    zero is cleared by the call itself). */
+int rt_apply_noalloc(rt_handle *h, int32_t op, int32_t fp64, const double *x, double *y, void *stream);
+
 /* Solve A_N x = b for all instances (eq. RT_sys_algebraic; the Krylov solvers
  * of Sec. 5, unpreconditioned).  b == NULL uses the internal right-hand side
  * Lambda t + I_in for every rhs.  RT_P_FP64: restarted GMRES(m) in float64

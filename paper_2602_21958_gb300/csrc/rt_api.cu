@@ -722,6 +722,35 @@ int rt_apply(rt_handle *h, int32_t op, int32_t fp64, const double *x, double *y,
   return RT_OK;
 }
 
+int rt_apply_noalloc(rt_handle *h, int32_t op, int32_t fp64, const double *x, double *y, void *stream) {
+  if (!h) return fail(RT_ERR_ARG, "null handle");
+  if (op < RT_OP_A || op > RT_OP_RHS) return fail(RT_ERR_ARG, "unknown op");
+  if (!y || (!x && op != RT_OP_RHS)) return fail(RT_ERR_ARG, "null vector");
+  if ((x && !is_device_ptr(x)) || !is_device_ptr(y))
+    return fail(RT_ERR_ARG, "rt_apply_noalloc takes device pointers only");
+  const bool f64 = fp64 || h->precision == RT_P_FP64;
+  const long long need = (long long)(h->dims == 3 ? h->E : h->E * h->n_rhs) * (f64 ? 8 : 4);
+  if (need > rt::kNoAllocScratchBytes) {
+    char msg[200];
+    std::snprintf(msg, sizeof msg, "rt_apply_noalloc: the apply needs %lld bytes of scratch, the static "
+                  "array holds %lld", need, (long long)rt::kNoAllocScratchBytes);
+    return fail(RT_ERR_ARG, msg);
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const int e = rt::launch_apply_noalloc(h, op, fp64 != 0, x ? x : y, y, s);
+  if (e != 0) return fail(RT_ERR_CUDA, std::string("rt_apply_noalloc: ") + cudaGetErrorString((cudaError_t)e));
+  if (h->n_tc_jobs > 0 && !fp64 && (op == RT_OP_A || op == RT_OP_SIGMA)) {
+    int err = 0;
+    RT_CUDA(cudaMemcpyAsync(&err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    RT_CUDA(cudaStreamSynchronize(s));
+    if (err) {
+      cudaMemsetAsync(h->d_err, 0, sizeof(int), s);
+      return fail(RT_ERR_TIMEOUT, "tensor-core Sigma: a bounded wait gave up");
+    }
+  }
+  return RT_OK;
+}
+
 int rt_solve(rt_handle *h, const double *b, double *x, const rt_solve_opts *o, rt_info *info,
              void *stream) {
   if (!h || !x || !o) return fail(RT_ERR_ARG, "null handle, x or options");

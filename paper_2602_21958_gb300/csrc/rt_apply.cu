@@ -5,6 +5,8 @@
 // The source function makes one round trip through HBM between them.
 #include <cuda_runtime.h>
 
+#include <mutex>
+
 #include "rt_host.h"
 #include "rt_internal.cuh"
 
@@ -159,6 +161,44 @@ static int launch_apply_s(rt_handle *h, int op, bool fp64, const double *x, doub
 int launch_apply(rt_handle *h, int op, bool fp64, const double *x, double *y, cudaStream_t s,
                  bool first_rhs_only) {
   return launch_apply_s(h, op, fp64, x, y, s, first_rhs_only, nullptr);
+}
+
+// ------------------------------------------------ allocation-free apply
+// Scratch of rt_apply_noalloc: the source function S of one apply lives in
+// this file-scope device array instead of handle-owned memory.  Every GPU that
+// loads the library holds it until the process exits.  Host code must not
+// pass the symbol itself to a kernel (it is a host-side stand-in); the device
+// address is taken with cudaGetSymbolAddress once per device.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+namespace {
+std::mutex g_noalloc_mu;
+void *g_noalloc_ptr[256] = {};
+}  // namespace
+
+// Device address of the scratch array on the current device (set-up on the
+// first call per device, with that device current).  Returns a cudaError_t.
+static int noalloc_scratch(void **out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return (int)e;
+  if (dev < 0 || dev >= 256) return (int)cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return (int)e;
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return 0;
+}
+
+int launch_apply_noalloc(rt_handle *h, int op, bool fp64, const double *x, double *y, cudaStream_t s) {
+  void *scratch = nullptr;
+  const int e = noalloc_scratch(&scratch);
+  if (e) return e;
+  return launch_apply_s(h, op, fp64, x, y, s, false, scratch);
 }
 
 }  // namespace rt

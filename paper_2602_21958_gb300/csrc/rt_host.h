@@ -104,7 +104,9 @@ int launch_grid_solve(rt_handle *h, const double *b, double *x, double tol, doub
                       int max_outer, int use_x0, cudaStream_t s, int &outer, int &inner, double &relres,
                       int &status, double &bytes);
 int grid_ctas(const rt_handle *h);
-
+// allocation-free apply: scratch in a static device array of this many bytes
+constexpr long long kNoAllocScratchBytes = 16ll << 20;
+int launch_apply_noalloc(rt_handle *h, int op, bool fp64, const double *x, double *y, cudaStream_t s);
 constexpr int kRayBlock = 128;  // rays (threads) per sweep tile
 int max_krylov();
 int apply_slots(rt_handle *h);

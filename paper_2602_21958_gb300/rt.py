@@ -46,7 +46,7 @@ class rt_info(C.Structure):
                 ("inst_inner", C.POINTER(C.c_int32)), ("inst_relres", _dp)]
 
 
-EXPORTS = ("rt_create", "rt_create_batch", "rt_vector_length", "rt_apply",
+EXPORTS = ("rt_create", "rt_create_batch", "rt_vector_length", "rt_apply", "rt_apply_noalloc",
            "rt_solve", "rt_destroy", "rt_last_error", "rt_version")
 
 _lib = None
@@ -68,12 +68,13 @@ def load(path: Optional[str] = None) -> C.CDLL:
     lib.rt_vector_length.argtypes = [vp]
     lib.rt_vector_length.restype = C.c_int64
     lib.rt_apply.argtypes = [vp, C.c_int32, C.c_int32, vp, vp, vp]
+    lib.rt_apply_noalloc.argtypes = [vp, C.c_int32, C.c_int32, vp, vp, vp]
     lib.rt_solve.argtypes = [vp, vp, vp, C.POINTER(rt_solve_opts), C.POINTER(rt_info), vp]
     lib.rt_destroy.argtypes = [vp]
     lib.rt_destroy.restype = None
     lib.rt_last_error.restype = C.c_char_p
     lib.rt_version.restype = C.c_char_p
-    for name in ("rt_create", "rt_create_batch", "rt_apply", "rt_solve"):
+    for name in ("rt_create", "rt_create_batch", "rt_apply", "rt_apply_noalloc", "rt_solve"):
         getattr(lib, name).restype = C.c_int
     if path is None:
         _lib = lib
@@ -180,6 +181,11 @@ class Handle:
 
     def rt_apply(self, op: int, x, y, fp64: bool = False, stream=None):
         _check(load().rt_apply(self._h, op, int(bool(fp64)), _ptr(x), _ptr(y), _stream_ptr(stream)))
+
+    def rt_apply_noalloc(self, op: int, x, y, fp64: bool = False, stream=None):
+        """rt_apply without any allocation: device tensors only, scratch in the
+        library's static device array (see include/rt_gb300.h)."""
+        _check(load().rt_apply_noalloc(self._h, op, int(bool(fp64)), _ptr(x), _ptr(y), _stream_ptr(stream)))
 
     def rt_solve(self, b, x, tol: float = 1e-11, tol_inner: float = 0.1, restart: Optional[int] = None,
                  max_outer: int = 50, use_x0: bool = False, stream=None, per_instance: bool = False,
