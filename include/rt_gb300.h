@@ -148,6 +148,27 @@ int64_t rt_vector_length(const rt_handle *h);
 int rt_apply(rt_handle *h, int32_t op, int32_t fp64, const double *x, double *y,
              void *stream);
 
+/* ---- launch-shape tuning ----------------------------------------------- */
+typedef struct rt_tune_info {
+  int32_t ray_block;     /* rays per sweep tile (threads per CTA): 64, 128 or 256        */
+  int32_t ahead;         /* depth points of loads issued ahead per ray: 4, 8 or 16       */
+  int32_t sigma_points;  /* cap on points per Sigma tile: 4, 8, or 0 (as many as fit)    */
+  int32_t from_cache;    /* 1 if read from the RT_TUNE_CACHE file                       */
+  double ms_best;        /* rt_apply(RT_OP_A) time of the choice                         */
+  double ms_default;     /* time of the default shape (128, 8, 0); 0 if from cache       */
+} rt_tune_info;
+
+/* Pick the launch shapes of the batched apply kernels (the sweep tile width and
+ * its load-ahead depth, the Sigma tile size) by timing rt_apply(RT_OP_A) on
+ * this handle's own problem for the 27 combinations, and keep the fastest on
+ * the handle (every later rt_apply uses it).  When the environment variable
+ * RT_TUNE_CACHE names a file, a previous result for the same problem signature
+ * is read from it (JSON lines) instead of re-timing, unless flags & 1; new
+ * results are appended.  Allocates two temporary vectors.  3D boxes have one
+ * launch shape: the call only reports it.  out may be NULL.  (Implementation
+ * choice; the paper has no counterpart.) */
+int rt_autotune(rt_handle *h, int32_t flags, rt_tune_info *out, void *stream);
+
 /* Allocation-free variant of rt_apply for callers that cannot allocate device
  * memory at call time: code running while a CUDA stream is being captured into
  * a graph (cudaMalloc is illegal there), real-time loops that must not touch

@@ -3,6 +3,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <numeric>
 #include <string>
@@ -113,7 +114,7 @@ void free_handle(rt_handle *h) {
                   h->b_int, h->d_order, h->d_queue, h->ws.V, h->ws.S, h->ws.H,
                   h->so.outer, h->so.inner, h->so.status, h->so.relres, h->so.bytes,
                   h->stage_x, h->stage_y, h->d_sig_tiles, h->d_sw_tiles, h->apply_S,
-                  h->d_tc_jobs, h->d_tc_off, h->d_tc_tiles, h->d_err, h->d_geo,
+                  h->d_tc_jobs, h->d_tc_off, h->d_tc_tiles, h->d_tc_xb, h->d_err, h->d_geo,
                   h->chi64, h->chi32, h->g_part, h->g_red, h->g_coef, h->g_r};
   for (void *p : ptrs)
     if (p) cudaFree(p);
@@ -302,6 +303,42 @@ int alloc_workspace(rt_handle *h, int max_restart) {
   return RT_OK;
 }
 
+// Sigma tiles (instance, first point, points) and sweep tiles (instance, first
+// ray) of a batch, rhs 0 first, longest columns first; replaces the handle's.
+int build_apply_tiles(rt_handle *h, int ray_block, int sigma_pts) {
+  const auto &cols = h->h_cols;
+  const int n_cols = h->n_cols, n_rhs = h->n_rhs;
+  std::vector<int3> sig;
+  std::vector<int2> sw;
+  std::vector<int> by_depth(n_cols);
+  std::iota(by_depth.begin(), by_depth.end(), 0);
+  // longest columns first: their sweeps are the longest sequential chains
+  std::stable_sort(by_depth.begin(), by_depth.end(), [&](int a, int b) { return cols[a].nz > cols[b].nz; });
+  for (int r = 0; r < n_rhs; ++r) {
+    for (int ci : by_depth) {
+      const rt::ColDev &c = cols[ci];
+      const int inst = r * n_cols + ci;
+      const int pb = rt::sigma_points_per_block(c, sigma_pts > 0 ? sigma_pts : 1 << 30);
+      for (int p0 = 0; p0 < c.nz; p0 += pb) sig.push_back(make_int3(inst, p0, std::min(pb, c.nz - p0)));
+      for (int r0 = 0; r0 < c.nr; r0 += ray_block) sw.push_back(make_int2(inst, r0));
+    }
+    if (r == 0) {
+      h->n_sig_tiles_rhs0 = (int)sig.size();
+      h->n_sw_tiles_rhs0 = (int)sw.size();
+    }
+  }
+  if (sig.size() > 0x7fffffff || sw.size() > 0x7fffffff) return fail(RT_ERR_ARG, "batch too large for the apply tiling");
+  if (h->d_sig_tiles) cudaFree(h->d_sig_tiles);
+  if (h->d_sw_tiles) cudaFree(h->d_sw_tiles);
+  h->d_sig_tiles = nullptr;
+  h->d_sw_tiles = nullptr;
+  h->n_sig_tiles = (int)sig.size();
+  h->n_sw_tiles = (int)sw.size();
+  int rc = dev_upload(&h->d_sig_tiles, sig);
+  if (rc == RT_OK) rc = dev_upload(&h->d_sw_tiles, sw);
+  return rc;
+}
+
 int create_columns(const rt_desc *descs, int n_cols, int n_rhs, int precision, int max_restart,
                    rt_handle **out) {
   if (!out) return fail(RT_ERR_ARG, "out is null");
@@ -468,41 +505,14 @@ int create_columns(const rt_desc *descs, int n_cols, int n_rhs, int precision, i
     return rc;
   }
   // apply tiles (rhs 0 first) and the source-function scratch of rt_apply
-  {
-    std::vector<int3> sig;
-    std::vector<int2> sw;
-    // longest columns first: their sweeps are the longest sequential chains
-    std::vector<int> by_depth(n_cols);
-    std::iota(by_depth.begin(), by_depth.end(), 0);
-    std::stable_sort(by_depth.begin(), by_depth.end(), [&](int a, int b) { return cols[a].nz > cols[b].nz; });
-    for (int r = 0; r < n_rhs; ++r) {
-      for (int ci : by_depth) {
-        const rt::ColDev &c = cols[ci];
-        const int inst = r * n_cols + ci;
-        const int pb = rt::sigma_points_per_block(c);
-        for (int p0 = 0; p0 < c.nz; p0 += pb) sig.push_back(make_int3(inst, p0, std::min(pb, c.nz - p0)));
-        for (int r0 = 0; r0 < c.nr; r0 += rt::kRayBlock) sw.push_back(make_int2(inst, r0));
-      }
-      if (r == 0) {
-        h->n_sig_tiles_rhs0 = (int)sig.size();
-        h->n_sw_tiles_rhs0 = (int)sw.size();
-      }
-    }
-    if (sig.size() > 0x7fffffff || sw.size() > 0x7fffffff) {
-      free_handle(h);
-      return fail(RT_ERR_ARG, "batch too large for the apply tiling");
-    }
-    h->n_sig_tiles = (int)sig.size();
-    h->n_sw_tiles = (int)sw.size();
-    if ((rc = dev_upload(&h->d_sig_tiles, sig)) != RT_OK || (rc = dev_upload(&h->d_sw_tiles, sw)) != RT_OK) {
-      free_handle(h);
-      return rc;
-    }
-    ce = cudaMalloc(&h->apply_S, (size_t)h->E * n_rhs * sizeof(double));
-    if (ce != cudaSuccess) {
-      free_handle(h);
-      return fail(RT_ERR_OOM, "apply scratch allocation failed");
-    }
+  if ((rc = build_apply_tiles(h, h->tune.ray_block, h->tune.sigma_pts)) != RT_OK) {
+    free_handle(h);
+    return rc;
+  }
+  ce = cudaMalloc(&h->apply_S, (size_t)h->E * n_rhs * sizeof(double));
+  if (ce != cudaSuccess) {
+    free_handle(h);
+    return fail(RT_ERR_OOM, "apply scratch allocation failed");
   }
   ce = cudaMalloc(&h->b_int, (size_t)h->E * sizeof(double));
   if (ce == cudaSuccess) ce = (cudaError_t)rt::launch_apply(h, RT_OP_RHS, true, h->b_int, h->b_int, 0, true);
@@ -533,6 +543,7 @@ int create_box(const rt_desc *d, int n_rhs, int precision, int max_restart, rt_h
   const int64_t npts = (int64_t)d->nx * d->ny * d->nz;
   const int64_t plane = (int64_t)d->nx * d->ny;
   if (plane * 32 > 200 * 1024) return fail(RT_ERR_ARG, "box: a z-plane must fit in shared memory (nx*ny <= 6400)");
+  if (plane * 8 > 32 * 1024) return fail(RT_ERR_ARG, "box: nx*ny must be at most 4096 (32 values per thread)");
   for (int k = 0; k < d->n_dir; ++k)
     if (!(std::fabs(d->dir[3 * k + 2]) > 0.0)) return fail(RT_ERR_ARG, "box: direction with Omega_z = 0");
   const size_t np = (size_t)npts * d->n_nu;
@@ -558,14 +569,20 @@ int create_box(const rt_desc *d, int n_rhs, int precision, int max_restart, rt_h
   h->E = npts * c.nr;
   h->nmax = h->E;
   h->box = rt::BoxDev{d->nx, d->ny, d->nz, d->n_dir, d->n_nu, d->formal_solver == RT_FS_IE ? 1 : 0};
-  std::vector<double> geo(4 * (size_t)d->n_dir);
+  // per direction: integer upwind shift reduced modulo the periodic plane,
+  // its fractional part, the path length between planes, the sweep sense
+  std::vector<double> geo(6 * (size_t)d->n_dir);
   for (int k = 0; k < d->n_dir; ++k) {
     const double ox = d->dir[3 * k], oy = d->dir[3 * k + 1], oz = d->dir[3 * k + 2];
     const double ds = d->z[2] / std::fabs(oz);
-    geo[4 * k + 0] = ox * ds / d->z[0];
-    geo[4 * k + 1] = oy * ds / d->z[1];
-    geo[4 * k + 2] = ds;
-    geo[4 * k + 3] = oz > 0 ? 1.0 : 0.0;
+    const double sx = ox * ds / d->z[0], sy = oy * ds / d->z[1];
+    const double fx = std::floor(sx), fy = std::floor(sy);
+    geo[6 * k + 0] = (double)((((long long)fx % d->nx) + d->nx) % d->nx);
+    geo[6 * k + 1] = (double)((((long long)fy % d->ny) + d->ny) % d->ny);
+    geo[6 * k + 2] = sx - fx;
+    geo[6 * k + 3] = sy - fy;
+    geo[6 * k + 4] = ds;
+    geo[6 * k + 5] = oz > 0 ? 1.0 : 0.0;
   }
   std::vector<double> chi(d->chi, d->chi + np), gam(d->gamma, d->gamma + np), itop, ibot, tsrc;
   for (int f = 0; f < d->n_nu; ++f) {
@@ -748,6 +765,120 @@ int rt_apply_noalloc(rt_handle *h, int32_t op, int32_t fp64, const double *x, do
       return fail(RT_ERR_TIMEOUT, "tensor-core Sigma: a bounded wait gave up");
     }
   }
+  return RT_OK;
+}
+
+int rt_autotune(rt_handle *h, int32_t flags, rt_tune_info *out, void *stream) {
+  if (!h) return fail(RT_ERR_ARG, "null handle");
+  cudaStream_t s = (cudaStream_t)stream;
+  char sig[256];
+  int nzmax = 0, nrmax = 0;
+  for (const rt::ColDev &c : h->h_cols) {
+    nzmax = std::max(nzmax, c.nz);
+    nrmax = std::max(nrmax, c.nr);
+  }
+  std::snprintf(sig, sizeof sig, "dims=%d cols=%d rhs=%d E=%lld nzmax=%d nrmax=%d prec=%d", h->dims, h->n_cols,
+                h->n_rhs, (long long)h->E, nzmax, nrmax, h->precision);
+  rt_tune_info loc{};
+  loc.ray_block = h->tune.ray_block;
+  loc.ahead = h->tune.ahead;
+  loc.sigma_points = h->tune.sigma_pts;
+  if (h->dims == 3) {  // the plane sweep has a single launch shape per box
+    if (out) *out = loc;
+    return RT_OK;
+  }
+  const char *path = std::getenv("RT_TUNE_CACHE");
+  if (path && !(flags & 1)) {
+    if (FILE *f = std::fopen(path, "r")) {
+      char line[512];
+      while (std::fgets(line, sizeof line, f)) {
+        int rb = 0, ah = 0, pts = 0;
+        double ms = 0;
+        const char *q = std::strstr(line, "\"sig\": \"");
+        if (!q || std::strncmp(q + 8, sig, std::strlen(sig)) != 0 || q[8 + std::strlen(sig)] != '"') continue;
+        const char *r = std::strstr(line, "\"ray_block\":");
+        if (r && std::sscanf(r, "\"ray_block\": %d, \"ahead\": %d, \"sigma_points\": %d, \"ms\": %lf", &rb, &ah,
+                             &pts, &ms) == 4) {
+          h->tune.ray_block = rb;
+          h->tune.ahead = ah;
+          h->tune.sigma_pts = pts;
+          h->tune.ms = ms;
+          h->tune.from_cache = 1;
+        }
+      }
+      std::fclose(f);
+      if (h->tune.from_cache) {
+        const int rc = build_apply_tiles(h, h->tune.ray_block, h->tune.sigma_pts);
+        loc.ray_block = h->tune.ray_block;
+        loc.ahead = h->tune.ahead;
+        loc.sigma_points = h->tune.sigma_pts;
+        loc.ms_best = h->tune.ms;
+        loc.from_cache = 1;
+        if (out) *out = loc;
+        return rc;
+      }
+    }
+  }
+  const int64_t len = h->E * h->n_rhs;
+  double *x = nullptr, *y = nullptr;
+  RT_CUDA(cudaMalloc(&x, len * sizeof(double)));
+  cudaError_t ce = cudaMalloc(&y, len * sizeof(double));
+  if (ce != cudaSuccess) {
+    cudaFree(x);
+    return fail(RT_ERR_OOM, "autotune buffers");
+  }
+  cudaMemsetAsync(x, 0, len * sizeof(double), s);
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  double best = 1e300, first = 0;
+  rt::Tune best_t = h->tune;
+  const int rbs[3] = {64, 128, 256}, ahs[3] = {4, 8, 16}, pts[3] = {4, 8, 0};
+  int rc = RT_OK;
+  for (int a = 0; a < 3 && rc == RT_OK; ++a)
+    for (int b = 0; b < 3 && rc == RT_OK; ++b)
+      for (int c = 0; c < 3 && rc == RT_OK; ++c) {
+        h->tune.ray_block = rbs[a];
+        h->tune.ahead = ahs[b];
+        h->tune.sigma_pts = pts[c];
+        if ((rc = build_apply_tiles(h, rbs[a], pts[c])) != RT_OK) break;
+        rt::launch_apply(h, RT_OP_A, false, x, y, s);
+        cudaEventRecord(e0, s);
+        for (int k = 0; k < 3; ++k) rt::launch_apply(h, RT_OP_A, false, x, y, s);
+        cudaEventRecord(e1, s);
+        if (cudaEventSynchronize(e1) != cudaSuccess) { rc = fail(RT_ERR_CUDA, "autotune launch"); break; }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        const double t = ms / 3.0;
+        if (rbs[a] == 128 && ahs[b] == 8 && pts[c] == 0) first = t;
+        if (t < best) {
+          best = t;
+          best_t = h->tune;
+        }
+      }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(x);
+  cudaFree(y);
+  if (rc != RT_OK) return rc;
+  h->tune = best_t;
+  h->tune.ms = best;
+  h->tune.from_cache = 0;
+  if ((rc = build_apply_tiles(h, best_t.ray_block, best_t.sigma_pts)) != RT_OK) return rc;
+  if (path) {
+    if (FILE *f = std::fopen(path, "a")) {
+      std::fprintf(f, "{\"sig\": \"%s\", \"ray_block\": %d, \"ahead\": %d, \"sigma_points\": %d, \"ms\": %.6f}\n",
+                   sig, best_t.ray_block, best_t.ahead, best_t.sigma_pts, best);
+      std::fclose(f);
+    }
+  }
+  loc.ray_block = best_t.ray_block;
+  loc.ahead = best_t.ahead;
+  loc.sigma_points = best_t.sigma_pts;
+  loc.ms_best = best;
+  loc.ms_default = first;
+  loc.from_cache = 0;
+  if (out) *out = loc;
   return RT_OK;
 }
 

@@ -29,12 +29,13 @@ __global__ void __launch_bounds__(kSigNT) k_sigma_tiles(Common cm, Tables<T> tb,
 }
 
 // out: kOutAminus (y = x - Lambda S), kOutI (y = Lambda S, or Lambda t + I_in
-// when tsrc is set and inflow is on)
-template <typename T>
-__global__ void __launch_bounds__(kRayBlock) k_sweep_tiles(Common cm, Tables<T> tb, const int2 *tiles,
-                                                           int n_cols, int64_t E, const T *S,
-                                                           const double *x, double *y, int out,
-                                                           int use_tsrc, int inflow) {
+// when tsrc is set and inflow is on).  RB rays per tile (threads), AH depth
+// points of loads issued ahead (both picked by rt_autotune).
+template <typename T, int RB, int AH>
+__global__ void __launch_bounds__(RB) k_sweep_tiles(Common cm, Tables<T> tb, const int2 *tiles,
+                                                    int n_cols, int64_t E, const T *S,
+                                                    const double *x, double *y, int out,
+                                                    int use_tsrc, int inflow) {
   const int2 t = tiles[blockIdx.x];
   const int ci = t.x % n_cols, rhs = t.x / n_cols;
   const ColDev c = cm.cols[ci];
@@ -42,8 +43,8 @@ __global__ void __launch_bounds__(kRayBlock) k_sweep_tiles(Common cm, Tables<T> 
   if (r >= c.nr) return;
   const int64_t base = rhs * E + c.x_off;
   const double *ts = use_tsrc ? cm.tsrc + c.g_off : nullptr;
-  sweep_ray<T, double, double, 8>(c, tb, cm, S ? S + base : nullptr, ts, x ? x + base : nullptr, nullptr,
-                                  y + base, out, inflow != 0, r);
+  sweep_ray<T, double, double, AH>(c, tb, cm, S ? S + base : nullptr, ts, x ? x + base : nullptr, nullptr,
+                                   y + base, out, inflow != 0, r);
 }
 
 template <typename T>
@@ -58,6 +59,24 @@ __global__ void k_widen(const T *a, double *b, int64_t n) {
     b[i] = (double)a[i];
 }
 
+// sweep launch with the handle's tuned (ray block, loads ahead)
+template <typename T>
+static void sweep_launch(rt_handle *h, int nsw, const Common &cm, const Tables<T> &tb, const T *S,
+                         const double *x, double *y, int out, int use_tsrc, int inflow, cudaStream_t s) {
+#define RT_SW(RB, AH)                                                                                      \
+  k_sweep_tiles<T, RB, AH><<<nsw, RB, 0, s>>>(cm, tb, h->d_sw_tiles, h->n_cols, h->E, S, x, y, out, use_tsrc, \
+                                             inflow)
+  const int rb = h->tune.ray_block, ah = h->tune.ahead;
+  if (rb == 64) {
+    if (ah == 4) RT_SW(64, 4); else if (ah == 16) RT_SW(64, 16); else RT_SW(64, 8);
+  } else if (rb == 256) {
+    if (ah == 4) RT_SW(256, 4); else if (ah == 16) RT_SW(256, 16); else RT_SW(256, 8);
+  } else {
+    if (ah == 4) RT_SW(128, 4); else if (ah == 16) RT_SW(128, 16); else RT_SW(128, 8);
+  }
+#undef RT_SW
+}
+
 template <typename T>
 static int run_apply(rt_handle *h, const Tables<T> &tb, int op, const double *x, double *y, cudaStream_t s,
                      bool first_rhs_only, void *scratch) {
@@ -69,31 +88,34 @@ static int run_apply(rt_handle *h, const Tables<T> &tb, int op, const double *x,
   const bool tc = sizeof(T) == 4 && h->n_tc_jobs > 0 && !first_rhs_only;
   auto sigma = [&]() -> int {
     k_sigma_tiles<T, double><<<nsig, kSigNT, 0, s>>>(cm, tb, h->d_sig_tiles, h->n_cols, h->E, x, S, tc ? 1 : 0);
-    if (tc) return launch_sigma_dense_tc(h, false, x, reinterpret_cast<float *>(S), s);
+    if (tc) return launch_sigma_dense_tc(h, false, x, S, false, s);
     return 0;
   };
   const int cgrid = (int)std::min<int64_t>((len + 255) / 256, 16 * 152);
   switch (op) {
     case 0:  // y = x - Lambda Sigma x
       sigma();
-      k_sweep_tiles<T><<<nsw, kRayBlock, 0, s>>>(cm, tb, h->d_sw_tiles, h->n_cols, h->E, S, x, y, kOutAminus, 0, 0);
+      sweep_launch<T>(h, nsw, cm, tb, S, x, y, kOutAminus, 0, 0, s);
       break;
     case 1:  // y = Lambda x
       k_convert<T><<<cgrid, 256, 0, s>>>(x, S, len);
-      k_sweep_tiles<T><<<nsw, kRayBlock, 0, s>>>(cm, tb, h->d_sw_tiles, h->n_cols, h->E, S, nullptr, y, kOutI, 0, 0);
+      sweep_launch<T>(h, nsw, cm, tb, S, nullptr, y, kOutI, 0, 0, s);
       break;
     case 2:  // y = Sigma x
+      if (tc && tc_all_columns(h)) {  // every column on the tensor cores: straight into y
+        const int e = launch_sigma_dense_tc(h, false, x, y, true, s);
+        if (e) return e;
+        break;
+      }
       sigma();
       k_widen<T><<<cgrid, 256, 0, s>>>(S, y, len);
       break;
     default:  // y = Lambda t + I_in
       if (h->d_tsrc) {
-        k_sweep_tiles<T><<<nsw, kRayBlock, 0, s>>>(cm, tb, h->d_sw_tiles, h->n_cols, h->E, nullptr, nullptr, y,
-                                                   kOutI, 1, 1);
+        sweep_launch<T>(h, nsw, cm, tb, nullptr, nullptr, y, kOutI, 1, 1, s);
       } else {
         cudaMemsetAsync(S, 0, len * sizeof(T), s);
-        k_sweep_tiles<T><<<nsw, kRayBlock, 0, s>>>(cm, tb, h->d_sw_tiles, h->n_cols, h->E, S, nullptr, y, kOutI,
-                                                   0, 1);
+        sweep_launch<T>(h, nsw, cm, tb, S, nullptr, y, kOutI, 0, 1, s);
       }
   }
   return (int)cudaGetLastError();

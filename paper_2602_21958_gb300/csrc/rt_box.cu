@@ -46,8 +46,11 @@ __device__ __forceinline__ void step_coef(T d, int ie, T &e, T &a, T &b) {
   a = w0 - beta;
 }
 
+// geo per direction (6 doubles): fx, fy (integer upwind shift in cells,
+// reduced modulo nx, ny: the box is periodic), ax, ay (fractional parts),
+// ds (path length between planes), up (1: Omega_z > 0)
 template <typename T, int VPT>
-__global__ void __launch_bounds__(1024) k_sweep3d(BoxDev bx, const double *__restrict__ geo,
+__global__ void __launch_bounds__(1024, 1) k_sweep3d(BoxDev bx, const double *__restrict__ geo,
                                                   const T *__restrict__ chi, const T *S,
                                                   const double *__restrict__ tsrc, const void *xin,
                                                   int x_is_float, void *yout, int y_is_float, int out,
@@ -61,11 +64,12 @@ __global__ void __launch_bounds__(1024) k_sweep3d(BoxDev bx, const double *__res
   const int nfb = (nn + FB - 1) / FB;
   const int d = blockIdx.x / nfb, f0 = (blockIdx.x % nfb) * FB;
   const int nr = nd * nn;
-  const double sx = geo[4 * d + 0], sy = geo[4 * d + 1], ds = geo[4 * d + 2];
-  const int up = geo[4 * d + 3] > 0.5;
-  const int fx = (int)floor(sx), fy = (int)floor(sy);
-  const T ax = (T)(sx - fx), ay = (T)(sy - fy);
-  const T hds = (T)(0.5 * ds);
+  const double *g = geo + 6 * d;
+  const int fx = (int)g[0], fy = (int)g[1];
+  const T ax = (T)g[2], ay = (T)g[3];
+  const T hds = (T)(0.5 * g[4]);
+  const int up = g[5] > 0.5;
+  const T w00 = ((T)1 - ay) * ((T)1 - ax), w01 = ((T)1 - ay) * ax, w10 = ay * ((T)1 - ax), w11 = ay * ax;
   const int step = up ? -1 : 1;
   const int k0 = up ? nz - 1 : 0;
   const int nval = plane * FB;
@@ -74,54 +78,58 @@ __global__ void __launch_bounds__(1024) k_sweep3d(BoxDev bx, const double *__res
   double *yd = static_cast<double *>(yout);
   float *yf = static_cast<float *>(yout);
   auto emit = [&](int64_t k, T I) {
-    double v;
-    if (out == kOutI) v = (double)I;
-    else v = (x_is_float ? (double)xf[k] : xd[k]) - (double)I;
-    if (y_is_float) yf[k] = (float)v;
-    else yd[k] = v;
+    if (out == kOutI) {
+      if (y_is_float) yf[k] = (float)I;
+      else yd[k] = (double)I;
+    } else if (y_is_float && x_is_float) {
+      yf[k] = xf[k] - (float)I;
+    } else {
+      const double v = (x_is_float ? (double)xf[k] : xd[k]) - (double)I;
+      if (y_is_float) yf[k] = (float)v;
+      else yd[k] = v;
+    }
   };
   auto src = [&](int64_t p, int f) -> T {
     return tsrc ? (T)tsrc[p * nn + f] : S[p * nr + (int64_t)d * nn + f];
   };
+  const bool pow2 = (nx & (nx - 1)) == 0;
+  const int lgx = __ffs(nx) - 1;
   // first plane: inflow (or zero)
   for (int v = threadIdx.x; v < nval; v += blockDim.x) {
-    const int cell = v / FB, fl = v - cell * FB, f = f0 + fl;
+    const int c = v / FB, fl = v - c * FB, f = f0 + fl;
     T I0 = 0;
     if (inflow && f < nn) I0 = (T)(up ? I_bot[f] : I_top[f]);
     Ip[v] = I0;
-    if (f < nn) emit(((int64_t)k0 * plane + cell) * nr + (int64_t)d * nn + f, I0);
+    if (f < nn) emit(((int64_t)k0 * plane + c) * nr + (int64_t)d * nn + f, I0);
   }
   __syncthreads();
   for (int s = 1; s < nz; ++s) {
     const int k = k0 + s * step, ku = k - step;
+    const int64_t pu = (int64_t)ku * plane, pk = (int64_t)k * plane;
     T In[VPT];
 #pragma unroll
     for (int i = 0; i < VPT; ++i) {
-      const int v = threadIdx.x + i * blockDim.x;
       In[i] = 0;
+      const int v = threadIdx.x + i * blockDim.x;
       if (v >= nval) continue;
-      const int cell = v / FB, fl = v - cell * FB, f = f0 + fl;
+      const int c = v / FB, fl = v - c * FB, f = f0 + fl;
       if (f >= nn) continue;
-      const int y = cell / nx, x = cell - y * nx;
-      // upwind neighbours in plane ku: (y-fy, x-fx), (y-fy, x-fx-1), (y-fy-1, x-fx), (y-fy-1, x-fx-1)
-      int x0 = (x - fx) % nx;
+      const int y = pow2 ? (c >> lgx) : c / nx, x = c - y * nx;
+      int x0 = x - fx, y0 = y - fy;
       if (x0 < 0) x0 += nx;
-      int y0 = (y - fy) % ny;
       if (y0 < 0) y0 += ny;
       const int x1 = x0 == 0 ? nx - 1 : x0 - 1;
       const int y1 = y0 == 0 ? ny - 1 : y0 - 1;
       const int c00 = y0 * nx + x0, c01 = y0 * nx + x1, c10 = y1 * nx + x0, c11 = y1 * nx + x1;
-      const T w00 = ((T)1 - ay) * ((T)1 - ax), w01 = ((T)1 - ay) * ax, w10 = ay * ((T)1 - ax), w11 = ay * ax;
-      const int64_t pu = (int64_t)ku * plane, pc = (int64_t)k * plane + cell;
+      const int64_t pc = pk + c;
       const T Iu = w00 * Ip[c00 * FB + fl] + w01 * Ip[c01 * FB + fl] + w10 * Ip[c10 * FB + fl] +
                    w11 * Ip[c11 * FB + fl];
       const T Su = w00 * src(pu + c00, f) + w01 * src(pu + c01, f) + w10 * src(pu + c10, f) +
                    w11 * src(pu + c11, f);
       const T cu = w00 * chi[(pu + c00) * nn + f] + w01 * chi[(pu + c01) * nn + f] +
                    w10 * chi[(pu + c10) * nn + f] + w11 * chi[(pu + c11) * nn + f];
-      const T cc = chi[pc * nn + f];
       T e, a, b;
-      step_coef<T>(hds * (cu + cc), bx.ie, e, a, b);
+      step_coef<T>(hds * (cu + chi[pc * nn + f]), bx.ie, e, a, b);
       In[i] = e * Iu + a * Su + b * src(pc, f);
       emit(pc * nr + (int64_t)d * nn + f, In[i]);
     }
@@ -136,35 +144,24 @@ __global__ void __launch_bounds__(1024) k_sweep3d(BoxDev bx, const double *__res
 }
 
 // Launch the 3D sweep; x/y may be float or double (the float64 path passes
-// double for both).  Threads per CTA: plane*FB / VPT, VPT in {4, 8, 16, 32}.
+// double for both).  32 values per thread; threads per CTA = plane*FB/32.
 template <typename T>
 static int sweep3d_launch(rt_handle *h, const T *chi, const T *S, const double *tsrc, const void *x,
                           bool xf, void *y, bool yf, int out, bool inflow, cudaStream_t s) {
   const BoxDev &bx = h->box;
   constexpr int FB = 32 / sizeof(T);
+  constexpr int VPT = 32;
   const int plane = bx.nx * bx.ny;
   const int nval = plane * FB;
   const int nfb = (bx.nn + FB - 1) / FB;
   const int grid = bx.nd * nfb;
   const size_t smem = (size_t)nval * sizeof(T);
-  int vpt = 4;
-  while (vpt < 32 && (nval + vpt - 1) / vpt > 1024) vpt *= 2;
-  int nt = (nval + vpt - 1) / vpt;
+  int nt = (nval + VPT - 1) / VPT;
   nt = (nt + 31) / 32 * 32;
-  if (nt > 1024) return (int)cudaErrorInvalidConfiguration;
-#define RT_SW3(V)                                                                                          \
-  do {                                                                                                     \
-    cudaFuncSetAttribute(k_sweep3d<T, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);         \
-    k_sweep3d<T, V><<<grid, nt, smem, s>>>(bx, h->d_geo, chi, S, tsrc, x, xf ? 1 : 0, y, yf ? 1 : 0, out, \
-                                           inflow ? 1 : 0, h->d_Itop, h->d_Ibot);                           \
-  } while (0)
-  switch (vpt) {
-    case 4: RT_SW3(4); break;
-    case 8: RT_SW3(8); break;
-    case 16: RT_SW3(16); break;
-    default: RT_SW3(32); break;
-  }
-#undef RT_SW3
+  if (nt > 1024 || plane >= 65536) return (int)cudaErrorInvalidConfiguration;
+  cudaFuncSetAttribute(k_sweep3d<T, VPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_sweep3d<T, VPT><<<grid, nt, smem, s>>>(bx, h->d_geo, chi, S, tsrc, x, xf ? 1 : 0, y, yf ? 1 : 0, out,
+                                           inflow ? 1 : 0, h->d_Itop, h->d_Ibot);
   return (int)cudaGetLastError();
 }
 

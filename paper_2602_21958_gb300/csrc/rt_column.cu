@@ -131,12 +131,16 @@ __device__ __forceinline__ double cta_norm2(const double *v, int64_t n, double *
 // over 8 consecutive elements of a thread are taken in TL, then accumulated
 // in float64, then summed over the block in float64.
 template <typename TL>
-__device__ double cta_dots(const TL *V, int64_t ldv, int j, const TL *w, int64_t n, double *h,
+__device__ __noinline__ double cta_dots(const TL *V, int64_t ldv, int j, const TL *w, int64_t n, double *h,
                            double *red, double *outb) {
   double nrm = 0.0;
   constexpr int kWiden = 8;  // loop iterations summed in TL before one float64 add
   for (int i0 = 0; i0 <= j; i0 += kDots) {
     const int cnt = min(kDots, j + 1 - i0);
+    // unconditional loads: vectors past the last one re-read the last (cache hit)
+    const TL *vp[kDots];
+#pragma unroll
+    for (int u = 0; u < kDots; ++u) vp[u] = V + (int64_t)min(i0 + u, j) * ldv;
     double acc[kDots + 1];
 #pragma unroll
     for (int u = 0; u <= kDots; ++u) acc[u] = 0.0;
@@ -145,30 +149,23 @@ __device__ double cta_dots(const TL *V, int64_t ldv, int j, const TL *w, int64_t
     for (int u = 0; u <= kDots; ++u) part[u] = 0;
     int it = 0;
     for (int64_t k0 = threadIdx.x; k0 < n; k0 += (int64_t)kU * blockDim.x) {
-      TL wv[kU];
+      TL wv[kU], vv[kDots][kU];
 #pragma unroll
       for (int e = 0; e < kU; ++e) {
-        const int64_t k = k0 + (int64_t)e * blockDim.x;
-        wv[e] = k < n ? w[k] : (TL)0;
+        const int64_t k = min(k0 + (int64_t)e * blockDim.x, n - 1);
+        wv[e] = w[k];
+#pragma unroll
+        for (int u = 0; u < kDots; ++u) vv[u][e] = vp[u][k];
       }
 #pragma unroll
-      for (int u = 0; u < kDots; ++u) {
-        if (u < cnt) {
-          const TL *vi = V + (int64_t)(i0 + u) * ldv;
-          TL vv[kU];
+      for (int e = 0; e < kU; ++e)
+        if (k0 + (int64_t)e * blockDim.x >= n) wv[e] = 0;
 #pragma unroll
-          for (int e = 0; e < kU; ++e) {
-            const int64_t k = k0 + (int64_t)e * blockDim.x;
-            vv[e] = k < n ? vi[k] : (TL)0;
-          }
+      for (int u = 0; u < kDots; ++u)
 #pragma unroll
-          for (int e = 0; e < kU; ++e) part[u] = fma(vv[e], wv[e], part[u]);
-        }
-      }
-      if (i0 == 0) {
+        for (int e = 0; e < kU; ++e) part[u] = fma(vv[u][e], wv[e], part[u]);
 #pragma unroll
-        for (int e = 0; e < kU; ++e) part[kDots] = fma(wv[e], wv[e], part[kDots]);
-      }
+      for (int e = 0; e < kU; ++e) part[kDots] = fma(wv[e], wv[e], part[kDots]);
       if (++it == kWiden) {
         it = 0;
 #pragma unroll
@@ -195,22 +192,20 @@ template <typename TL>
 __device__ __forceinline__ void axpy_block(const TL *V, int64_t ldv, int cnt, const TL *coef, int64_t k0,
                                            int64_t n, TL (&acc)[kU]) {
   for (int i0 = 0; i0 < cnt; i0 += kDots) {
-    TL v[kDots][kU];
+    TL v[kDots][kU], hu[kDots];
 #pragma unroll
     for (int u = 0; u < kDots; ++u) {
-      const TL *vi = V + (int64_t)(i0 + u) * ldv;
+      // unconditional loads: rows past cnt re-read row cnt-1 with a zero coefficient
+      const int i = min(i0 + u, cnt - 1);
+      hu[u] = (i0 + u < cnt) ? coef[i0 + u] : (TL)0;
+      const TL *vi = V + (int64_t)i * ldv;
 #pragma unroll
-      for (int e = 0; e < kU; ++e) {
-        const int64_t k = k0 + (int64_t)e * blockDim.x;
-        v[u][e] = (i0 + u < cnt && k < n) ? vi[k] : (TL)0;
-      }
+      for (int e = 0; e < kU; ++e) v[u][e] = vi[min(k0 + (int64_t)e * blockDim.x, n - 1)];
     }
 #pragma unroll
-    for (int u = 0; u < kDots; ++u) {
-      const TL hu = (i0 + u < cnt) ? coef[i0 + u] : (TL)0;
+    for (int u = 0; u < kDots; ++u)
 #pragma unroll
-      for (int e = 0; e < kU; ++e) acc[e] = fma(hu, v[u][e], acc[e]);
-    }
+      for (int e = 0; e < kU; ++e) acc[e] = fma(hu[u], v[u][e], acc[e]);
   }
 }
 
@@ -224,7 +219,7 @@ __device__ __forceinline__ void stage_coef(const double *h, int cnt, double sgn,
 // w = (w - V[0..j] h) * scale; returns ||result||^2 when want_norm (else 0).
 // hf: shared scratch of at least j+1 TL.
 template <typename TL>
-__device__ double cta_update(const TL *V, int64_t ldv, int j, TL *w, int64_t n, const double *h,
+__device__ __noinline__ double cta_update(const TL *V, int64_t ldv, int j, TL *w, int64_t n, const double *h,
                              double scale, bool want_norm, TL *hf, double *red, double *outb) {
   stage_coef<TL>(h, j + 1, -1.0, hf);
   const TL sc = (TL)scale;
@@ -266,8 +261,8 @@ constexpr int kMaxM = 512;  // largest Krylov basis per instance
 //   Givens rotations and the triangular solve in float64 by thread 0;
 //   x += V y with the correction summed in TL.
 template <typename TL>
-__global__ void __launch_bounds__(kNT) k_solve(SolveParams p) {
-  __shared__ double sm[2 * kSigBuf];
+__global__ void __launch_bounds__(kNT, 1) k_solve(SolveParams p) {
+  __shared__ double sm[4 * kSigBuf];
   __shared__ double red[(kNT / 32) * (kDots + 1)];
   __shared__ double outb[kDots + 1];
   __shared__ double hbuf[2 * (kMaxM + 8)];
@@ -324,7 +319,7 @@ __global__ void __launch_bounds__(kNT) k_solve(SolveParams p) {
         rsrc = bv;
         bpe += 0.0;
       } else {
-        sigma_column<double, double>(c, p.t64, x, S64, sm, sm + kSigBuf);
+        sigma_column<double, double>(c, p.t64, x, S64, sm, 4 * kSigBuf);
         double a[1] = {sweep_column<double, double, double>(c, p.t64, p.cm, S64, nullptr, x, bv, S64,
                                                             kOutResid, false)};
         block_sum<1>(a, red, outb);
@@ -346,7 +341,7 @@ __global__ void __launch_bounds__(kNT) k_solve(SolveParams p) {
       for (int j = 0; j < m; ++j) {
         TL *vj = Vslot + (int64_t)j * ldv;
         TL *w = Vslot + (int64_t)(j + 1) * ldv;
-        sigma_column<TL, TL>(c, tl, vj, SL, reinterpret_cast<TL *>(sm), reinterpret_cast<TL *>(sm) + kSigBuf);
+        sigma_column<TL, TL>(c, tl, vj, SL, reinterpret_cast<TL *>(sm), 4 * kSigBuf * (int)(8 / sizeof(TL)));
         sweep_column<TL, TL, TL>(c, tl, p.cm, SL, nullptr, vj, nullptr, w, kOutAminus, false);
         __syncthreads();
         bpe += 5.0 * sz;  // v, S, S, v, w
@@ -512,8 +507,8 @@ __device__ __forceinline__ void tri_solve(const double *Hc, int ld, const double
 //   z_i ~ A^-1 v_i (float32), w = A z_i (float64 operator), orthogonalise w,
 //   x += Z y at the end of a cycle; cycles restart from the true residual.
 // One CTA per (column, rhs) instance, as k_solve.
-__global__ void __launch_bounds__(kNT) k_solve_nested(SolveParams p) {
-  __shared__ double sm[2 * kSigBuf];
+__global__ void __launch_bounds__(kNT, 1) k_solve_nested(SolveParams p) {
+  __shared__ double sm[4 * kSigBuf];
   __shared__ double red[(kNT / 32) * (kDots + 1)];
   __shared__ double outb[kDots + 1];
   __shared__ double hbuf[2 * (kMaxM + 8)];
@@ -572,7 +567,7 @@ __global__ void __launch_bounds__(kNT) k_solve_nested(SolveParams p) {
         rn = bn;
         rsrc = bv;
       } else {
-        sigma_column<double, double>(c, p.t64, x, S64, sm, sm + kSigBuf);
+        sigma_column<double, double>(c, p.t64, x, S64, sm, 4 * kSigBuf);
         double a[1] = {sweep_column<double, double, double>(c, p.t64, p.cm, S64, nullptr, x, bv, S64,
                                                             kOutResid, false)};
         block_sum<1>(a, red, outb);
@@ -612,9 +607,8 @@ __global__ void __launch_bounds__(kNT) k_solve_nested(SolveParams p) {
         for (int j = 0; j < m_in; ++j) {
           float *uj = U + (int64_t)j * ldv;
           float *w = U + (int64_t)(j + 1) * ldv;
-          sigma_column<float, float>(c, p.t32, uj, S32, reinterpret_cast<float *>(sm),
-                                     reinterpret_cast<float *>(sm) + kSigBuf);
-          sweep_column<float, float, float>(c, p.t32, p.cm, S32, nullptr, uj, nullptr, w, kOutAminus, false);
+          sigma_column<float, float>(c, p.t32, uj, S32, reinterpret_cast<float *>(sm), 8 * kSigBuf);
+          sweep_column<float, float, float, 4>(c, p.t32, p.cm, S32, nullptr, uj, nullptr, w, kOutAminus, false);
           __syncthreads();
           bpe += 20.0;
           const double hn = arnoldi_orth<float>(U, ldv, j, n, h, h2, hf32, red, outb, bpe);
@@ -644,8 +638,8 @@ __global__ void __launch_bounds__(kNT) k_solve_nested(SolveParams p) {
         bpe += 4.0 * (jdone + 1);
         // ---- outer: w = A z_i in float64, orthogonalise in float64 ----------
         double *w = Vo + (int64_t)(i + 1) * ldv;
-        sigma_column<double, float>(c, p.t64, zi, S64, sm, sm + kSigBuf);
-        sweep_column<double, float, double>(c, p.t64, p.cm, S64, nullptr, zi, nullptr, w, kOutAminus, false);
+        sigma_column<double, float>(c, p.t64, zi, S64, sm, 4 * kSigBuf);
+        sweep_column<double, float, double, 4>(c, p.t64, p.cm, S64, nullptr, zi, nullptr, w, kOutAminus, false);
         __syncthreads();
         bpe += 4.0 + 8.0 + 8.0 + 4.0 + 8.0;
         const double hn = arnoldi_orth<double>(Vo, ldv, i, n, h, h2, hf64, red, outb, bpe);

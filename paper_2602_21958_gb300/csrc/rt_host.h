@@ -26,6 +26,15 @@ struct Workspace {
   double *H = nullptr;     // [slots][hld]
 };
 
+// Launch shapes of the apply kernels (rt_autotune)
+struct Tune {
+  int ray_block = 128;   // rays per sweep tile (threads per CTA): 64, 128, 256
+  int ahead = 8;         // depth points of loads in flight per ray: 4, 8, 16
+  int sigma_pts = 0;     // cap on points per Sigma tile: 4, 8, or 0 (as many as fit)
+  double ms = 0.0;       // apply time measured for this choice
+  int from_cache = 0;
+};
+
 // 3D box geometry (device-side copy of the scalars)
 struct BoxDev {
   int nx, ny, nz, nd, nn, ie;
@@ -67,6 +76,7 @@ struct rt_handle {
   void *d_tc_jobs = nullptr;          // TcJob[n_tc_jobs]
   int64_t *d_tc_off = nullptr;        // per column offset into the bf16 tiles
   uint16_t *d_tc_tiles = nullptr;     // pre-tiled bf16 PsiW
+  uint32_t *d_tc_xb = nullptr;        // X packed to bf16 (A operand), n_rhs*E values
   int *d_err = nullptr;               // device error word (bounded waits)
   // 3D boxes: geometry, per-direction (sx, sy, ds, up), opacity, grid-solve scratch
   // CUDA graph of the batched solve (queue reset + persistent kernel), reused
@@ -75,6 +85,7 @@ struct rt_handle {
   cudaStream_t capture_stream = nullptr;
   unsigned long long graph_key[8] = {};
   int graph_replays = 0;
+  rt::Tune tune{};
   rt::BoxDev box{};
   double *d_geo = nullptr;
   double *chi64 = nullptr;
@@ -94,7 +105,9 @@ int launch_apply(rt_handle *h, int op, bool fp64, const double *x, double *y, cu
 int launch_solve(rt_handle *h, const double *b, double *x, double tol, double tol_inner, int m,
                  int max_outer, int use_x0, cudaStream_t s, int m_in);
 int solve_block_threads();
-int launch_sigma_dense_tc(rt_handle *h, bool x_is_float, const void *x, float *S, cudaStream_t s);
+int launch_sigma_dense_tc(rt_handle *h, bool x_is_float, const void *x, void *S, bool s_is_double,
+                          cudaStream_t s);
+int tc_all_columns(const rt_handle *h);
 struct TcJob;
 int tc_prepare(rt_handle *h, const std::vector<double> &psiwT);
 int launch_sweep3d(rt_handle *h, bool fp64, const void *S, const double *tsrc, const void *x, bool xf,
@@ -107,7 +120,7 @@ int grid_ctas(const rt_handle *h);
 // allocation-free apply: scratch in a static device array of this many bytes
 constexpr long long kNoAllocScratchBytes = 16ll << 20;
 int launch_apply_noalloc(rt_handle *h, int op, bool fp64, const double *x, double *y, cudaStream_t s);
-constexpr int kRayBlock = 128;  // rays (threads) per sweep tile
+constexpr int kRayBlock = 128;  // default rays (threads) per sweep tile
 int max_krylov();
 int apply_slots(rt_handle *h);
 }  // namespace rt

@@ -94,10 +94,11 @@ template <typename T> __device__ __forceinline__ T to(double v) { return (T)v; }
 // X is read in its own type and rounded to T; S is written in T.  Shared buffers:
 // sm0, sm1 each kSigBuf elements of T.
 // Points [p0, p0+np) of one column; np * rp * nn (separable) or np * nr
-// (dense) must not exceed kSigBuf.  Ends with __syncthreads().
-template <typename T, typename TX>
-__device__ void sigma_block(const ColDev &c, const Tables<T> &tb, const TX *__restrict__ X,
-                            T *__restrict__ S, int p0, int np, T *sm0, T *sm1) {
+// (dense) must not exceed kSigBuf.  Ends with __syncthreads().  KR: ranks kept
+// in registers per pass (a compile-time bound, so no dead predicated work).
+template <typename T, typename TX, int KR>
+__device__ void sigma_block_kr(const ColDev &c, const Tables<T> &tb, const TX *__restrict__ X,
+                               T *__restrict__ S, int p0, int np, T *sm0, T *sm1) {
   const int nd = c.nd, nn = c.nn, nr = c.nr, rp = c.rp;
   const T *gam = tb.gamma + c.g_off;
   if (c.psi_off >= 0) {
@@ -119,15 +120,15 @@ __device__ void sigma_block(const ColDev &c, const Tables<T> &tb, const TX *__re
   const T *Ul = tb.Ul + c.u_off;
   const T *Rw = tb.RwT + c.r_off;
   const int per_pt = rp * nn;
-  // 1. angular moments, one thread per (point, nu'), up to kMaxRank ranks in registers
+  // 1. angular moments, one thread per (point, nu'), KR ranks in registers per pass
   for (int i = threadIdx.x; i < np * nn; i += blockDim.x) {
     const int b = i / nn, f = i - b * nn;
     const TX *xp = X + (int64_t)(p0 + b) * nr + f;
-    for (int k0 = 0; k0 < rp; k0 += kMaxRank) {
-      const int kn = min(kMaxRank, rp - k0);
-      T m[kMaxRank];
+    for (int k0 = 0; k0 < rp; k0 += KR) {
+      const int kn = min(KR, rp - k0);
+      T m[KR];
 #pragma unroll
-      for (int k = 0; k < kMaxRank; ++k) m[k] = 0;
+      for (int k = 0; k < KR; ++k) m[k] = 0;
       int d = 0;
       for (; d + 4 <= nd; d += 4) {  // four independent loads in flight
         T xv[4];
@@ -137,7 +138,7 @@ __device__ void sigma_block(const ColDev &c, const Tables<T> &tb, const TX *__re
         for (int e = 0; e < 4; ++e) {
           const T *u = Uw + (d + e) * rp + k0;
 #pragma unroll
-          for (int k = 0; k < kMaxRank; ++k)
+          for (int k = 0; k < KR; ++k)
             if (k < kn) m[k] = fma(u[k], xv[e], m[k]);
         }
       }
@@ -145,11 +146,11 @@ __device__ void sigma_block(const ColDev &c, const Tables<T> &tb, const TX *__re
         const T xv = to<T>(xp[d * nn]);
         const T *u = Uw + d * rp + k0;
 #pragma unroll
-        for (int k = 0; k < kMaxRank; ++k)
+        for (int k = 0; k < KR; ++k)
           if (k < kn) m[k] = fma(u[k], xv, m[k]);
       }
 #pragma unroll
-      for (int k = 0; k < kMaxRank; ++k)
+      for (int k = 0; k < KR; ++k)
         if (k < kn) sm0[(b * rp + k0 + k) * nn + f] = m[k];
     }
   }
@@ -180,19 +181,151 @@ __device__ void sigma_block(const ColDev &c, const Tables<T> &tb, const TX *__re
   __syncthreads();
 }
 
-// Points per Sigma block for one column (fits the two shared buffers).
-__host__ __device__ inline int sigma_points_per_block(const ColDev &c) {
+template <typename T, typename TX>
+__device__ void sigma_block(const ColDev &c, const Tables<T> &tb, const TX *__restrict__ X,
+                            T *__restrict__ S, int p0, int np, T *sm0, T *sm1) {
+  if (c.rp <= 2) sigma_block_kr<T, TX, 2>(c, tb, X, S, p0, np, sm0, sm1);
+  else sigma_block_kr<T, TX, 8>(c, tb, X, S, p0, np, sm0, sm1);
+}
+
+// ---- separable Sigma, one warp per point --------------------------------
+constexpr int kWarpBuf = 1024;  // elements of each per-warp shared buffer
+
+// True when the per-warp form applies (separable kernel, rank*n_nu small).
+__host__ __device__ inline bool sigma_warp_ok(const ColDev &c) {
+  return c.psi_off < 0 && c.rp * c.nn <= kWarpBuf;
+}
+
+// S_p = Gamma_p (factored P (x) R) X_p for points p = p_begin + warp, stepping
+// by the number of warps in the block.  wm, wz: this warp's two shared
+// buffers of kWarpBuf T.  Only __syncwarp inside: warps progress on their own,
+// so the loads of many points are in flight at once.
+template <typename T, typename TX, int KR>
+__device__ void sigma_points_warp(const ColDev &c, const Tables<T> &tb, const TX *__restrict__ X,
+                                  T *__restrict__ S, int p_begin, int p_end, T *wm, T *wz) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int nd = c.nd, nn = c.nn, nr = c.nr, rp = c.rp;
+  const T *Uw = tb.Uw + c.u_off;
+  const T *Ul = tb.Ul + c.u_off;
+  const T *Rw = tb.RwT + c.r_off;
+  const T *gam = tb.gamma + c.g_off;
+  for (int p = p_begin + warp; p < p_end; p += nw) {
+    const TX *xp = X + (int64_t)p * nr;
+    // 1. moments m_k(f) = sum_d Uw[d][k] X(d, f); lanes over f, KR ranks per pass
+    for (int f = lane; f < nn; f += 32) {
+      for (int k0 = 0; k0 < rp; k0 += KR) {
+        const int kn = min(KR, rp - k0);
+        T m[KR];
+#pragma unroll
+        for (int k = 0; k < KR; ++k) m[k] = 0;
+        int d = 0;
+        for (; d + 8 <= nd; d += 8) {
+          T xv[8];
+#pragma unroll
+          for (int e = 0; e < 8; ++e) xv[e] = to<T>(xp[(d + e) * nn + f]);
+#pragma unroll
+          for (int e = 0; e < 8; ++e) {
+            const T *u = Uw + (d + e) * rp + k0;
+#pragma unroll
+            for (int k = 0; k < KR; ++k)
+              if (k < kn) m[k] = fma(u[k], xv[e], m[k]);
+          }
+        }
+        for (; d < nd; ++d) {
+          const T xv = to<T>(xp[d * nn + f]);
+          const T *u = Uw + d * rp + k0;
+#pragma unroll
+          for (int k = 0; k < KR; ++k)
+            if (k < kn) m[k] = fma(u[k], xv, m[k]);
+        }
+#pragma unroll
+        for (int k = 0; k < KR; ++k)
+          if (k < kn) wm[(k0 + k) * nn + f] = m[k];
+      }
+    }
+    __syncwarp();
+    // 2. frequency kernel z_k(f) = sum_q RwT[q][f] m_k(q): each lane owns two
+    //    frequencies (f, f+32) and KR ranks, so a RwT load feeds KR FMAs and a
+    //    moment load feeds two
+    for (int fb = 0; fb < nn; fb += 64) {
+      const int fa = fb + lane, fc = fa + 32;
+      const bool va = fa < nn, vc = fc < nn;
+      const int fa_ = va ? fa : 0, fc_ = vc ? fc : 0;
+      for (int k0 = 0; k0 < rp; k0 += KR) {
+        const int kn = min(KR, rp - k0);
+        const T *mk = wm + k0 * nn;
+        T aa[KR], ac[KR];
+#pragma unroll
+        for (int k = 0; k < KR; ++k) aa[k] = ac[k] = 0;
+        if (c.rdiag) {
+#pragma unroll
+          for (int k = 0; k < KR; ++k)
+            if (k < kn) {
+              aa[k] = Rw[fa_] * mk[k * nn + fa_];
+              ac[k] = Rw[fc_] * mk[k * nn + fc_];
+            }
+        } else {
+          for (int q = 0; q < nn; ++q) {
+            const T ra = Rw[q * nn + fa_], rc = Rw[q * nn + fc_];
+#pragma unroll
+            for (int k = 0; k < KR; ++k)
+              if (k < kn) {
+                const T mv = mk[k * nn + q];
+                aa[k] = fma(ra, mv, aa[k]);
+                ac[k] = fma(rc, mv, ac[k]);
+              }
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < KR; ++k)
+          if (k < kn) {
+            if (va) wz[(k0 + k) * nn + fa] = aa[k];
+            if (vc) wz[(k0 + k) * nn + fc] = ac[k];
+          }
+      }
+    }
+    __syncwarp();
+    // 3. expansion S(d, f) = gamma(f) sum_k Ul[d][k] z_k(f)
+    const T *g = gam + (int64_t)p * nn;
+    T *sp = S + (int64_t)p * nr;
+    for (int r = lane; r < nr; r += 32) {
+      const int d = r / nn, f = r - d * nn;
+      const T *u = Ul + d * rp;
+      T acc = 0;
+      for (int k = 0; k < rp; ++k) acc = fma(u[k], wz[k * nn + f], acc);
+      sp[r] = g[f] * acc;
+    }
+    __syncwarp();
+  }
+}
+
+// Points per Sigma tile of the apply kernel (256 threads): what fits the two
+// block buffers, at most max_pts.
+__host__ __device__ inline int sigma_points_per_block(const ColDev &c, int max_pts = 1 << 30) {
   const int per_pt = c.psi_off >= 0 ? c.nr : c.rp * c.nn;
-  const int pb = kSigBuf / per_pt;
+  int pb = kSigBuf / per_pt;
+  if (pb > max_pts) pb = max_pts;
   return pb < 1 ? 1 : pb;
 }
 
 // Every point of one column, block by block (one CTA).
+// smbuf holds cap elements of T (cap >= 2*kSigBuf); warps take equal shares
+// of it when the per-warp form fits, else it is split into the two block buffers.
 template <typename T, typename TX>
-__device__ void sigma_column(const ColDev &c, const Tables<T> &tb, const TX *__restrict__ X,
-                             T *__restrict__ S, T *sm0, T *sm1) {
+__device__ __noinline__ void sigma_column(const ColDev &c, const Tables<T> &tb, const TX *__restrict__ X,
+                             T *__restrict__ S, T *smbuf, int cap) {
+  const int nw = blockDim.x >> 5;
+  const int per_warp = cap / nw / 2;
+  if (sigma_warp_ok(c) && c.rp * c.nn <= per_warp) {
+    T *wm = smbuf + (threadIdx.x >> 5) * 2 * per_warp;
+    if (c.rp <= 2) sigma_points_warp<T, TX, 2>(c, tb, X, S, 0, c.nz, wm, wm + per_warp);
+    else sigma_points_warp<T, TX, 8>(c, tb, X, S, 0, c.nz, wm, wm + per_warp);
+    __syncthreads();
+    return;
+  }
   const int pb = sigma_points_per_block(c);
-  for (int p0 = 0; p0 < c.nz; p0 += pb) sigma_block<T, TX>(c, tb, X, S, p0, min(pb, c.nz - p0), sm0, sm1);
+  for (int p0 = 0; p0 < c.nz; p0 += pb)
+    sigma_block<T, TX>(c, tb, X, S, p0, min(pb, c.nz - p0), smbuf, smbuf + kSigBuf);
 }
 
 // ------------------------------------------------------------------ sweep
@@ -285,7 +418,7 @@ __device__ double sweep_ray(const ColDev &c, const Tables<T> &tb, const Common &
 // only at the points of its own rays, the source value is read before the
 // output at the same point is written.
 template <typename T, typename TX, typename TY, int kAhead = 4>
-__device__ double sweep_column(const ColDev &c, const Tables<T> &tb, const Common &cm,
+__device__ __noinline__ double sweep_column(const ColDev &c, const Tables<T> &tb, const Common &cm,
                                const T *S, const double *__restrict__ tsrc,
                                const TX *__restrict__ x, const double *__restrict__ bv,
                                TY *y, int out, bool inflow) {

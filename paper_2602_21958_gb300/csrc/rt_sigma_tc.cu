@@ -33,7 +33,8 @@ constexpr int kTcBK = 64;                // q per stage: four MMAs of K = 16
 constexpr int kTcThreads = 256;
 constexpr int kTcABytes = kTcBM * kTcBK * 2;   // 16 KB
 constexpr int kTcBBytes = kTcBN * kTcBK * 2;   // 32 KB
-constexpr int kTcSmem = 2 * (kTcABytes + kTcBBytes) + 1024;
+constexpr int kTcStages = 4;
+constexpr int kTcSmem = kTcStages * (kTcABytes + kTcBBytes) + 1024;
 constexpr long long kSpinLimit = 1ll << 26;
 
 struct TcJob {
@@ -81,6 +82,15 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
       "l"(src), "r"(bytes), "r"(smem_u32(bar))
       : "memory");
 }
+
+// 16-byte asynchronous copy global -> shared; src_bytes = 0 zero-fills.
+__device__ __forceinline__ void cp_async16(void *dst, const void *src, uint32_t src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 // Shared-memory matrix descriptor: no swizzle, K-major canonical layout of
 // 8-row x 16-byte core matrices; lbo = byte distance of K-adjacent core
@@ -131,38 +141,45 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
 }
 
 // ----------------------------------------------------------------- kernel
+// X -> bf16 (same layout), the A operand of the GEMM
 template <typename TX>
+__global__ void k_to_bf16(const TX *__restrict__ X, uint32_t *__restrict__ Xb, int64_t n2) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n2; i += (int64_t)gridDim.x * blockDim.x)
+    Xb[i] = pack_bf16((float)X[2 * i], (float)X[2 * i + 1]);
+}
+
+// One (rows m0.., rays n0..) tile per CTA.  A (bf16 rows of X) arrives by
+// 16-byte cp.async copies straight into the core-matrix layout, B by one
+// cp.async.bulk per stage; kTcStages stages in flight.
+template <typename TS>
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_sigma_dense_tc(const ColDev *__restrict__ cols, const TcJob *__restrict__ jobs,
                      const int64_t *__restrict__ btile_off, const uint16_t *__restrict__ btiles,
-                     const float *__restrict__ gamma, int n_rhs, int64_t E, const TX *__restrict__ X,
-                     float *__restrict__ S, int *err) {
+                     const float *__restrict__ gamma, int n_rhs, int64_t E, const uint16_t *__restrict__ Xb,
+                     TS *__restrict__ S, int *err) {
   extern __shared__ __align__(1024) uint8_t tc_smem[];
   uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(tc_smem) + 1023) & ~uintptr_t(1023));
-  uint8_t *sA[2] = {base, base + kTcABytes};
-  uint8_t *sB[2] = {base + 2 * kTcABytes, base + 2 * kTcABytes + kTcBBytes};
-  __shared__ __align__(8) uint64_t bar_b[2], bar_mma[2];
+  __shared__ __align__(8) uint64_t bar_b[kTcStages], bar_mma[kTcStages];
   __shared__ uint32_t tmem_base;
-  __shared__ int s_fail;
+  auto sA = [&](int st) { return base + st * kTcABytes; };
+  auto sB = [&](int st) { return base + kTcStages * kTcABytes + st * kTcBBytes; };
 
   const TcJob job = jobs[blockIdx.x];
   const ColDev c = cols[job.col];
   const int nr = c.nr, nn = c.nn, nz = c.nz;
   const int M = n_rhs * nz;
-  const int n_valid = min(kTcBN, nr - job.n0);      // multiple of 16 (nr is)
-  const int nk = nr / 16;                            // MMA K-steps in total
+  const int n_valid = min(kTcBN, nr - job.n0);  // multiple of 16 (nr is)
+  const int nk = nr / 16;                        // MMA K-steps in total
   const int nchunk = (nr + kTcBK - 1) / kTcBK;
-  const int ntile_n = (nr + kTcBN - 1) / kTcBN;
-  const uint16_t *Bcol = btiles + btile_off[job.col];
+  const uint16_t *Bcol = btiles + btile_off[job.col] + (int64_t)(job.n0 / kTcBN) * nchunk * (kTcBN * kTcBK);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
   if (tid == 0) {
-    mbar_init(&bar_b[0], 1);
-    mbar_init(&bar_b[1], 1);
-    mbar_init(&bar_mma[0], 1);
-    mbar_init(&bar_mma[1], 1);
+    for (int i = 0; i < kTcStages; ++i) {
+      mbar_init(&bar_b[i], 1);
+      mbar_init(&bar_mma[i], 1);
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    s_fail = 0;
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
@@ -176,49 +193,56 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   const uint32_t tmem = tmem_base;
   const uint32_t idesc = tc_idesc(kTcBM, (n_valid + 15) / 16 * 16);
 
-  // rows handled by this thread in the A conversion: item = tid + 256*j,
-  // row = item % 128, 8-wide K group = item / 128 (j = 0..3)
-  int issued_chunks = 0;
-  bool ok = true;
-  for (int kc = 0; kc < nchunk && ok; ++kc) {
-    const int s = kc & 1;
-    if (kc >= 2) {  // stage s was read by the MMAs of chunk kc-2
-      if (!mbar_wait(&bar_mma[s], ((kc - 2) >> 1) & 1)) ok = false;
-    }
-    if (!ok) break;
-    if (tid == 0) {
-      mbar_expect_tx(&bar_b[s], kTcBBytes);
-      const int nt = job.n0 / kTcBN;
-      bulk_g2s(sB[s], Bcol + ((int64_t)nt * nchunk + kc) * (kTcBN * kTcBK), kTcBBytes, &bar_b[s]);
-    }
+  // A chunk = 128 rows x 8 groups of 8 bf16 (16 bytes).  Thread t copies row
+  // t/2, groups 2j + (t&1), j = 0..3: a lane pair reads one 32-byte sector.
+  const int arow = tid >> 1, akq = tid & 1;
+  const int agrow = job.m0 + arow;
+  const bool arow_ok = agrow < M;
+  int64_t arow_base = 0;
+  if (arow_ok) {
+    const int rhs = agrow / nz, p = agrow - rhs * nz;
+    arow_base = rhs * E + c.x_off + (int64_t)p * nr;
+  }
+  const uint32_t a_dst = (uint32_t)((arow >> 3) * 128 + (arow & 7) * 16);
+  auto issue = [&](int kc) {  // copies of chunk kc into stage kc % kTcStages
+    const int st = kc % kTcStages;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      const int item = tid + kTcThreads * j;
-      const int row = item & (kTcBM - 1), kq = item >> 7;
-      const int grow = job.m0 + row;
+      const int kq = 2 * j + akq;
       const int q0 = kc * kTcBK + kq * 8;
-      uint4 pk = make_uint4(0, 0, 0, 0);
-      if (grow < M && q0 < nr) {
-        const int rhs = grow / nz, p = grow - rhs * nz;
-        const TX *xr = X + rhs * E + c.x_off + (int64_t)p * nr + q0;
-        float f[8];
-#pragma unroll
-        for (int e = 0; e < 8; ++e) f[e] = (q0 + e < nr) ? (float)xr[e] : 0.f;
-        pk.x = pack_bf16(f[0], f[1]);
-        pk.y = pack_bf16(f[2], f[3]);
-        pk.z = pack_bf16(f[4], f[5]);
-        pk.w = pack_bf16(f[6], f[7]);
-      }
-      *reinterpret_cast<uint4 *>(sA[s] + kq * (kTcBM / 8) * 128 + (row >> 3) * 128 + (row & 7) * 16) = pk;
+      const bool in = arow_ok && q0 < nr;
+      cp_async16(sA(st) + kq * (kTcBM / 8) * 128 + a_dst, Xb + (in ? arow_base + q0 : 0), in ? 16u : 0u);
     }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
+    cp_async_commit();
     if (tid == 0) {
-      if (!mbar_wait(&bar_b[s], (kc >> 1) & 1)) {
-        s_fail = 1;
+      mbar_expect_tx(&bar_b[st], kTcBBytes);
+      bulk_g2s(sB(st), Bcol + (int64_t)kc * (kTcBN * kTcBK), kTcBBytes, &bar_b[st]);
+    }
+  };
+  const int pre = min(kTcStages - 1, nchunk);
+  for (int kc = 0; kc < pre; ++kc) issue(kc);
+  // Chunk kc: wait for its copies, MMAs by thread 0, then (while those run)
+  // refill the stage freed by chunk kc-1 with chunk kc+3.  A failed wait is
+  // made uniform by __syncthreads_or before anyone acts on it.
+  int committed = 0;  // chunks whose MMAs were committed
+  bool ok = true, bad = false;
+  for (int kc = 0; kc < nchunk; ++kc) {
+    const int st = kc % kTcStages;
+    const int later = min(nchunk - 1 - kc, kTcStages - 2);  // chunks issued after kc
+    if (later >= 2) cp_async_wait<2>();
+    else if (later == 1) cp_async_wait<1>();
+    else cp_async_wait<0>();
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    if (__syncthreads_or(bad ? 1 : 0)) {
+      ok = false;
+      break;
+    }
+    if (tid == 0) {
+      if (!mbar_wait(&bar_b[st], (kc / kTcStages) & 1)) {
+        bad = true;
       } else {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t a0 = smem_u32(sA[s]), b0 = smem_u32(sB[s]);
+        const uint32_t a0 = smem_u32(sA(st)), b0 = smem_u32(sB(st));
 #pragma unroll
         for (int ks = 0; ks < 4; ++ks) {
           if (kc * 4 + ks < nk) {
@@ -227,18 +251,28 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             tc_mma(tmem, ad, bd, idesc, (kc | ks) ? 1u : 0u);
           }
         }
-        tc_commit(&bar_mma[s]);
+        tc_commit(&bar_mma[st]);
       }
     }
-    __syncthreads();
-    if (s_fail) ok = false;
-    issued_chunks = kc + 1;
+    if (!bad) committed = kc + 1;  // thread 0's flag decides; others follow at the next barrier
+    const int nxt = kc + kTcStages - 1;
+    if (!bad && nxt < nchunk) {
+      // stage of chunk nxt was last read by the MMAs of chunk kc-1
+      if (kc >= 1 && !mbar_wait(&bar_mma[(kc - 1) % kTcStages], ((kc - 1) / kTcStages) & 1)) bad = true;
+      else issue(nxt);
+    }
   }
-  // drain: the last commit completes after every earlier MMA of this thread
+  if (__syncthreads_or(bad ? 1 : 0)) ok = false;
+  cp_async_wait<0>();
+  // drain: a commit completes after every earlier MMA of the issuing thread
   bool drained = true;
-  if (issued_chunks > 0) {
-    const int kl = issued_chunks - 1;
-    drained = mbar_wait(&bar_mma[kl & 1], (kl >> 1) & 1);
+  {
+    __shared__ int s_committed;
+    if (tid == 0) s_committed = committed;
+    __syncthreads();
+    const int kl = s_committed - 1;
+    if (kl >= 0) drained = mbar_wait(&bar_mma[kl % kTcStages], (kl / kTcStages) & 1);
+    drained = !__syncthreads_or(drained ? 0 : 1);
   }
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (ok && drained) {
@@ -248,7 +282,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const int grow = job.m0 + row;
     const bool valid_row = grow < M;
     const int rhs = valid_row ? grow / nz : 0, p = valid_row ? grow - rhs * nz : 0;
-    float *srow = S + rhs * E + c.x_off + (int64_t)p * nr;
+    TS *srow = S + rhs * E + c.x_off + (int64_t)p * nr;
     const float *grow_g = gamma + c.g_off + (int64_t)p * nn;
     for (int cc = 0; cc < kTcBN / 2; cc += 16) {
       const int col0 = half * (kTcBN / 2) + cc;
@@ -259,7 +293,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
           const int r = job.n0 + col0 + i;
-          if (col0 + i < n_valid) srow[r] = grow_g[r % nn] * v[i];
+          if (col0 + i < n_valid) srow[r] = (TS)(grow_g[r % nn] * v[i]);
         }
       }
     }
@@ -270,7 +304,6 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   __syncthreads();
   if (warp == 0)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcBN) : "memory");
-  (void)ntile_n;
 }
 
 // ------------------------------------------------------------ host side
@@ -329,8 +362,13 @@ int tc_prepare(rt_handle *h, const std::vector<double> &psiwT) {
   std::vector<TcJob> jobs;
   tc_build_tiles(h->h_cols, psiwT, tiles, offs);
   tc_build_jobs(h->h_cols, h->n_rhs, jobs);
-  h->n_tc_jobs = (int)jobs.size();
-  if (jobs.empty()) return 0;
+  // 16-byte cp.async of bf16 rows needs every row start on 8 elements
+  bool aligned = h->E % 8 == 0;
+  for (const ColDev &c : h->h_cols) aligned = aligned && c.x_off % 8 == 0;
+  h->n_tc_jobs = aligned ? (int)jobs.size() : 0;
+  if (h->n_tc_jobs == 0) return 0;
+  cudaError_t ex = cudaMalloc(&h->d_tc_xb, (size_t)h->E * h->n_rhs * 2);
+  if (ex != cudaSuccess) return (int)ex;
   cudaError_t e = cudaMalloc(&h->d_tc_tiles, tiles.size() * 2);
   if (e == cudaSuccess) e = cudaMemcpy(h->d_tc_tiles, tiles.data(), tiles.size() * 2, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMalloc(&h->d_tc_off, offs.size() * 8);
@@ -340,23 +378,36 @@ int tc_prepare(rt_handle *h, const std::vector<double> &psiwT) {
   return (int)e;
 }
 
-int launch_sigma_dense_tc(rt_handle *h, bool x_is_float, const void *x, float *S, cudaStream_t s) {
+// S is float32 scratch, or the float64 output when s_is_double (all-dense
+// batches computing Sigma alone).  X is first packed to bf16 (h->d_tc_xb).
+int launch_sigma_dense_tc(rt_handle *h, bool x_is_float, const void *x, void *S, bool s_is_double,
+                          cudaStream_t s) {
   if (h->n_tc_jobs == 0) return 0;
   static bool attr_set = false;
   if (!attr_set) {
-    cudaFuncSetAttribute(k_sigma_dense_tc<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
     cudaFuncSetAttribute(k_sigma_dense_tc<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
+    cudaFuncSetAttribute(k_sigma_dense_tc<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
     attr_set = true;
   }
-  if (x_is_float)
-    k_sigma_dense_tc<float><<<h->n_tc_jobs, kTcThreads, kTcSmem, s>>>(
-        h->d_cols, static_cast<const TcJob *>(h->d_tc_jobs), h->d_tc_off, h->d_tc_tiles, h->gam32, h->n_rhs,
-        h->E, static_cast<const float *>(x), S, h->d_err);
-  else
+  const int64_t n2 = h->E * h->n_rhs / 2;
+  const int g = (int)std::min<int64_t>((n2 + 255) / 256, 32 * 152);
+  if (x_is_float) k_to_bf16<float><<<g, 256, 0, s>>>(static_cast<const float *>(x), h->d_tc_xb, n2);
+  else k_to_bf16<double><<<g, 256, 0, s>>>(static_cast<const double *>(x), h->d_tc_xb, n2);
+  const TcJob *jobs = static_cast<const TcJob *>(h->d_tc_jobs);
+  const uint16_t *xb = reinterpret_cast<const uint16_t *>(h->d_tc_xb);
+  if (s_is_double)
     k_sigma_dense_tc<double><<<h->n_tc_jobs, kTcThreads, kTcSmem, s>>>(
-        h->d_cols, static_cast<const TcJob *>(h->d_tc_jobs), h->d_tc_off, h->d_tc_tiles, h->gam32, h->n_rhs,
-        h->E, static_cast<const double *>(x), S, h->d_err);
+        h->d_cols, jobs, h->d_tc_off, h->d_tc_tiles, h->gam32, h->n_rhs, h->E, xb, static_cast<double *>(S), h->d_err);
+  else
+    k_sigma_dense_tc<float><<<h->n_tc_jobs, kTcThreads, kTcSmem, s>>>(
+        h->d_cols, jobs, h->d_tc_off, h->d_tc_tiles, h->gam32, h->n_rhs, h->E, xb, static_cast<float *>(S), h->d_err);
   return (int)cudaGetLastError();
+}
+
+int tc_all_columns(const rt_handle *h) {
+  for (const ColDev &c : h->h_cols)
+    if (c.psi_off < 0 || c.nr % 16) return 0;
+  return h->n_tc_jobs > 0 ? 1 : 0;
 }
 
 }  // namespace rt

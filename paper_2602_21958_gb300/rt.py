@@ -47,7 +47,12 @@ class rt_info(C.Structure):
 
 
 EXPORTS = ("rt_create", "rt_create_batch", "rt_vector_length", "rt_apply", "rt_apply_noalloc",
-           "rt_solve", "rt_destroy", "rt_last_error", "rt_version")
+           "rt_autotune", "rt_solve", "rt_destroy", "rt_last_error", "rt_version")
+
+
+class rt_tune_info(C.Structure):
+    _fields_ = [("ray_block", C.c_int32), ("ahead", C.c_int32), ("sigma_points", C.c_int32),
+                ("from_cache", C.c_int32), ("ms_best", C.c_double), ("ms_default", C.c_double)]
 
 _lib = None
 
@@ -69,6 +74,8 @@ def load(path: Optional[str] = None) -> C.CDLL:
     lib.rt_vector_length.restype = C.c_int64
     lib.rt_apply.argtypes = [vp, C.c_int32, C.c_int32, vp, vp, vp]
     lib.rt_apply_noalloc.argtypes = [vp, C.c_int32, C.c_int32, vp, vp, vp]
+    lib.rt_autotune.argtypes = [vp, C.c_int32, C.POINTER(rt_tune_info), vp]
+    lib.rt_autotune.restype = C.c_int
     lib.rt_solve.argtypes = [vp, vp, vp, C.POINTER(rt_solve_opts), C.POINTER(rt_info), vp]
     lib.rt_destroy.argtypes = [vp]
     lib.rt_destroy.restype = None
@@ -186,6 +193,13 @@ class Handle:
         """rt_apply without any allocation: device tensors only, scratch in the
         library's static device array (see include/rt_gb300.h)."""
         _check(load().rt_apply_noalloc(self._h, op, int(bool(fp64)), _ptr(x), _ptr(y), _stream_ptr(stream)))
+
+    def rt_autotune(self, force: bool = False, stream=None) -> dict:
+        """Time the apply kernels' launch shapes on this problem and keep the fastest."""
+        t = rt_tune_info()
+        _check(load().rt_autotune(self._h, 1 if force else 0, C.byref(t), _stream_ptr(stream)))
+        return {"ray_block": t.ray_block, "ahead": t.ahead, "sigma_points": t.sigma_points,
+                "from_cache": bool(t.from_cache), "ms_best": t.ms_best, "ms_default": t.ms_default}
 
     def rt_solve(self, b, x, tol: float = 1e-11, tol_inner: float = 0.1, restart: Optional[int] = None,
                  max_outer: int = 50, use_x0: bool = False, stream=None, per_instance: bool = False,

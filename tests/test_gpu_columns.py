@@ -263,3 +263,29 @@ def test_repeated_solve_replays_identically(rt):
         outs.append(x.cpu().numpy().copy())
     assert np.array_equal(outs[0], outs[1])
     assert np.linalg.norm(outs[2] - outs[0]) <= 1e-10 * np.linalg.norm(outs[0])
+
+
+def test_autotune_picks_a_shape_and_caches_it(rt, tmp_path, monkeypatch):
+    """rt_autotune times the apply launch shapes, keeps the fastest (results
+    unchanged: parity with the oracle after tuning), and a second handle of the
+    same problem reads the choice from the RT_TUNE_CACHE file."""
+    cache = tmp_path / "tune.jsonl"
+    monkeypatch.setenv("RT_TUNE_CACHE", str(cache))
+    probs = [small_problems()[k] for k in ("crd", "r2_ragged", "minimal")]
+    h = rt.Handle(probs, n_rhs=2, precision=rt.RT_P_MIXED, max_restart=8)
+    t = h.rt_autotune(force=True)
+    assert t["ray_block"] in (64, 128, 256) and t["ahead"] in (4, 8, 16) and t["sigma_points"] in (4, 8, 0)
+    assert not t["from_cache"] and t["ms_best"] > 0 and t["ms_best"] <= t["ms_default"] + 1e-9
+    E = sum(p.n for p in probs)
+    x = W.random_vectors(2 * E, 1, 61)[0]
+    y = torch.empty(2 * E, dtype=torch.float64, device="cuda:0")
+    h.rt_apply(0, dev(x), y, fp64=True)
+    torch.cuda.synchronize()
+    for r in range(2):
+        ref = O.apply_A_batch(probs, x[r * E:(r + 1) * E])
+        a, _ = rel(y.cpu().numpy()[r * E:(r + 1) * E], ref)
+        assert a < FP64_TOL
+    h2 = rt.Handle(probs, n_rhs=2, precision=rt.RT_P_MIXED, max_restart=8)
+    t2 = h2.rt_autotune()
+    assert t2["from_cache"] and (t2["ray_block"], t2["ahead"], t2["sigma_points"]) == \
+        (t["ray_block"], t["ahead"], t["sigma_points"])

@@ -44,6 +44,7 @@ def emulated_sigma(p, x):
 
 CASES = {
     "nr64": lambda: W.two_level_column(np.logspace(-2, 2, 9), 4, 2, 8, "r2", 1e-2, 1.0),
+    "nr208_partial_chunk": lambda: W.two_level_column(np.logspace(-2, 3, 23), 4, 2, 26, "r2", 1e-3, 1.0),
     "nr320_ragged": lambda: W.two_level_column(np.logspace(-3, 3, 37), 8, 2, 20, "r2", 1e-3, 1.0),
     "nr1280": lambda: W.two_level_column(np.logspace(-4, 4, 150), 8, 2, 80, "r2", 1e-4, 1.0),
 }
