@@ -178,7 +178,7 @@ __device__ __noinline__ double cta_dots(const TL *V, int64_t ldv, int j, const T
 #pragma unroll
     for (int u = 0; u <= kDots; ++u) acc[u] += (double)part[u];
     block_sum<kDots + 1>(acc, red, outb);
-    if (threadIdx.x < cnt) h[i0 + threadIdx.x] = acc[threadIdx.x];
+    if (threadIdx.x < cnt) h[i0 + threadIdx.x] = outb[threadIdx.x];
     if (i0 == 0) nrm = acc[kDots];
   }
   __syncthreads();
@@ -460,8 +460,9 @@ __device__ __forceinline__ void givens_step(double *Hc, int ld, double *cs, doub
 }
 
 // One Arnoldi step on basis V[0..j] (TL) with w = V[j+1] unnormalised:
-// classical Gram-Schmidt with the DGKS test and a fused normalisation (see
-// k_solve).  Leaves h (+ h2) and returns ||w - V h||; bytes per element in bpe.
+// classical Gram-Schmidt with the DGKS test (second projection when
+// ||w - V h||^2 <= ||w||^2 / 2) and a fused normalisation (see k_solve).
+// Leaves h (+ h2) and returns ||w - V h||; bytes per element in bpe.
 template <typename TL>
 __device__ double arnoldi_orth(TL *V, int64_t ldv, int j, int64_t n, double *h, double *h2, TL *hf,
                                double *red, double *outb, double &bpe) {
@@ -484,6 +485,209 @@ __device__ double arnoldi_orth(TL *V, int64_t ldv, int j, int64_t n, double *h, 
     const TL inv = (TL)(hn > 0.0 ? 1.0 / hn : 0.0);
     for (int64_t k = threadIdx.x; k < n; k += blockDim.x) w[k] *= inv;
     bpe += sz * (3.0 * j + 10.0);
+  }
+  __syncthreads();
+  return hn;
+}
+
+// ------------------------------------------- inner cycles with a binary16 basis
+// The float32 inner GMRES cycles of the mixed solve keep their basis rows U_i
+// in IEEE binary16.  The rows have unit norm, so every entry is at most 1 in
+// magnitude; entries below 6e-8 flush to zero, an absolute error far below
+// what a preconditioner solved to a relative 0.1 can notice, and the 2^-11
+// relative rounding of the rest perturbs the Arnoldi relation by ~5e-4.  The
+// outer float64 FGMRES is exact for whatever direction the cycle returns, so
+// the final accuracy does not depend on it; the basis traffic halves.
+// Rows are ldv (a multiple of 32) long and their entries n..ldv-1 are kept
+// zero; the unnormalised direction w is float32 and its entries past n are
+// ignored.  Vector loops walk quads (4 consecutive entries): 8-byte loads of
+// U, 16-byte loads of w.
+constexpr int kQ = 2;  // quads per thread per loop iteration
+
+__device__ __forceinline__ void h4_to_f(uint2 raw, float (&f)[4]) {
+  const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&raw.x));
+  const float2 b = __half22float2(*reinterpret_cast<const __half2 *>(&raw.y));
+  f[0] = a.x;
+  f[1] = a.y;
+  f[2] = b.x;
+  f[3] = b.y;
+}
+
+__device__ __forceinline__ void st_h4(__half *p, const float (&f)[4]) {
+  const __half2 a = __floats2half2_rn(f[0], f[1]), b = __floats2half2_rn(f[2], f[3]);
+  uint2 raw;
+  raw.x = *reinterpret_cast<const uint32_t *>(&a);
+  raw.y = *reinterpret_cast<const uint32_t *>(&b);
+  *reinterpret_cast<uint2 *>(p) = raw;
+}
+
+// entries k..k+3 of w, zero where k + t >= n or the quad is a clamped duplicate
+__device__ __forceinline__ void ld_w4(const float *w, int64_t k, int64_t n, bool live, float (&f)[4]) {
+  const float4 v = *reinterpret_cast<const float4 *>(w + k);
+  f[0] = live && k < n ? v.x : 0.f;
+  f[1] = live && k + 1 < n ? v.y : 0.f;
+  f[2] = live && k + 2 < n ? v.z : 0.f;
+  f[3] = live && k + 3 < n ? v.w : 0.f;
+}
+
+// h[0..j] = U[0..j]^T w, returns ||w||^2 (float64 block sums)
+__device__ __noinline__ double cta_dots16(const __half *U, int64_t ldv, int j, const float *w, int64_t n,
+                                          double *h, double *red, double *outb) {
+  const int64_t nq = ldv / 4;
+  double nrm = 0.0;
+  constexpr int kWiden = 8;
+  for (int i0 = 0; i0 <= j; i0 += kDots) {
+    const int cnt = min(kDots, j + 1 - i0);
+    const __half *up[kDots];
+#pragma unroll
+    for (int u = 0; u < kDots; ++u) up[u] = U + (int64_t)min(i0 + u, j) * ldv;
+    double acc[kDots + 1];
+    float part[kDots + 1];
+#pragma unroll
+    for (int u = 0; u <= kDots; ++u) {
+      acc[u] = 0.0;
+      part[u] = 0.f;
+    }
+    int it = 0;
+    for (int64_t q0 = threadIdx.x; q0 < nq; q0 += (int64_t)kQ * blockDim.x) {
+      float wv[kQ][4];
+      uint2 raw[kDots][kQ];
+#pragma unroll
+      for (int e = 0; e < kQ; ++e) {
+        const int64_t q = q0 + (int64_t)e * blockDim.x;
+        const int64_t qc = min(q, nq - 1);
+        ld_w4(w, 4 * qc, n, q < nq, wv[e]);
+#pragma unroll
+        for (int u = 0; u < kDots; ++u) raw[u][e] = *reinterpret_cast<const uint2 *>(up[u] + 4 * qc);
+      }
+#pragma unroll
+      for (int u = 0; u < kDots; ++u)
+#pragma unroll
+        for (int e = 0; e < kQ; ++e) {
+          float f[4];
+          h4_to_f(raw[u][e], f);
+#pragma unroll
+          for (int t = 0; t < 4; ++t) part[u] = fmaf(f[t], wv[e][t], part[u]);
+        }
+#pragma unroll
+      for (int e = 0; e < kQ; ++e)
+#pragma unroll
+        for (int t = 0; t < 4; ++t) part[kDots] = fmaf(wv[e][t], wv[e][t], part[kDots]);
+      if (++it == kWiden) {
+        it = 0;
+#pragma unroll
+        for (int u = 0; u <= kDots; ++u) {
+          acc[u] += (double)part[u];
+          part[u] = 0.f;
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u <= kDots; ++u) acc[u] += (double)part[u];
+    block_sum<kDots + 1>(acc, red, outb);
+    if (threadIdx.x < cnt) h[i0 + threadIdx.x] = outb[threadIdx.x];
+    if (i0 == 0) nrm = acc[kDots];
+  }
+  __syncthreads();
+  return nrm;
+}
+
+// acc[e][t] += sum_{i < cnt} coef[i] U_i[quad q_e]; kDots rows' loads in flight
+__device__ __forceinline__ void axpy16(const __half *U, int64_t ldv, int cnt, const float *coef,
+                                       const int64_t (&qc)[kQ], float (&acc)[kQ][4]) {
+  for (int i0 = 0; i0 < cnt; i0 += kDots) {
+    uint2 raw[kDots][kQ];
+    float hu[kDots];
+#pragma unroll
+    for (int u = 0; u < kDots; ++u) {
+      const int i = min(i0 + u, cnt - 1);  // rows past cnt: re-read with a zero coefficient
+      hu[u] = (i0 + u < cnt) ? coef[i0 + u] : 0.f;
+      const __half *ui = U + (int64_t)i * ldv;
+#pragma unroll
+      for (int e = 0; e < kQ; ++e) raw[u][e] = *reinterpret_cast<const uint2 *>(ui + 4 * qc[e]);
+    }
+#pragma unroll
+    for (int u = 0; u < kDots; ++u)
+#pragma unroll
+      for (int e = 0; e < kQ; ++e) {
+        float f[4];
+        h4_to_f(raw[u][e], f);
+#pragma unroll
+        for (int t = 0; t < 4; ++t) acc[e][t] = fmaf(hu[u], f[t], acc[e][t]);
+      }
+  }
+}
+
+// r = (w - U[0..j] h) * scale.  out16: write r to that binary16 row (zero past
+// n), else r overwrites w.  Returns ||r||^2 when want_norm (else 0).
+__device__ __noinline__ double cta_update16(const __half *U, int64_t ldv, int j, float *w, int64_t n,
+                                            const double *h, double scale, __half *out16, bool want_norm,
+                                            float *hf, double *red, double *outb) {
+  stage_coef<float>(h, j + 1, -1.0, hf);
+  const int64_t nq = ldv / 4;
+  const float sc = (float)scale;
+  double a[1] = {0.0};
+  for (int64_t q0 = threadIdx.x; q0 < nq; q0 += (int64_t)kQ * blockDim.x) {
+    int64_t qc[kQ];
+    bool live[kQ];
+    float acc[kQ][4];
+#pragma unroll
+    for (int e = 0; e < kQ; ++e) {
+      const int64_t q = q0 + (int64_t)e * blockDim.x;
+      live[e] = q < nq;
+      qc[e] = min(q, nq - 1);
+      ld_w4(w, 4 * qc[e], n, live[e], acc[e]);
+    }
+    axpy16(U, ldv, j + 1, hf, qc, acc);
+    float part = 0.f;
+#pragma unroll
+    for (int e = 0; e < kQ; ++e) {
+      const int64_t k = 4 * qc[e];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        acc[e][t] = k + t < n ? acc[e][t] * sc : 0.f;
+        part = fmaf(acc[e][t], acc[e][t], part);
+      }
+      if (live[e]) {
+        if (out16) st_h4(out16 + k, acc[e]);
+        else *reinterpret_cast<float4 *>(w + k) = make_float4(acc[e][0], acc[e][1], acc[e][2], acc[e][3]);
+      }
+    }
+    if (want_norm) a[0] += (double)part;
+  }
+  if (want_norm) block_sum<1>(a, red, outb);
+  else __syncthreads();
+  return want_norm ? a[0] : 0.0;
+}
+
+// One Arnoldi step of an inner cycle: w (float32) against U[0..j] (binary16),
+// the normalised result written to U[j+1].  Classical Gram-Schmidt; a second
+// projection only when ||w - U h||^2 <= 1e-4 ||w||^2.  On these operators the
+// DGKS bound of 1/2 is crossed at nearly every step (w = A u keeps most of u),
+// which would double the traffic, while a preconditioner solved to 0.1 needs
+// the basis orthogonal only to ~1e-3: single-pass loss measured ~2e-5.
+// Leaves h (+ h2), returns ||w - U h||; bytes per element in bpe.
+__device__ double arnoldi16(__half *U, int64_t ldv, int j, float *w, int64_t n, double *h, double *h2,
+                            float *hf, double *red, double *outb, double &bpe) {
+  __half *out = U + (int64_t)(j + 1) * ldv;
+  const double ww = cta_dots16(U, ldv, j, w, n, h, red, outb);
+  double hh = 0.0;
+  for (int i = 0; i <= j; ++i) hh += h[i] * h[i];
+  bpe += 2.0 * (j + 1) + 4.0;
+  double hn;
+  if (ww - hh > 1e-4 * ww) {
+    hn = sqrt(ww - hh);
+    cta_update16(U, ldv, j, w, n, h, hn > 0.0 ? 1.0 / hn : 0.0, out, false, hf, red, outb);
+    for (int i = threadIdx.x; i <= j; i += blockDim.x) h2[i] = 0.0;
+    bpe += 2.0 * (j + 1) + 6.0;
+  } else {
+    cta_update16(U, ldv, j, w, n, h, 1.0, nullptr, false, hf, red, outb);
+    const double w1 = cta_dots16(U, ldv, j, w, n, h2, red, outb);
+    double hh2 = 0.0;
+    for (int i = 0; i <= j; ++i) hh2 += h2[i] * h2[i];
+    hn = sqrt(fmax(w1 - hh2, 0.0));
+    cta_update16(U, ldv, j, w, n, h2, hn > 0.0 ? 1.0 / hn : 0.0, out, false, hf, red, outb);
+    bpe += 6.0 * (j + 1) + 18.0;
   }
   __syncthreads();
   return hn;
@@ -520,6 +724,7 @@ __global__ void __launch_bounds__(kNT, 1) k_solve_nested(SolveParams p) {
   uint8_t *slot = reinterpret_cast<uint8_t *>(p.V) + (int64_t)blockIdx.x * p.cap;
   double *S64 = p.S + (int64_t)blockIdx.x * p.ld;
   float *S32 = reinterpret_cast<float *>(S64);
+  float *W32 = S32 + p.ld;  // inner cycles: the new direction (second half of the float64 scratch)
   double *Hbase = p.H + (int64_t)blockIdx.x * p.hld;
   double *h = hbuf;
   double *h2 = hbuf + kMaxM + 8;
@@ -532,13 +737,13 @@ __global__ void __launch_bounds__(kNT, 1) k_solve_nested(SolveParams p) {
     const int64_t n = (int64_t)c.nz * c.nr;
     const int64_t ldv = (n + 31) / 32 * 32;
     const int m_in = min(p.m_in, kMaxM);
-    // slot: Vout [(kout+1) ldv] double | Z [kout ldv] float | U [(m_in+1) ldv] float
+    // slot: Vout [(kout+1) ldv] double | Z [kout ldv] float | U [(m_in+1) ldv] binary16
     const int64_t per = p.cap / ldv;  // bytes per vector element available
-    const int64_t kfit = (per - 8 - 4 * (int64_t)(m_in + 1)) / 12;
+    const int64_t kfit = (per - 8 - 2 * (int64_t)(m_in + 1)) / 12;
     const int kout = (int)(kfit < (int64_t)min(p.m, kMaxM) ? kfit : (int64_t)min(p.m, kMaxM));
     double *Vo = reinterpret_cast<double *>(slot);
     float *Z = reinterpret_cast<float *>(Vo + (int64_t)(kout + 1) * ldv);
-    float *U = Z + (int64_t)kout * ldv;
+    __half *U = reinterpret_cast<__half *>(Z + (int64_t)kout * ldv);
     double *Ho = Hbase;
     double *cso = Ho + (int64_t)(kout + 1) * kout, *sno = cso + (kout + 1), *go = sno + (kout + 1);
     double *Hi = go + (kout + 2);
@@ -589,29 +794,30 @@ __global__ void __launch_bounds__(kNT, 1) k_solve_nested(SolveParams p) {
         const double *vi = Vo + (int64_t)i * ldv;
         float *zi = Z + (int64_t)i * ldv;
         double a0[1] = {0.0};
-        for (int64_t k = threadIdx.x; k < n; k += blockDim.x) {
-          const float u = (float)vi[k];
-          U[k] = u;
-          a0[0] += (double)u * (double)u;
-        }
+        for (int64_t k = threadIdx.x; k < n; k += blockDim.x) a0[0] += vi[k] * vi[k];
         block_sum<1>(a0, red, outb);
         const double beta = sqrt(a0[0]);
         {
-          const float inv = (float)(1.0 / beta);
-          for (int64_t k = threadIdx.x; k < n; k += blockDim.x) U[k] *= inv;
+          const double inv = beta > 0.0 ? 1.0 / beta : 0.0;
+          for (int64_t q = threadIdx.x; q < ldv / 4; q += blockDim.x) {
+            float f[4];
+#pragma unroll
+            for (int t = 0; t < 4; ++t) f[t] = 4 * q + t < n ? (float)(vi[4 * q + t] * inv) : 0.f;
+            st_h4(U + 4 * q, f);
+          }
           __syncthreads();
         }
-        bpe += 8.0 + 4.0 + 8.0;
+        bpe += 8.0 + 8.0 + 2.0;
         if (threadIdx.x == 0) gi[0] = beta;
         int jdone = 0;
         for (int j = 0; j < m_in; ++j) {
-          float *uj = U + (int64_t)j * ldv;
-          float *w = U + (int64_t)(j + 1) * ldv;
-          sigma_column<float, float>(c, p.t32, uj, S32, reinterpret_cast<float *>(sm), 8 * kSigBuf);
-          sweep_column<float, float, float, 4>(c, p.t32, p.cm, S32, nullptr, uj, nullptr, w, kOutAminus, false);
+          const __half *uj = U + (int64_t)j * ldv;
+          sigma_column<float, __half>(c, p.t32, uj, S32, reinterpret_cast<float *>(sm), 8 * kSigBuf);
+          sweep_column<float, __half, float, 4>(c, p.t32, p.cm, S32, nullptr, uj, nullptr, W32, kOutAminus,
+                                                 false);
           __syncthreads();
-          bpe += 20.0;
-          const double hn = arnoldi_orth<float>(U, ldv, j, n, h, h2, hf32, red, outb, bpe);
+          bpe += 16.0;
+          const double hn = arnoldi16(U, ldv, j, W32, n, h, h2, hf32, red, outb, bpe);
           if (threadIdx.x == 0) givens_step(Hi, m_in + 1, csi, sni, gi, j, h, h2, hn, s_val);
           __syncthreads();
           const double est = s_val[0], den = s_val[1];
@@ -623,19 +829,23 @@ __global__ void __launch_bounds__(kNT, 1) k_solve_nested(SolveParams p) {
         inner_total += jdone;
         tri_solve(Hi, m_in + 1, gi, jdone, ybuf);
         stage_coef<float>(ybuf, jdone, 1.0, hf32);
-        for (int64_t k0 = threadIdx.x; k0 < n; k0 += (int64_t)kU * blockDim.x) {
-          float d[kU];
+        for (int64_t q0 = threadIdx.x; q0 < ldv / 4; q0 += (int64_t)kQ * blockDim.x) {
+          int64_t qc[kQ];
+          float d[kQ][4];
 #pragma unroll
-          for (int e = 0; e < kU; ++e) d[e] = 0.f;
-          axpy_block<float>(U, ldv, jdone, hf32, k0, n, d);
+          for (int e = 0; e < kQ; ++e) {
+            qc[e] = min(q0 + (int64_t)e * blockDim.x, ldv / 4 - 1);
 #pragma unroll
-          for (int e = 0; e < kU; ++e) {
-            const int64_t k = k0 + (int64_t)e * blockDim.x;
-            if (k < n) zi[k] = d[e];
+            for (int t = 0; t < 4; ++t) d[e][t] = 0.f;
           }
+          axpy16(U, ldv, jdone, hf32, qc, d);
+#pragma unroll
+          for (int e = 0; e < kQ; ++e)
+            if (q0 + (int64_t)e * blockDim.x < ldv / 4)
+              *reinterpret_cast<float4 *>(zi + 4 * qc[e]) = make_float4(d[e][0], d[e][1], d[e][2], d[e][3]);
         }
         __syncthreads();
-        bpe += 4.0 * (jdone + 1);
+        bpe += 2.0 * jdone + 4.0;
         // ---- outer: w = A z_i in float64, orthogonalise in float64 ----------
         double *w = Vo + (int64_t)(i + 1) * ldv;
         sigma_column<double, float>(c, p.t64, zi, S64, sm, 4 * kSigBuf);

@@ -7,6 +7,7 @@
 // space-based ordering of Sec. 3.1 (point, direction, frequency fastest).
 #pragma once
 #include <cstdint>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 namespace rt {
@@ -84,6 +85,14 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double *red, double *
 }
 
 template <typename T> __device__ __forceinline__ T to(double v) { return (T)v; }
+template <typename T> __device__ __forceinline__ T to(float v) { return (T)v; }
+template <typename T> __device__ __forceinline__ T to(__half v) { return (T)__half2float(v); }
+__device__ __forceinline__ float as_f32(float v) { return v; }
+__device__ __forceinline__ float as_f32(double v) { return (float)v; }
+__device__ __forceinline__ float as_f32(__half v) { return __half2float(v); }
+__device__ __forceinline__ double as_f64(double v) { return v; }
+__device__ __forceinline__ double as_f64(float v) { return (double)v; }
+__device__ __forceinline__ double as_f64(__half v) { return (double)__half2float(v); }
 
 // ------------------------------------------------------------------ Sigma
 // S_p = Gamma_p Psi W X_p for every point of one column (eq. Sigma), the
@@ -364,15 +373,15 @@ __device__ double sweep_ray(const ColDev &c, const Tables<T> &tb, const Common &
   auto emit = [&](int i, T I) {
     const int64_t k = (int64_t)i * nr + r;
     if (out == kOutResid) {
-      const double v = bv[k] - (double)x[k] + (double)I;
+      const double v = bv[k] - as_f64(x[k]) + (double)I;
       y[k] = (TY)v;
       ss += v * v;
     } else if (out == kOutI) {
       y[k] = (TY)I;
-    } else if (sizeof(TY) == 4 && sizeof(TX) == 4) {
-      y[k] = (TY)((float)x[k] - (float)I);   // float pipeline: no float64 op
+    } else if (sizeof(TY) == 4 && sizeof(TX) <= 4) {
+      y[k] = (TY)(as_f32(x[k]) - (float)I);   // float pipeline: no float64 op
     } else {
-      y[k] = (TY)((double)x[k] - (double)I);
+      y[k] = (TY)(as_f64(x[k]) - (double)I);
     }
   };
   T Su = src(i0);
