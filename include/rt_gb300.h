@@ -151,11 +151,11 @@ int rt_apply(rt_handle *h, int32_t op, int32_t fp64, const double *x, double *y,
 /* ---- launch-shape tuning ----------------------------------------------- */
 typedef struct rt_tune_info {
   int32_t ray_block;     /* rays per sweep tile (threads per CTA): 64, 128 or 256        */
-  int32_t ahead;         /* depth points of loads issued ahead per ray: 4, 8 or 16       */
+  int32_t ahead;         /* depth points per load chunk of a ray (two chunks in flight): 2, 4 or 8 */
   int32_t sigma_points;  /* cap on points per Sigma tile: 4, 8, or 0 (as many as fit)    */
   int32_t from_cache;    /* 1 if read from the RT_TUNE_CACHE file                       */
   double ms_best;        /* rt_apply(RT_OP_A) time of the choice                         */
-  double ms_default;     /* time of the default shape (128, 8, 0); 0 if from cache       */
+  double ms_default;     /* time of the default shape (128, 4, 0); 0 if from cache       */
 } rt_tune_info;
 
 /* Pick the launch shapes of the batched apply kernels (the sweep tile width and

@@ -833,7 +833,7 @@ int rt_autotune(rt_handle *h, int32_t flags, rt_tune_info *out, void *stream) {
   cudaEventCreate(&e1);
   double best = 1e300, first = 0;
   rt::Tune best_t = h->tune;
-  const int rbs[3] = {64, 128, 256}, ahs[3] = {4, 8, 16}, pts[3] = {4, 8, 0};
+  const int rbs[3] = {64, 128, 256}, ahs[3] = {2, 4, 8}, pts[3] = {4, 8, 0};
   int rc = RT_OK;
   for (int a = 0; a < 3 && rc == RT_OK; ++a)
     for (int b = 0; b < 3 && rc == RT_OK; ++b)

@@ -68,11 +68,11 @@ static void sweep_launch(rt_handle *h, int nsw, const Common &cm, const Tables<T
                                              inflow)
   const int rb = h->tune.ray_block, ah = h->tune.ahead;
   if (rb == 64) {
-    if (ah == 4) RT_SW(64, 4); else if (ah == 16) RT_SW(64, 16); else RT_SW(64, 8);
+    if (ah == 2) RT_SW(64, 2); else if (ah == 8) RT_SW(64, 8); else RT_SW(64, 4);
   } else if (rb == 256) {
-    if (ah == 4) RT_SW(256, 4); else if (ah == 16) RT_SW(256, 16); else RT_SW(256, 8);
+    if (ah == 2) RT_SW(256, 2); else if (ah == 8) RT_SW(256, 8); else RT_SW(256, 4);
   } else {
-    if (ah == 4) RT_SW(128, 4); else if (ah == 16) RT_SW(128, 16); else RT_SW(128, 8);
+    if (ah == 2) RT_SW(128, 2); else if (ah == 8) RT_SW(128, 8); else RT_SW(128, 4);
   }
 #undef RT_SW
 }

@@ -119,6 +119,7 @@ struct SolveParams {
 };
 
 constexpr int kU = 4;  // independent elements per thread in the vector loops
+constexpr int kRwCache = 128 * 128;  // floats of frequency kernel kept in shared memory by the mixed solve
 
 __device__ __forceinline__ double cta_norm2(const double *v, int64_t n, double *red, double *outb) {
   double a[1] = {0.0};
@@ -320,7 +321,7 @@ __global__ void __launch_bounds__(kNT, 1) k_solve(SolveParams p) {
         bpe += 0.0;
       } else {
         sigma_column<double, double>(c, p.t64, x, S64, sm, 4 * kSigBuf);
-        double a[1] = {sweep_column<double, double, double>(c, p.t64, p.cm, S64, nullptr, x, bv, S64,
+        double a[1] = {sweep_column<double, double, double, 2>(c, p.t64, p.cm, S64, nullptr, x, bv, S64,
                                                             kOutResid, false)};
         block_sum<1>(a, red, outb);
         rn = sqrt(a[0]);
@@ -342,7 +343,7 @@ __global__ void __launch_bounds__(kNT, 1) k_solve(SolveParams p) {
         TL *vj = Vslot + (int64_t)j * ldv;
         TL *w = Vslot + (int64_t)(j + 1) * ldv;
         sigma_column<TL, TL>(c, tl, vj, SL, reinterpret_cast<TL *>(sm), 4 * kSigBuf * (int)(8 / sizeof(TL)));
-        sweep_column<TL, TL, TL>(c, tl, p.cm, SL, nullptr, vj, nullptr, w, kOutAminus, false);
+        sweep_column<TL, TL, TL, sizeof(TL) == 8 ? 2 : 4>(c, tl, p.cm, SL, nullptr, vj, nullptr, w, kOutAminus, false);
         __syncthreads();
         bpe += 5.0 * sz;  // v, S, S, v, w
         const double ww = cta_dots<TL>(Vslot, ldv, j, w, n, h, red, outb);
@@ -436,11 +437,19 @@ __global__ void __launch_bounds__(kNT, 1) k_solve(SolveParams p) {
 // ---------------------------------------------------------------- mixed solve
 // Givens update of column j of a Hessenberg matrix stored column-major with
 // leading dimension ld (thread 0 only); returns |g_{j+1}| and den via s_val.
+// shifted: the Arnoldi step ran on K = Id - A (same Krylov space), so the
+// column of A's Hessenberg is e_j - (h + h2) with subdiagonal -hn.
 __device__ __forceinline__ void givens_step(double *Hc, int ld, double *cs, double *sn, double *g, int j,
-                                            const double *h, const double *h2, double hn, double *s_val) {
+                                            const double *h, const double *h2, double hn, double *s_val,
+                                            bool shifted = false) {
   double *col = Hc + (int64_t)j * ld;
-  for (int i = 0; i <= j; ++i) col[i] = h[i] + h2[i];
-  col[j + 1] = hn;
+  if (shifted) {
+    for (int i = 0; i <= j; ++i) col[i] = (i == j ? 1.0 : 0.0) - (h[i] + h2[i]);
+    col[j + 1] = -hn;
+  } else {
+    for (int i = 0; i <= j; ++i) col[i] = h[i] + h2[i];
+    col[j + 1] = hn;
+  }
   for (int i = 0; i < j; ++i) {
     const double t0 = cs[i] * col[i] + sn[i] * col[i + 1];
     col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
@@ -721,6 +730,7 @@ __global__ void __launch_bounds__(kNT, 1) k_solve_nested(SolveParams p) {
   __shared__ double hf64[kMaxM + 8];
   __shared__ int s_q;
   __shared__ double s_val[4];
+  __shared__ float rw_s[kRwCache];  // float32 frequency kernel of the current column
   uint8_t *slot = reinterpret_cast<uint8_t *>(p.V) + (int64_t)blockIdx.x * p.cap;
   double *S64 = p.S + (int64_t)blockIdx.x * p.ld;
   float *S32 = reinterpret_cast<float *>(S64);
@@ -751,6 +761,13 @@ __global__ void __launch_bounds__(kNT, 1) k_solve_nested(SolveParams p) {
     const double *bv = p.b + (p.b_shared ? 0 : rhs * p.E) + c.x_off;
     double *x = p.x + rhs * p.E + c.x_off;
     const double bn = sqrt(cta_norm2(bv, n, red, outb));
+    // stage the float32 frequency kernel of this column (dense, up to 128 x 128)
+    const float *rw_c = nullptr;
+    if (!c.rdiag && c.psi_off < 0 && c.nn * c.nn <= kRwCache) {
+      for (int k = threadIdx.x; k < c.nn * c.nn; k += blockDim.x) rw_s[k] = p.t32.RwT[c.r_off + k];
+      __syncthreads();
+      rw_c = rw_s;
+    }
     if (!p.use_x0) {
       for (int64_t k = threadIdx.x; k < n; k += blockDim.x) x[k] = 0.0;
       __syncthreads();
@@ -773,7 +790,7 @@ __global__ void __launch_bounds__(kNT, 1) k_solve_nested(SolveParams p) {
         rsrc = bv;
       } else {
         sigma_column<double, double>(c, p.t64, x, S64, sm, 4 * kSigBuf);
-        double a[1] = {sweep_column<double, double, double>(c, p.t64, p.cm, S64, nullptr, x, bv, S64,
+        double a[1] = {sweep_column<double, double, double, 2>(c, p.t64, p.cm, S64, nullptr, x, bv, S64,
                                                             kOutResid, false)};
         block_sum<1>(a, red, outb);
         rn = sqrt(a[0]);
@@ -812,13 +829,14 @@ __global__ void __launch_bounds__(kNT, 1) k_solve_nested(SolveParams p) {
         int jdone = 0;
         for (int j = 0; j < m_in; ++j) {
           const __half *uj = U + (int64_t)j * ldv;
-          sigma_column<float, __half>(c, p.t32, uj, S32, reinterpret_cast<float *>(sm), 8 * kSigBuf);
-          sweep_column<float, __half, float, 4>(c, p.t32, p.cm, S32, nullptr, uj, nullptr, W32, kOutAminus,
-                                                 false);
+          sigma_column<float, __half>(c, p.t32, uj, S32, reinterpret_cast<float *>(sm), 8 * kSigBuf, rw_c);
+          // Arnoldi on K = Lambda Sigma (A = Id - K, same Krylov space): the
+          // sweep emits K u_j and needs no read of u_j
+          sweep_column<float, __half, float, 4>(c, p.t32, p.cm, S32, nullptr, uj, nullptr, W32, kOutI, false);
           __syncthreads();
-          bpe += 16.0;
+          bpe += 14.0;
           const double hn = arnoldi16(U, ldv, j, W32, n, h, h2, hf32, red, outb, bpe);
-          if (threadIdx.x == 0) givens_step(Hi, m_in + 1, csi, sni, gi, j, h, h2, hn, s_val);
+          if (threadIdx.x == 0) givens_step(Hi, m_in + 1, csi, sni, gi, j, h, h2, hn, s_val, true);
           __syncthreads();
           const double est = s_val[0], den = s_val[1];
           jdone = j + 1;
@@ -849,7 +867,7 @@ __global__ void __launch_bounds__(kNT, 1) k_solve_nested(SolveParams p) {
         // ---- outer: w = A z_i in float64, orthogonalise in float64 ----------
         double *w = Vo + (int64_t)(i + 1) * ldv;
         sigma_column<double, float>(c, p.t64, zi, S64, sm, 4 * kSigBuf);
-        sweep_column<double, float, double, 4>(c, p.t64, p.cm, S64, nullptr, zi, nullptr, w, kOutAminus, false);
+        sweep_column<double, float, double, 2>(c, p.t64, p.cm, S64, nullptr, zi, nullptr, w, kOutAminus, false);
         __syncthreads();
         bpe += 4.0 + 8.0 + 8.0 + 4.0 + 8.0;
         const double hn = arnoldi_orth<double>(Vo, ldv, i, n, h, h2, hf64, red, outb, bpe);

@@ -29,7 +29,7 @@ struct Workspace {
 // Launch shapes of the apply kernels (rt_autotune)
 struct Tune {
   int ray_block = 128;   // rays per sweep tile (threads per CTA): 64, 128, 256
-  int ahead = 8;         // depth points of loads in flight per ray: 4, 8, 16
+  int ahead = 4;         // depth points per load chunk of a ray (2 chunks in flight): 2, 4, 8
   int sigma_pts = 0;     // cap on points per Sigma tile: 4, 8, or 0 (as many as fit)
   double ms = 0.0;       // apply time measured for this choice
   int from_cache = 0;

@@ -211,12 +211,13 @@ __host__ __device__ inline bool sigma_warp_ok(const ColDev &c) {
 // so the loads of many points are in flight at once.
 template <typename T, typename TX, int KR>
 __device__ void sigma_points_warp(const ColDev &c, const Tables<T> &tb, const TX *__restrict__ X,
-                                  T *__restrict__ S, int p_begin, int p_end, T *wm, T *wz) {
+                                  T *__restrict__ S, int p_begin, int p_end, T *wm, T *wz,
+                                  const T *rw_cached = nullptr) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int nd = c.nd, nn = c.nn, nr = c.nr, rp = c.rp;
   const T *Uw = tb.Uw + c.u_off;
   const T *Ul = tb.Ul + c.u_off;
-  const T *Rw = tb.RwT + c.r_off;
+  const T *Rw = rw_cached ? rw_cached : tb.RwT + c.r_off;
   const T *gam = tb.gamma + c.g_off;
   for (int p = p_begin + warp; p < p_end; p += nw) {
     const TX *xp = X + (int64_t)p * nr;
@@ -320,15 +321,16 @@ __host__ __device__ inline int sigma_points_per_block(const ColDev &c, int max_p
 // Every point of one column, block by block (one CTA).
 // smbuf holds cap elements of T (cap >= 2*kSigBuf); warps take equal shares
 // of it when the per-warp form fits, else it is split into the two block buffers.
+// rw_cached: this column's RwT already staged in shared memory, or nullptr.
 template <typename T, typename TX>
 __device__ __noinline__ void sigma_column(const ColDev &c, const Tables<T> &tb, const TX *__restrict__ X,
-                             T *__restrict__ S, T *smbuf, int cap) {
+                             T *__restrict__ S, T *smbuf, int cap, const T *rw_cached = nullptr) {
   const int nw = blockDim.x >> 5;
   const int per_warp = cap / nw / 2;
   if (sigma_warp_ok(c) && c.rp * c.nn <= per_warp) {
     T *wm = smbuf + (threadIdx.x >> 5) * 2 * per_warp;
-    if (c.rp <= 2) sigma_points_warp<T, TX, 2>(c, tb, X, S, 0, c.nz, wm, wm + per_warp);
-    else sigma_points_warp<T, TX, 8>(c, tb, X, S, 0, c.nz, wm, wm + per_warp);
+    if (c.rp <= 2) sigma_points_warp<T, TX, 2>(c, tb, X, S, 0, c.nz, wm, wm + per_warp, rw_cached);
+    else sigma_points_warp<T, TX, 8>(c, tb, X, S, 0, c.nz, wm, wm + per_warp, rw_cached);
     __syncthreads();
     return;
   }
@@ -365,54 +367,78 @@ __device__ double sweep_ray(const ColDev &c, const Tables<T> &tb, const Common &
   const int cls = cm.dir_cls[c.d_off + d];
   const int step = up ? -1 : 1;
   const int i0 = up ? nz - 1 : 0;
+  const bool want_x = out != kOutI;
   T Iu = 0;
   if (inflow) Iu = (T)(up ? cm.I_bot[c.in_off + f] : cm.I_top[c.in_off + f]);
   auto src = [&](int i) -> T {
     return tsrc ? (T)tsrc[(int64_t)i * nn + f] : S[(int64_t)i * nr + r];
   };
-  auto emit = [&](int i, T I) {
+  // y at point i from the intensity I and the prefetched x value xi
+  auto emit = [&](int i, T I, TX xi) {
     const int64_t k = (int64_t)i * nr + r;
     if (out == kOutResid) {
-      const double v = bv[k] - as_f64(x[k]) + (double)I;
+      const double v = bv[k] - as_f64(xi) + (double)I;
       y[k] = (TY)v;
       ss += v * v;
     } else if (out == kOutI) {
       y[k] = (TY)I;
     } else if (sizeof(TY) == 4 && sizeof(TX) <= 4) {
-      y[k] = (TY)(as_f32(x[k]) - (float)I);   // float pipeline: no float64 op
+      y[k] = (TY)(as_f32(xi) - (float)I);  // float pipeline: no float64 op
     } else {
-      y[k] = (TY)(as_f64(x[k]) - (double)I);
+      y[k] = (TY)(as_f64(xi) - (double)I);
+    }
+  };
+  // loads of the points i+step .. i+cnt*step (cnt <= kAhead); indices past
+  // the column are clamped to its last point (the values are not used)
+  auto load = [&](int i, int cnt, T (&e)[kAhead], T (&a)[kAhead], T (&b)[kAhead], T (&sc)[kAhead],
+                  TX (&xv)[kAhead]) {
+#pragma unroll
+    for (int u = 0; u < kAhead; ++u) {
+      int ic = i + (u + 1) * step;
+      ic = u < cnt ? ic : i0 + (nz - 1) * step;
+      const int layer = up ? ic : ic - 1;  // layer between ic and its upwind point
+      const int64_t ci = ((int64_t)layer * ncls + cls) * nn + f;
+      e[u] = E[ci];
+      a[u] = A[ci];
+      b[u] = B[ci];
+      sc[u] = src(ic);
+      xv[u] = want_x ? x[(int64_t)ic * nr + r] : TX(0);
     }
   };
   T Su = src(i0);
-  emit(i0, Iu);
-  // march the remaining nz-1 points in chunks with loads issued ahead
+  emit(i0, Iu, want_x ? x[(int64_t)i0 * nr + r] : TX(0));
+  // chunks of kAhead points; the next chunk's loads are issued before the
+  // current chunk's recurrence (2 kAhead points of loads in flight)
+  T e0[kAhead], a0[kAhead], b0[kAhead], s0[kAhead];
+  TX x0[kAhead];
   int i = i0;
+  int cnt = min(kAhead, nz - 1);
+  if (cnt > 0) load(i, cnt, e0, a0, b0, s0, x0);
   for (int done = 1; done < nz; done += kAhead) {
-    const int cnt = min(kAhead, nz - done);
-    T e[kAhead], a[kAhead], b[kAhead], sc[kAhead];
+    const int inext = i + cnt * step;
+    const int cnext = min(kAhead, nz - done - cnt);
+    T e1[kAhead], a1[kAhead], b1[kAhead], s1[kAhead];
+    TX x1[kAhead];
+    if (cnext > 0) load(inext, cnext, e1, a1, b1, s1, x1);
 #pragma unroll
     for (int u = 0; u < kAhead; ++u) {
       if (u < cnt) {
-        const int ic = i + (u + 1) * step;
-        const int layer = up ? ic : ic - 1;  // layer between ic and its upwind point
-        const int64_t ci = ((int64_t)layer * ncls + cls) * nn + f;
-        e[u] = E[ci];
-        a[u] = A[ci];
-        b[u] = B[ci];
-        sc[u] = src(ic);
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < kAhead; ++u) {
-      if (u < cnt) {
-        const T Ic = fma(e[u], Iu, fma(a[u], Su, b[u] * sc[u]));
-        emit(i + (u + 1) * step, Ic);
+        const T Ic = fma(e0[u], Iu, fma(a0[u], Su, b0[u] * s0[u]));
+        emit(i + (u + 1) * step, Ic, x0[u]);
         Iu = Ic;
-        Su = sc[u];
+        Su = s0[u];
       }
     }
-    i += cnt * step;
+#pragma unroll
+    for (int u = 0; u < kAhead; ++u) {
+      e0[u] = e1[u];
+      a0[u] = a1[u];
+      b0[u] = b1[u];
+      s0[u] = s1[u];
+      x0[u] = x1[u];
+    }
+    i = inext;
+    cnt = cnext;
   }
   return out == kOutResid ? ss : 0.0;
 }

@@ -274,7 +274,7 @@ def test_autotune_picks_a_shape_and_caches_it(rt, tmp_path, monkeypatch):
     probs = [small_problems()[k] for k in ("crd", "r2_ragged", "minimal")]
     h = rt.Handle(probs, n_rhs=2, precision=rt.RT_P_MIXED, max_restart=8)
     t = h.rt_autotune(force=True)
-    assert t["ray_block"] in (64, 128, 256) and t["ahead"] in (4, 8, 16) and t["sigma_points"] in (4, 8, 0)
+    assert t["ray_block"] in (64, 128, 256) and t["ahead"] in (2, 4, 8) and t["sigma_points"] in (4, 8, 0)
     assert not t["from_cache"] and t["ms_best"] > 0 and t["ms_best"] <= t["ms_default"] + 1e-9
     E = sum(p.n for p in probs)
     x = W.random_vectors(2 * E, 1, 61)[0]
