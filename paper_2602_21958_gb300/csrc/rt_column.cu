@@ -499,6 +499,131 @@ __device__ double arnoldi_orth(TL *V, int64_t ldv, int j, int64_t n, double *h, 
   return hn;
 }
 
+// ------------------------------------- Sigma of an inner cycle (binary16 input)
+// Separable kernel, X in binary16 (a basis row of the inner cycle), S in
+// float32.  Each warp takes points warp, warp + nw, ...; the X block of its
+// next point is copied into the warp's shared buffer by 16-byte cp.async
+// while the current point's frequency-kernel and expansion steps run, so the
+// global latency is hidden behind compute.  Per-warp buffer (16-byte aligned
+// parts): wm [rp][nn] float | wz [rp][nn] float | xs [nr] binary16.
+constexpr int kSig16WarpBytes = 6144;  // shared bytes per warp (16 warps: 96 KB)
+
+__host__ __device__ inline int sig16_part(const ColDev &c) { return (4 * c.rp * c.nn + 15) / 16 * 16; }
+
+__device__ inline bool sig16_ok(const ColDev &c) {
+  return c.psi_off < 0 && c.nr % 8 == 0 && 2 * sig16_part(c) + 2 * c.nr <= kSig16WarpBytes;
+}
+
+__device__ __forceinline__ void cp_async16_s(void *dst, const void *src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+}
+
+template <int KR>
+__device__ __noinline__ void sigma_points_h16(const ColDev &c, const Tables<float> &tb,
+                                              const __half *__restrict__ X, float *__restrict__ S,
+                                              unsigned char *wbuf, const float *Rw) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int nd = c.nd, nn = c.nn, nr = c.nr, rp = c.rp;
+  const float *Uw = tb.Uw + c.u_off, *Ul = tb.Ul + c.u_off, *gam = tb.gamma + c.g_off;
+  float *wm = reinterpret_cast<float *>(wbuf);
+  float *wz = reinterpret_cast<float *>(wbuf + sig16_part(c));
+  __half *xs = reinterpret_cast<__half *>(wbuf + 2 * sig16_part(c));
+  const int nvec = nr / 8;
+  auto fetch = [&](int p) {  // X block of point p -> xs (asynchronous)
+    const uint4 *src = reinterpret_cast<const uint4 *>(X + (int64_t)p * nr);
+    for (int i = lane; i < nvec; i += 32) cp_async16_s(reinterpret_cast<uint4 *>(xs) + i, src + i);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  if (warp < c.nz) fetch(warp);
+  for (int p = warp; p < c.nz; p += nw) {
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    __syncwarp();
+    // 1. moments m_k(f) = sum_d Uw[d][k] X(d, f), lanes over f
+    for (int f = lane; f < nn; f += 32) {
+      for (int k0 = 0; k0 < rp; k0 += KR) {
+        const int kn = min(KR, rp - k0);
+        float m[KR];
+#pragma unroll
+        for (int k = 0; k < KR; ++k) m[k] = 0.f;
+        for (int d = 0; d < nd; ++d) {
+          const float xv = __half2float(xs[d * nn + f]);
+          const float *u = Uw + d * rp + k0;
+#pragma unroll
+          for (int k = 0; k < KR; ++k)
+            if (k < kn) m[k] = fmaf(u[k], xv, m[k]);
+        }
+#pragma unroll
+        for (int k = 0; k < KR; ++k)
+          if (k < kn) wm[(k0 + k) * nn + f] = m[k];
+      }
+    }
+    __syncwarp();
+    if (p + nw < c.nz) fetch(p + nw);  // xs is free again
+    // 2. frequency kernel z_k(f) = sum_q RwT[q][f] m_k(q), two frequencies per lane
+    for (int fb = 0; fb < nn; fb += 64) {
+      const int fa = fb + lane, fc = fa + 32;
+      const bool va = fa < nn, vc = fc < nn;
+      const int fa_ = va ? fa : 0, fc_ = vc ? fc : 0;
+      for (int k0 = 0; k0 < rp; k0 += KR) {
+        const int kn = min(KR, rp - k0);
+        const float *mk = wm + k0 * nn;
+        float aa[KR], ac[KR];
+#pragma unroll
+        for (int k = 0; k < KR; ++k) aa[k] = ac[k] = 0.f;
+        if (c.rdiag) {
+#pragma unroll
+          for (int k = 0; k < KR; ++k)
+            if (k < kn) {
+              aa[k] = Rw[fa_] * mk[k * nn + fa_];
+              ac[k] = Rw[fc_] * mk[k * nn + fc_];
+            }
+        } else {
+          for (int q = 0; q < nn; ++q) {
+            const float ra = Rw[q * nn + fa_], rc = Rw[q * nn + fc_];
+#pragma unroll
+            for (int k = 0; k < KR; ++k)
+              if (k < kn) {
+                const float mv = mk[k * nn + q];
+                aa[k] = fmaf(ra, mv, aa[k]);
+                ac[k] = fmaf(rc, mv, ac[k]);
+              }
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < KR; ++k)
+          if (k < kn) {
+            if (va) wz[(k0 + k) * nn + fa] = aa[k];
+            if (vc) wz[(k0 + k) * nn + fc] = ac[k];
+          }
+      }
+    }
+    __syncwarp();
+    // 3. expansion S(d, f) = gamma(f) sum_k Ul[d][k] z_k(f)
+    const float *g = gam + (int64_t)p * nn;
+    float *sp = S + (int64_t)p * nr;
+    for (int r = lane; r < nr; r += 32) {
+      const int d = r / nn, f = r - d * nn;
+      const float *u = Ul + d * rp;
+      float acc = 0.f;
+      for (int k = 0; k < rp; ++k) acc = fmaf(u[k], wz[k * nn + f], acc);
+      sp[r] = g[f] * acc;
+    }
+    __syncwarp();
+  }
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+}
+
+// Every point of one column (one CTA); wbase: nw * kSig16WarpBytes of shared
+// memory; Rw: the column's float32 frequency kernel (shared or global).
+__device__ __noinline__ void sigma_column_h16(const ColDev &c, const Tables<float> &tb, const __half *X,
+                                              float *S, unsigned char *wbase, const float *Rw) {
+  unsigned char *wbuf = wbase + (threadIdx.x >> 5) * kSig16WarpBytes;
+  if (c.rp <= 2) sigma_points_h16<2>(c, tb, X, S, wbuf, Rw);
+  else sigma_points_h16<8>(c, tb, X, S, wbuf, Rw);
+  __syncthreads();
+}
+
 // ------------------------------------------- inner cycles with a binary16 basis
 // The float32 inner GMRES cycles of the mixed solve keep their basis rows U_i
 // in IEEE binary16.  The rows have unit norm, so every entry is at most 1 in
@@ -721,7 +846,7 @@ __device__ __forceinline__ void tri_solve(const double *Hc, int ld, const double
 //   x += Z y at the end of a cycle; cycles restart from the true residual.
 // One CTA per (column, rhs) instance, as k_solve.
 __global__ void __launch_bounds__(kNT, 1) k_solve_nested(SolveParams p) {
-  __shared__ double sm[4 * kSigBuf];
+  __shared__ __align__(16) double sm[6 * kSigBuf];  // Sigma work buffers (inner: 16 x kSig16WarpBytes)
   __shared__ double red[(kNT / 32) * (kDots + 1)];
   __shared__ double outb[kDots + 1];
   __shared__ double hbuf[2 * (kMaxM + 8)];
@@ -761,6 +886,7 @@ __global__ void __launch_bounds__(kNT, 1) k_solve_nested(SolveParams p) {
     const double *bv = p.b + (p.b_shared ? 0 : rhs * p.E) + c.x_off;
     double *x = p.x + rhs * p.E + c.x_off;
     const double bn = sqrt(cta_norm2(bv, n, red, outb));
+    const bool h16 = sig16_ok(c) && (blockDim.x >> 5) * kSig16WarpBytes <= (int)sizeof(sm);
     // stage the float32 frequency kernel of this column (dense, up to 128 x 128)
     const float *rw_c = nullptr;
     if (!c.rdiag && c.psi_off < 0 && c.nn * c.nn <= kRwCache) {
@@ -829,7 +955,11 @@ __global__ void __launch_bounds__(kNT, 1) k_solve_nested(SolveParams p) {
         int jdone = 0;
         for (int j = 0; j < m_in; ++j) {
           const __half *uj = U + (int64_t)j * ldv;
-          sigma_column<float, __half>(c, p.t32, uj, S32, reinterpret_cast<float *>(sm), 8 * kSigBuf, rw_c);
+          if (h16)
+            sigma_column_h16(c, p.t32, uj, S32, reinterpret_cast<unsigned char *>(sm),
+                             rw_c ? rw_c : p.t32.RwT + c.r_off);
+          else
+            sigma_column<float, __half>(c, p.t32, uj, S32, reinterpret_cast<float *>(sm), 8 * kSigBuf, rw_c);
           // Arnoldi on K = Lambda Sigma (A = Id - K, same Krylov space): the
           // sweep emits K u_j and needs no read of u_j
           sweep_column<float, __half, float, 4>(c, p.t32, p.cm, S32, nullptr, uj, nullptr, W32, kOutI, false);
