@@ -267,7 +267,7 @@ def run_ours(args, rank: int, world: int):
         "applies": applies, "e2e_ms": e2e_ms,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks[0], "unit": "GB/s",
                      "frac": achieved / peaks[0], "traffic": None,
-                     "kernel": "k_solve<float>", "peak_source": peaks[1],
+                     "kernel": "k_solve_nested", "peak_source": peaks[1],
                      "bytes_per_launch": bytes_avg, "kernel_ms": kern_avg},
     }
 

@@ -104,7 +104,7 @@ typedef struct rt_solve_opts {
 } rt_solve_opts;
 
 typedef struct rt_info {
-  int32_t status;          /* RT_OK, RT_ERR_NOCONV or RT_ERR_BREAKDOWN (worst over batch) */
+  int32_t status;          /* RT_OK or the worst instance outcome: RT_ERR_NOCONV, RT_ERR_BREAKDOWN, RT_ERR_NONFINITE, RT_ERR_TIMEOUT */
   int32_t n_instances;     /* n_cols * n_rhs                                          */
   int32_t max_outer;       /* largest number of outer steps over the instances        */
   int32_t max_inner;       /* largest total inner (Arnoldi) iterations                */

@@ -1023,7 +1023,9 @@ int rt_solve(rt_handle *h, const double *b, double *x, const rt_solve_opts *o, r
     loc.max_inner = std::max(loc.max_inner, inner[i]);
     loc.total_inner += inner[i];
     loc.max_relres = std::max(loc.max_relres, relres[i]);
-    if (status[i] != RT_OK && (worst == RT_OK || status[i] == RT_ERR_NONFINITE)) worst = status[i];
+    if (status[i] != RT_OK && worst != RT_ERR_TIMEOUT &&
+        (worst == RT_OK || status[i] == RT_ERR_NONFINITE || status[i] == RT_ERR_TIMEOUT))
+      worst = status[i];
   }
   loc.status = worst;
   loc.ms = ms;

@@ -10,13 +10,14 @@
 
 #include <cuda_runtime.h>
 
+#include "rt_async.cuh"
 #include "rt_host.h"
 #include "rt_internal.cuh"
 
 namespace rt {
 
 constexpr int kNT = 512;      // threads per CTA of the solve kernel (one CTA per SM)
-constexpr int kDots = 8;      // basis vectors per block reduction in Gram-Schmidt
+constexpr int kDots = 4;      // basis vectors per block reduction in Gram-Schmidt
 
 int solve_block_threads() { return kNT; }
 
@@ -118,7 +119,7 @@ struct SolveParams {
   SolveOut out;
 };
 
-constexpr int kU = 4;  // independent elements per thread in the vector loops
+constexpr int kU = 8;  // independent elements per thread in the vector loops
 constexpr int kRwCache = 128 * 128;  // floats of frequency kernel kept in shared memory by the mixed solve
 
 __device__ __forceinline__ double cta_norm2(const double *v, int64_t n, double *red, double *outb) {
@@ -514,11 +515,6 @@ __device__ inline bool sig16_ok(const ColDev &c) {
   return c.psi_off < 0 && c.nr % 8 == 0 && 2 * sig16_part(c) + 2 * c.nr <= kSig16WarpBytes;
 }
 
-__device__ __forceinline__ void cp_async16_s(void *dst, const void *src) {
-  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
-}
-
 template <int KR>
 __device__ __noinline__ void sigma_points_h16(const ColDev &c, const Tables<float> &tb,
                                               const __half *__restrict__ X, float *__restrict__ S,
@@ -532,12 +528,12 @@ __device__ __noinline__ void sigma_points_h16(const ColDev &c, const Tables<floa
   const int nvec = nr / 8;
   auto fetch = [&](int p) {  // X block of point p -> xs (asynchronous)
     const uint4 *src = reinterpret_cast<const uint4 *>(X + (int64_t)p * nr);
-    for (int i = lane; i < nvec; i += 32) cp_async16_s(reinterpret_cast<uint4 *>(xs) + i, src + i);
-    asm volatile("cp.async.commit_group;" ::: "memory");
+    for (int i = lane; i < nvec; i += 32) cp_async16(reinterpret_cast<uint4 *>(xs) + i, src + i, 16u);
+    cp_async_commit();
   };
   if (warp < c.nz) fetch(warp);
   for (int p = warp; p < c.nz; p += nw) {
-    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    cp_async_wait<0>();
     __syncwarp();
     // 1. moments m_k(f) = sum_d Uw[d][k] X(d, f), lanes over f
     for (int f = lane; f < nn; f += 32) {
@@ -611,7 +607,7 @@ __device__ __noinline__ void sigma_points_h16(const ColDev &c, const Tables<floa
     }
     __syncwarp();
   }
-  asm volatile("cp.async.wait_group 0;" ::: "memory");
+  cp_async_wait<0>();
 }
 
 // Every point of one column (one CTA); wbase: nw * kSig16WarpBytes of shared
@@ -636,7 +632,8 @@ __device__ __noinline__ void sigma_column_h16(const ColDev &c, const Tables<floa
 // zero; the unnormalised direction w is float32 and its entries past n are
 // ignored.  Vector loops walk quads (4 consecutive entries): 8-byte loads of
 // U, 16-byte loads of w.
-constexpr int kQ = 2;  // quads per thread per loop iteration
+constexpr int kQ = 4;    // quads per thread per loop iteration (measured best with kD16 = 8)
+constexpr int kD16 = 8;  // basis rows per streaming group
 
 __device__ __forceinline__ void h4_to_f(uint2 raw, float (&f)[4]) {
   const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&raw.x));
@@ -664,38 +661,39 @@ __device__ __forceinline__ void ld_w4(const float *w, int64_t k, int64_t n, bool
   f[3] = live && k + 3 < n ? v.w : 0.f;
 }
 
-// h[0..j] = U[0..j]^T w, returns ||w||^2 (float64 block sums)
+// h[0..j] = U[0..j]^T w, returns ||w||^2.  Sums are float32 over a thread's
+// 8 loop steps, then float64, then one block reduction per group of kD16 rows.
 __device__ __noinline__ double cta_dots16(const __half *U, int64_t ldv, int j, const float *w, int64_t n,
                                           double *h, double *red, double *outb) {
   const int64_t nq = ldv / 4;
   double nrm = 0.0;
   constexpr int kWiden = 8;
-  for (int i0 = 0; i0 <= j; i0 += kDots) {
-    const int cnt = min(kDots, j + 1 - i0);
-    const __half *up[kDots];
+  for (int i0 = 0; i0 <= j; i0 += kD16) {
+    const int cnt = min(kD16, j + 1 - i0);
+    const __half *up[kD16];
 #pragma unroll
-    for (int u = 0; u < kDots; ++u) up[u] = U + (int64_t)min(i0 + u, j) * ldv;
-    double acc[kDots + 1];
-    float part[kDots + 1];
+    for (int u = 0; u < kD16; ++u) up[u] = U + (int64_t)min(i0 + u, j) * ldv;
+    double acc[kD16 + 1];
+    float part[kD16 + 1];
 #pragma unroll
-    for (int u = 0; u <= kDots; ++u) {
+    for (int u = 0; u <= kD16; ++u) {
       acc[u] = 0.0;
       part[u] = 0.f;
     }
     int it = 0;
     for (int64_t q0 = threadIdx.x; q0 < nq; q0 += (int64_t)kQ * blockDim.x) {
       float wv[kQ][4];
-      uint2 raw[kDots][kQ];
+      uint2 raw[kD16][kQ];
 #pragma unroll
       for (int e = 0; e < kQ; ++e) {
         const int64_t q = q0 + (int64_t)e * blockDim.x;
         const int64_t qc = min(q, nq - 1);
         ld_w4(w, 4 * qc, n, q < nq, wv[e]);
 #pragma unroll
-        for (int u = 0; u < kDots; ++u) raw[u][e] = *reinterpret_cast<const uint2 *>(up[u] + 4 * qc);
+        for (int u = 0; u < kD16; ++u) raw[u][e] = *reinterpret_cast<const uint2 *>(up[u] + 4 * qc);
       }
 #pragma unroll
-      for (int u = 0; u < kDots; ++u)
+      for (int u = 0; u < kD16; ++u)
 #pragma unroll
         for (int e = 0; e < kQ; ++e) {
           float f[4];
@@ -706,34 +704,34 @@ __device__ __noinline__ double cta_dots16(const __half *U, int64_t ldv, int j, c
 #pragma unroll
       for (int e = 0; e < kQ; ++e)
 #pragma unroll
-        for (int t = 0; t < 4; ++t) part[kDots] = fmaf(wv[e][t], wv[e][t], part[kDots]);
+        for (int t = 0; t < 4; ++t) part[kD16] = fmaf(wv[e][t], wv[e][t], part[kD16]);
       if (++it == kWiden) {
         it = 0;
 #pragma unroll
-        for (int u = 0; u <= kDots; ++u) {
+        for (int u = 0; u <= kD16; ++u) {
           acc[u] += (double)part[u];
           part[u] = 0.f;
         }
       }
     }
 #pragma unroll
-    for (int u = 0; u <= kDots; ++u) acc[u] += (double)part[u];
-    block_sum<kDots + 1>(acc, red, outb);
+    for (int u = 0; u <= kD16; ++u) acc[u] += (double)part[u];
+    block_sum<kD16 + 1>(acc, red, outb);
     if (threadIdx.x < cnt) h[i0 + threadIdx.x] = outb[threadIdx.x];
-    if (i0 == 0) nrm = acc[kDots];
+    if (i0 == 0) nrm = acc[kD16];
   }
   __syncthreads();
   return nrm;
 }
 
-// acc[e][t] += sum_{i < cnt} coef[i] U_i[quad q_e]; kDots rows' loads in flight
+// acc[e][t] += sum_{i < cnt} coef[i] U_i[quad q_e]; kD16 rows' loads in flight
 __device__ __forceinline__ void axpy16(const __half *U, int64_t ldv, int cnt, const float *coef,
                                        const int64_t (&qc)[kQ], float (&acc)[kQ][4]) {
-  for (int i0 = 0; i0 < cnt; i0 += kDots) {
-    uint2 raw[kDots][kQ];
-    float hu[kDots];
+  for (int i0 = 0; i0 < cnt; i0 += kD16) {
+    uint2 raw[kD16][kQ];
+    float hu[kD16];
 #pragma unroll
-    for (int u = 0; u < kDots; ++u) {
+    for (int u = 0; u < kD16; ++u) {
       const int i = min(i0 + u, cnt - 1);  // rows past cnt: re-read with a zero coefficient
       hu[u] = (i0 + u < cnt) ? coef[i0 + u] : 0.f;
       const __half *ui = U + (int64_t)i * ldv;
@@ -741,7 +739,7 @@ __device__ __forceinline__ void axpy16(const __half *U, int64_t ldv, int cnt, co
       for (int e = 0; e < kQ; ++e) raw[u][e] = *reinterpret_cast<const uint2 *>(ui + 4 * qc[e]);
     }
 #pragma unroll
-    for (int u = 0; u < kDots; ++u)
+    for (int u = 0; u < kD16; ++u)
 #pragma unroll
       for (int e = 0; e < kQ; ++e) {
         float f[4];
@@ -847,8 +845,9 @@ __device__ __forceinline__ void tri_solve(const double *Hc, int ld, const double
 // One CTA per (column, rhs) instance, as k_solve.
 __global__ void __launch_bounds__(kNT, 1) k_solve_nested(SolveParams p) {
   __shared__ __align__(16) double sm[6 * kSigBuf];  // Sigma work buffers (inner: 16 x kSig16WarpBytes)
-  __shared__ double red[(kNT / 32) * (kDots + 1)];
-  __shared__ double outb[kDots + 1];
+  constexpr int kRed = (kDots > kD16 ? kDots : kD16) + 1;  // widest block_sum
+  __shared__ double red[(kNT / 32) * kRed];
+  __shared__ double outb[kRed];
   __shared__ double hbuf[2 * (kMaxM + 8)];
   __shared__ double ybuf[kMaxM + 8];
   __shared__ float hf32[kMaxM + 8];
