@@ -3,16 +3,18 @@
 // column the GEMM  C[rows, r] = sum_q X[rows, q] PsiW[r, q]  with the rows the
 // points of every right-hand side stacked, then S = gamma * C.
 //
-//   operands  : bf16.  A = X rows, converted in registers by all threads and
-//               stored in the canonical no-swizzle K-major layout; B = PsiW,
+//   operands  : bf16.  X is packed to bf16 once per apply (k_to_bf16); A tiles
+//               (128 rows x 64 q) arrive by 16-byte cp.async copies straight
+//               into the canonical no-swizzle K-major layout; B = PsiW is
 //               pre-tiled in global memory as the exact shared-memory image of
 //               each (256-ray, 64-q) block and fetched with one cp.async.bulk
 //               completing on an mbarrier.
 //   accumulate: fp32 in tensor memory (128 lanes x 256 columns), read back
 //               with tcgen05.ld and scaled by Gamma in the epilogue.
-//   pipeline  : two stages; thread 0 issues tcgen05.mma (M=128, N<=256, K=16,
-//               four per 64-wide chunk) and commits each stage to an mbarrier
-//               that gates the overwrite of that stage two chunks later.
+//   pipeline  : four stages; thread 0 issues tcgen05.mma (M=128, N<=256,
+//               K=16, four per 64-wide chunk) and commits each chunk to an
+//               mbarrier; the stage freed by chunk k-1 is refilled with chunk
+//               k+3 while the MMAs of chunk k run.
 // Every wait is bounded; on timeout the CTA raises an error flag, drains what
 // it issued (bounded), frees its tensor memory and returns.
 #include <cuda_bf16.h>
@@ -22,6 +24,7 @@
 #include <cstring>
 #include <vector>
 
+#include "rt_async.cuh"
 #include "rt_host.h"
 #include "rt_internal.cuh"
 
@@ -34,8 +37,8 @@ constexpr int kTcThreads = 256;
 constexpr int kTcABytes = kTcBM * kTcBK * 2;   // 16 KB
 constexpr int kTcBBytes = kTcBN * kTcBK * 2;   // 32 KB
 constexpr int kTcStages = 4;
+constexpr int kTcLdt = kTcBN + 4;        // row stride (floats) of the epilogue tile in shared memory
 constexpr int kTcSmem = kTcStages * (kTcABytes + kTcBBytes) + 1024;
-constexpr long long kSpinLimit = 1ll << 26;
 
 struct TcJob {
   int32_t col;  // column index
@@ -43,54 +46,6 @@ struct TcJob {
   int32_t n0;   // first ray
   int32_t pad;
 };
-
-// ----------------------------------------------------------- PTX helpers
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-               : "memory");
-}
-
-// Bounded wait for the phase with parity `par`; false on timeout.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t par) {
-  const uint32_t a = smem_u32(bar);
-  for (long long it = 0; it < kSpinLimit; ++it) {
-    uint32_t done;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(done)
-        : "r"(a), "r"(par)
-        : "memory");
-    if (done) return true;
-  }
-  return false;
-}
-
-__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(bar))
-      : "memory");
-}
-
-// 16-byte asynchronous copy global -> shared; src_bytes = 0 zero-fills.
-__device__ __forceinline__ void cp_async16(void *dst, const void *src, uint32_t src_bytes) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(src_bytes)
-               : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 // Shared-memory matrix descriptor: no swizzle, K-major canonical layout of
 // 8-row x 16-byte core matrices; lbo = byte distance of K-adjacent core
@@ -204,6 +159,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     arow_base = rhs * E + c.x_off + (int64_t)p * nr;
   }
   const uint32_t a_dst = (uint32_t)((arow >> 3) * 128 + (arow & 7) * 16);
+  int b_issued = 0;  // thread 0: B copies issued (chunks 0 .. b_issued-1)
   auto issue = [&](int kc) {  // copies of chunk kc into stage kc % kTcStages
     const int st = kc % kTcStages;
 #pragma unroll
@@ -217,6 +173,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     if (tid == 0) {
       mbar_expect_tx(&bar_b[st], kTcBBytes);
       bulk_g2s(sB(st), Bcol + (int64_t)kc * (kTcBN * kTcBK), kTcBBytes, &bar_b[st]);
+      b_issued = kc + 1;
     }
   };
   const int pre = min(kTcStages - 1, nchunk);
@@ -276,29 +233,52 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   }
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (ok && drained) {
-    // epilogue: warp w reads TMEM lanes 32*(w%4).. and columns 128*(w/4)..
+    // epilogue, two steps.  (1) TMEM -> shared tile ct[row][col] (the stage
+    // buffers are idle now): warp w reads TMEM lanes 32*(w%4).. and columns
+    // 128*(w/4)..; row stride kTcLdt floats keeps the 16-byte stores
+    // conflict-free.  (2) ct -> S with Gamma, a warp per row, lanes along
+    // the rays: coalesced 16-byte stores.
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    float *ct = reinterpret_cast<float *>(base);
     const int quarter = warp & 3, half = warp >> 2;
     const int row = quarter * 32 + lane;
-    const int grow = job.m0 + row;
-    const bool valid_row = grow < M;
-    const int rhs = valid_row ? grow / nz : 0, p = valid_row ? grow - rhs * nz : 0;
-    TS *srow = S + rhs * E + c.x_off + (int64_t)p * nr;
-    const float *grow_g = gamma + c.g_off + (int64_t)p * nn;
     for (int cc = 0; cc < kTcBN / 2; cc += 16) {
       const int col0 = half * (kTcBN / 2) + cc;
       if (col0 >= n_valid) break;  // uniform across the warp
       float v[16];
       tc_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)col0, v);
-      if (valid_row) {
+      float4 *dst = reinterpret_cast<float4 *>(ct + row * kTcLdt + col0);
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
-          const int r = job.n0 + col0 + i;
-          if (col0 + i < n_valid) srow[r] = (TS)(grow_g[r % nn] * v[i]);
+      for (int t = 0; t < 4; ++t) dst[t] = make_float4(v[4 * t], v[4 * t + 1], v[4 * t + 2], v[4 * t + 3]);
+    }
+    __syncthreads();
+    const int nwarps = kTcThreads / 32;
+    for (int r = warp; r < kTcBM; r += nwarps) {
+      const int grow = job.m0 + r;
+      if (grow >= M) break;  // uniform across the warp
+      const int rhs = grow / nz, p = grow - rhs * nz;
+      TS *srow = S + rhs * E + c.x_off + (int64_t)p * nr + job.n0;
+      const float *g = gamma + c.g_off + (int64_t)p * nn;
+      for (int ci = 4 * lane; ci < n_valid; ci += 128) {
+        const float4 v = *reinterpret_cast<const float4 *>(ct + r * kTcLdt + ci);
+        const int r0 = job.n0 + ci;
+        const float a0 = g[r0 % nn] * v.x, a1 = g[(r0 + 1) % nn] * v.y;
+        const float a2 = g[(r0 + 2) % nn] * v.z, a3 = g[(r0 + 3) % nn] * v.w;
+        if (sizeof(TS) == 4) {
+          *reinterpret_cast<float4 *>(srow + ci) = make_float4(a0, a1, a2, a3);
+        } else {
+          reinterpret_cast<double2 *>(srow + ci)[0] = make_double2(a0, a1);
+          reinterpret_cast<double2 *>(srow + ci)[1] = make_double2(a2, a3);
         }
       }
     }
-  } else if (tid == 0) {
-    atomicOr(err, 1);
+  } else {
+    if (tid == 0) {
+      atomicOr(err, 1);
+      // B copies issued but never consumed may still be landing: wait (bounded)
+      for (int kc = committed; kc < b_issued; ++kc) mbar_wait(&bar_b[kc % kTcStages], (kc / kTcStages) & 1);
+    }
+    __syncthreads();
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
