@@ -121,6 +121,7 @@ struct SolveParams {
 
 constexpr int kU = 8;  // independent elements per thread in the vector loops
 constexpr int kRwCache = 128 * 128;  // floats of frequency kernel kept in shared memory by the mixed solve
+constexpr int kUwlCache = 256;       // floats of each angular factor kept in shared memory
 
 __device__ __forceinline__ double cta_norm2(const double *v, int64_t n, double *red, double *outb) {
   double a[1] = {0.0};
@@ -502,33 +503,41 @@ __device__ double arnoldi_orth(TL *V, int64_t ldv, int j, int64_t n, double *h, 
 
 // ------------------------------------- Sigma of an inner cycle (binary16 input)
 // Separable kernel, X in binary16 (a basis row of the inner cycle), S in
-// float32.  Each warp takes points warp, warp + nw, ...; the X block of its
-// next point is copied into the warp's shared buffer by 16-byte cp.async
-// while the current point's frequency-kernel and expansion steps run, so the
-// global latency is hidden behind compute.  Per-warp buffer (16-byte aligned
-// parts): wm [rp][nn] float | wz [rp][nn] float | xs [nr] binary16.
-constexpr int kSig16WarpBytes = 6144;  // shared bytes per warp (16 warps: 96 KB)
+// float32.  Each warp takes points warp, warp + nw, ...; the X block and the
+// Gamma row of its next point are copied into the warp's shared buffer by
+// cp.async while the current point's frequency-kernel and expansion steps
+// run, so the global latency is hidden behind compute.  Per-warp buffer
+// (16-byte aligned parts): wm [rp][nn] float | wz [rp][nn] float | xs [nr]
+// binary16 | gs [nn] float.  The angular factors Uw, Ul come from shared
+// memory when the caller staged them.
+constexpr int kSig16WarpBytes = 7168;  // shared bytes per warp (16 warps: 112 KB)
 
-__host__ __device__ inline int sig16_part(const ColDev &c) { return (4 * c.rp * c.nn + 15) / 16 * 16; }
+__host__ __device__ inline int sig16_part(int elems, int bytes) { return (elems * bytes + 15) / 16 * 16; }
 
 __device__ inline bool sig16_ok(const ColDev &c) {
-  return c.psi_off < 0 && c.nr % 8 == 0 && 2 * sig16_part(c) + 2 * c.nr <= kSig16WarpBytes;
+  const int need = 2 * sig16_part(c.rp * c.nn, 4) + sig16_part(c.nr, 2) + sig16_part(c.nn, 4);
+  return c.psi_off < 0 && c.nr % 8 == 0 && c.rp <= 8 && need <= kSig16WarpBytes;
 }
 
 template <int KR>
 __device__ __noinline__ void sigma_points_h16(const ColDev &c, const Tables<float> &tb,
                                               const __half *__restrict__ X, float *__restrict__ S,
-                                              unsigned char *wbuf, const float *Rw) {
+                                              unsigned char *wbuf, const float *Rw, const float *Uw,
+                                              const float *Ul) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int nd = c.nd, nn = c.nn, nr = c.nr, rp = c.rp;
-  const float *Uw = tb.Uw + c.u_off, *Ul = tb.Ul + c.u_off, *gam = tb.gamma + c.g_off;
+  const float *gam = tb.gamma + c.g_off;
+  const int pz = sig16_part(rp * nn, 4);
   float *wm = reinterpret_cast<float *>(wbuf);
-  float *wz = reinterpret_cast<float *>(wbuf + sig16_part(c));
-  __half *xs = reinterpret_cast<__half *>(wbuf + 2 * sig16_part(c));
+  float *wz = reinterpret_cast<float *>(wbuf + pz);
+  __half *xs = reinterpret_cast<__half *>(wbuf + 2 * pz);
+  float *gs = reinterpret_cast<float *>(wbuf + 2 * pz + sig16_part(nr, 2));
   const int nvec = nr / 8;
-  auto fetch = [&](int p) {  // X block of point p -> xs (asynchronous)
+  auto fetch = [&](int p) {  // X block and Gamma row of point p -> xs, gs (asynchronous)
     const uint4 *src = reinterpret_cast<const uint4 *>(X + (int64_t)p * nr);
     for (int i = lane; i < nvec; i += 32) cp_async16(reinterpret_cast<uint4 *>(xs) + i, src + i, 16u);
+    const float *g = gam + (int64_t)p * nn;
+    for (int f = lane; f < nn; f += 32) cp_async4(gs + f, g + f);
     cp_async_commit();
   };
   if (warp < c.nz) fetch(warp);
@@ -537,86 +546,87 @@ __device__ __noinline__ void sigma_points_h16(const ColDev &c, const Tables<floa
     __syncwarp();
     // 1. moments m_k(f) = sum_d Uw[d][k] X(d, f), lanes over f
     for (int f = lane; f < nn; f += 32) {
-      for (int k0 = 0; k0 < rp; k0 += KR) {
-        const int kn = min(KR, rp - k0);
-        float m[KR];
+      float m[KR];
 #pragma unroll
-        for (int k = 0; k < KR; ++k) m[k] = 0.f;
-        for (int d = 0; d < nd; ++d) {
-          const float xv = __half2float(xs[d * nn + f]);
-          const float *u = Uw + d * rp + k0;
-#pragma unroll
-          for (int k = 0; k < KR; ++k)
-            if (k < kn) m[k] = fmaf(u[k], xv, m[k]);
-        }
+      for (int k = 0; k < KR; ++k) m[k] = 0.f;
+      for (int d = 0; d < nd; ++d) {
+        const float xv = __half2float(xs[d * nn + f]);
+        const float *u = Uw + d * rp;
 #pragma unroll
         for (int k = 0; k < KR; ++k)
-          if (k < kn) wm[(k0 + k) * nn + f] = m[k];
+          if (k < rp) m[k] = fmaf(u[k], xv, m[k]);
       }
+#pragma unroll
+      for (int k = 0; k < KR; ++k)
+        if (k < rp) wm[k * nn + f] = m[k];
     }
     __syncwarp();
-    if (p + nw < c.nz) fetch(p + nw);  // xs is free again
     // 2. frequency kernel z_k(f) = sum_q RwT[q][f] m_k(q), two frequencies per lane
     for (int fb = 0; fb < nn; fb += 64) {
       const int fa = fb + lane, fc = fa + 32;
       const bool va = fa < nn, vc = fc < nn;
       const int fa_ = va ? fa : 0, fc_ = vc ? fc : 0;
-      for (int k0 = 0; k0 < rp; k0 += KR) {
-        const int kn = min(KR, rp - k0);
-        const float *mk = wm + k0 * nn;
-        float aa[KR], ac[KR];
+      float aa[KR], ac[KR];
 #pragma unroll
-        for (int k = 0; k < KR; ++k) aa[k] = ac[k] = 0.f;
-        if (c.rdiag) {
-#pragma unroll
-          for (int k = 0; k < KR; ++k)
-            if (k < kn) {
-              aa[k] = Rw[fa_] * mk[k * nn + fa_];
-              ac[k] = Rw[fc_] * mk[k * nn + fc_];
-            }
-        } else {
-          for (int q = 0; q < nn; ++q) {
-            const float ra = Rw[q * nn + fa_], rc = Rw[q * nn + fc_];
-#pragma unroll
-            for (int k = 0; k < KR; ++k)
-              if (k < kn) {
-                const float mv = mk[k * nn + q];
-                aa[k] = fmaf(ra, mv, aa[k]);
-                ac[k] = fmaf(rc, mv, ac[k]);
-              }
-          }
-        }
+      for (int k = 0; k < KR; ++k) aa[k] = ac[k] = 0.f;
+      if (c.rdiag) {
 #pragma unroll
         for (int k = 0; k < KR; ++k)
-          if (k < kn) {
-            if (va) wz[(k0 + k) * nn + fa] = aa[k];
-            if (vc) wz[(k0 + k) * nn + fc] = ac[k];
+          if (k < rp) {
+            aa[k] = Rw[fa_] * wm[k * nn + fa_];
+            ac[k] = Rw[fc_] * wm[k * nn + fc_];
           }
+      } else {
+        for (int q = 0; q < nn; ++q) {
+          const float ra = Rw[q * nn + fa_], rc = Rw[q * nn + fc_];
+#pragma unroll
+          for (int k = 0; k < KR; ++k)
+            if (k < rp) {
+              const float mv = wm[k * nn + q];
+              aa[k] = fmaf(ra, mv, aa[k]);
+              ac[k] = fmaf(rc, mv, ac[k]);
+            }
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < KR; ++k)
+        if (k < rp) {
+          if (va) wz[k * nn + fa] = aa[k];
+          if (vc) wz[k * nn + fc] = ac[k];
+        }
+    }
+    __syncwarp();
+    // 3. expansion S(d, f) = gamma(f) sum_k Ul[d][k] z_k(f): lanes over f
+    //    (coalesced stores), the lane's z and gamma in registers, loop over d
+    float *sp = S + (int64_t)p * nr;
+    for (int f = lane; f < nn; f += 32) {
+      float zf[KR];
+#pragma unroll
+      for (int k = 0; k < KR; ++k) zf[k] = k < rp ? wz[k * nn + f] : 0.f;
+      const float gf = gs[f];
+      for (int d = 0; d < nd; ++d) {
+        const float *u = Ul + d * rp;
+        float acc = 0.f;
+#pragma unroll
+        for (int k = 0; k < KR; ++k)
+          if (k < rp) acc = fmaf(u[k], zf[k], acc);
+        sp[d * nn + f] = gf * acc;
       }
     }
     __syncwarp();
-    // 3. expansion S(d, f) = gamma(f) sum_k Ul[d][k] z_k(f)
-    const float *g = gam + (int64_t)p * nn;
-    float *sp = S + (int64_t)p * nr;
-    for (int r = lane; r < nr; r += 32) {
-      const int d = r / nn, f = r - d * nn;
-      const float *u = Ul + d * rp;
-      float acc = 0.f;
-      for (int k = 0; k < rp; ++k) acc = fmaf(u[k], wz[k * nn + f], acc);
-      sp[r] = g[f] * acc;
-    }
-    __syncwarp();
+    if (p + nw < c.nz) fetch(p + nw);  // xs, gs are free again
   }
   cp_async_wait<0>();
 }
 
 // Every point of one column (one CTA); wbase: nw * kSig16WarpBytes of shared
-// memory; Rw: the column's float32 frequency kernel (shared or global).
+// memory; Rw, Uw, Ul: the column's float32 factors (shared or global).
 __device__ __noinline__ void sigma_column_h16(const ColDev &c, const Tables<float> &tb, const __half *X,
-                                              float *S, unsigned char *wbase, const float *Rw) {
+                                              float *S, unsigned char *wbase, const float *Rw, const float *Uw,
+                                              const float *Ul) {
   unsigned char *wbuf = wbase + (threadIdx.x >> 5) * kSig16WarpBytes;
-  if (c.rp <= 2) sigma_points_h16<2>(c, tb, X, S, wbuf, Rw);
-  else sigma_points_h16<8>(c, tb, X, S, wbuf, Rw);
+  if (c.rp <= 2) sigma_points_h16<2>(c, tb, X, S, wbuf, Rw, Uw, Ul);
+  else sigma_points_h16<8>(c, tb, X, S, wbuf, Rw, Uw, Ul);
   __syncthreads();
 }
 
@@ -844,7 +854,7 @@ __device__ __forceinline__ void tri_solve(const double *Hc, int ld, const double
 //   x += Z y at the end of a cycle; cycles restart from the true residual.
 // One CTA per (column, rhs) instance, as k_solve.
 __global__ void __launch_bounds__(kNT, 1) k_solve_nested(SolveParams p) {
-  __shared__ __align__(16) double sm[6 * kSigBuf];  // Sigma work buffers (inner: 16 x kSig16WarpBytes)
+  __shared__ __align__(16) double sm[7 * kSigBuf];  // Sigma work buffers (inner: 16 x kSig16WarpBytes)
   constexpr int kRed = (kDots > kD16 ? kDots : kD16) + 1;  // widest block_sum
   __shared__ double red[(kNT / 32) * kRed];
   __shared__ double outb[kRed];
@@ -855,6 +865,7 @@ __global__ void __launch_bounds__(kNT, 1) k_solve_nested(SolveParams p) {
   __shared__ int s_q;
   __shared__ double s_val[4];
   __shared__ float rw_s[kRwCache];  // float32 frequency kernel of the current column
+  __shared__ float uwl_s[2 * kUwlCache];  // float32 angular factors Uw | Ul of the current column
   uint8_t *slot = reinterpret_cast<uint8_t *>(p.V) + (int64_t)blockIdx.x * p.cap;
   double *S64 = p.S + (int64_t)blockIdx.x * p.ld;
   float *S32 = reinterpret_cast<float *>(S64);
@@ -892,6 +903,16 @@ __global__ void __launch_bounds__(kNT, 1) k_solve_nested(SolveParams p) {
       for (int k = threadIdx.x; k < c.nn * c.nn; k += blockDim.x) rw_s[k] = p.t32.RwT[c.r_off + k];
       __syncthreads();
       rw_c = rw_s;
+    }
+    const float *uw_c = p.t32.Uw + c.u_off, *ul_c = p.t32.Ul + c.u_off;
+    if (c.nd * c.rp <= kUwlCache) {
+      for (int k = threadIdx.x; k < c.nd * c.rp; k += blockDim.x) {
+        uwl_s[k] = uw_c[k];
+        uwl_s[kUwlCache + k] = ul_c[k];
+      }
+      __syncthreads();
+      uw_c = uwl_s;
+      ul_c = uwl_s + kUwlCache;
     }
     if (!p.use_x0) {
       for (int64_t k = threadIdx.x; k < n; k += blockDim.x) x[k] = 0.0;
@@ -956,7 +977,7 @@ __global__ void __launch_bounds__(kNT, 1) k_solve_nested(SolveParams p) {
           const __half *uj = U + (int64_t)j * ldv;
           if (h16)
             sigma_column_h16(c, p.t32, uj, S32, reinterpret_cast<unsigned char *>(sm),
-                             rw_c ? rw_c : p.t32.RwT + c.r_off);
+                             rw_c ? rw_c : p.t32.RwT + c.r_off, uw_c, ul_c);
           else
             sigma_column<float, __half>(c, p.t32, uj, S32, reinterpret_cast<float *>(sm), 8 * kSigBuf, rw_c);
           // Arnoldi on K = Lambda Sigma (A = Id - K, same Krylov space): the
