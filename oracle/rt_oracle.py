@@ -366,6 +366,65 @@ def solve_gmres(prob: Problem, b: np.ndarray | None = None, tol: float = 1e-13,
     return gmres(lambda v: apply_A(prob, v), bb, tol=tol, restart=restart, max_iter=max_iter)
 
 
+def bicgstab(matvec, b: np.ndarray, tol: float = 1e-10, max_iter: int = 5000,
+             x0: np.ndarray | None = None) -> GmresResult:
+    """BiCGStab (van der Vorst 1992), the paper's second Krylov solver for the
+    1D systems (Sec. 5, with GMRES), unpreconditioned, shadow residual = the
+    initial residual.  One iteration = two operator applications:
+        rho = (r0^, r);  beta = (rho / rho_old) (alpha / omega)
+        p = r + beta (p - omega v);  v = A p;  alpha = rho / (r0^, v)
+        s = r - alpha v;  t = A s;  omega = (t, s) / (t, t)
+        x += alpha p + omega s;  r = s - omega t
+    Stops when ||r|| / ||b|| <= tol (recursive residual, confirmed by the true
+    residual at exit) or after the half step when ||s|| / ||b|| <= tol.
+    ``iterations`` counts full iterations (half steps count as one)."""
+    b = np.asarray(b, dtype=float)
+    n = b.size
+    x = np.zeros(n) if x0 is None else np.array(x0, dtype=float)
+    bn = np.linalg.norm(b)
+    if bn == 0.0:
+        return GmresResult(x, 0, 0, 0.0, [0.0])
+    r = b - matvec(x)
+    rhat = r.copy()
+    p = np.zeros(n)
+    v = np.zeros(n)
+    rho_old = alpha = omega = 1.0
+    hist = [np.linalg.norm(r) / bn]
+    it = 0
+    while it < max_iter and hist[-1] > tol:
+        rho = rhat @ r
+        if rho == 0.0:
+            break
+        beta = (rho / rho_old) * (alpha / omega)
+        p = r + beta * (p - omega * v)
+        v = matvec(p)
+        alpha = rho / (rhat @ v)
+        s = r - alpha * v
+        it += 1
+        if np.linalg.norm(s) / bn <= tol:
+            x = x + alpha * p
+            hist.append(np.linalg.norm(s) / bn)
+            break
+        t = matvec(s)
+        tt = t @ t
+        omega = (t @ s) / tt if tt > 0.0 else 0.0
+        x = x + alpha * p + omega * s
+        r = s - omega * t
+        rho_old = rho
+        hist.append(np.linalg.norm(r) / bn)
+        if omega == 0.0:
+            break
+    relres = np.linalg.norm(b - matvec(x)) / bn
+    return GmresResult(x, it, 0, relres, hist)
+
+
+def solve_bicgstab(prob: Problem, b: np.ndarray | None = None, tol: float = 1e-13,
+                   max_iter: int = 5000) -> GmresResult:
+    """Matrix-free solve of A_N I = b with the oracle's own BiCGStab."""
+    bb = rhs(prob) if b is None else b
+    return bicgstab(lambda v: apply_A(prob, v), bb, tol=tol, max_iter=max_iter)
+
+
 # ------------------------------------------------- reduced CRD system (1D only)
 def solve_crd_reduced(prob: Problem) -> np.ndarray:
     """Isotropic CRD (P = 1, R = phi phi^T, gamma = (1 - eps)/phi, t = eps B):

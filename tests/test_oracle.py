@@ -155,6 +155,31 @@ def test_lu_equals_gmres():
     assert np.linalg.norm(g.x - x_lu) <= 1e-12 * np.linalg.norm(x_lu)
 
 
+def test_bicgstab_solves_a_random_nonsymmetric_system():
+    # library LU as the independent reference; a wrong beta/omega or sign stalls
+    rng = np.random.default_rng(7)
+    A = np.eye(60) + 0.3 * rng.standard_normal((60, 60)) / np.sqrt(60)
+    b = rng.standard_normal(60)
+    r = O.bicgstab(lambda v: A @ v, b, tol=1e-14)
+    x = np.linalg.solve(A, b)
+    assert r.relres <= 1e-13
+    assert np.linalg.norm(r.x - x) <= 1e-12 * np.linalg.norm(x)
+
+
+def test_bicgstab_on_a_multiple_of_identity_takes_one_half_step():
+    b = np.random.default_rng(8).standard_normal(30)
+    r = O.bicgstab(lambda v: 2.5 * v, b, tol=1e-14)
+    assert r.iterations == 1
+    assert np.allclose(r.x, b / 2.5, rtol=0, atol=1e-15)
+
+
+def test_lu_equals_bicgstab():
+    q = W.two_level_column(np.logspace(-3, 3, 12), 4, 2, 7, "r2", 1e-3, 1.0)
+    x_lu = O.solve_dense(q)
+    r = O.solve_bicgstab(q, tol=1e-14)
+    assert np.linalg.norm(r.x - x_lu) <= 1e-11 * np.linalg.norm(x_lu)
+
+
 def test_reduced_crd_system_equals_full_solve():
     """Independent route at full C1 size: the N_z x N_z reduced CRD system."""
     p = W.config_c1()
