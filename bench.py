@@ -311,6 +311,72 @@ def tensor_roofline(rank: int = 0) -> dict:
             "peak_source": peak[1], "workload": "C5 physics as dense Psi, 256 columns x 4 rhs, bf16 in / fp32 acc"}
 
 
+def configs_sweep(rank: int = 0) -> dict:
+    """Per-configuration figures for the other workloads: C1 and C2 (one 1D
+    column), C3 (3D box 32^3), C4 (3D box 64^3).  Apply latency in both
+    precisions (CUDA events over repeated rt_apply(RT_OP_A) on the launching
+    stream); time to relative residual 1e-10 (wall clock around rt_solve) for
+    the mixed FGMRES, the float64 GMRES (C1-C3: a float64 GMRES basis of C4's
+    1.3e9 dofs does not fit) and the float64 BiCGStab (all four)."""
+    import torch
+
+    from paper_2602_21958_gb300 import rt, workloads as W
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    stream = torch.cuda.current_stream()
+    out = {}
+
+    def timed_solve(h, b, x, **kw):
+        x.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        info = h.rt_solve(b, x, **kw)
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t0) * 1e3, {"outer": info["max_outer"], "inner": info["max_inner"],
+                                                  "relres": info["max_relres"], "status": info["status"]}
+
+    for name, make in (("C1", W.config_c1), ("C2", W.config_c2), ("C3", W.config_c3), ("C4", W.config_c4)):
+        p = make()
+        big = name == "C4"
+        entry = {"dofs": int(p.n), "applies_ms": {}, "solve_ms": {}, "iterations": {}}
+        for label, prec in (("mixed", rt.RT_P_MIXED), ("fp64", rt.RT_P_FP64)):
+            if p.dims == 1:
+                m = RESTART_MIXED if label == "mixed" else RESTART
+            else:
+                m = 5 if big else 24
+            h = rt.Handle(p, n_rhs=1, precision=prec, max_restart=m)
+            x = torch.rand(p.n, dtype=torch.float64, device=dev)
+            y = torch.empty_like(x)
+            reps = 3 if big else 20
+            for _ in range(3):
+                h.rt_apply(rt.RT_OP_A, x, y)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                h.rt_apply(rt.RT_OP_A, x, y)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            entry["applies_ms"][label] = e0.elapsed_time(e1) / reps
+            b = y
+            h.rt_apply(rt.RT_OP_RHS, None, b, fp64=True)
+            if not big:
+                kw = dict(tol=1e-10, restart=m, max_outer=MAX_OUTER, tol_inner=TOL_INNER, inner_restart=INNER)
+                timed_solve(h, b, x, **kw)  # warm-up (graph capture, first touch)
+                entry["solve_ms"][label], entry["iterations"][label] = timed_solve(h, b, x, **kw)
+            if label == "fp64":
+                kw = dict(tol=1e-10, max_outer=10, method=rt.RT_KRYLOV_BICGSTAB, max_iter=150 if big else 0)
+                if not big:
+                    timed_solve(h, b, x, **kw)
+                key = "bicgstab_fp64"
+                entry["solve_ms"][key], entry["iterations"][key] = timed_solve(h, b, x, **kw)
+            h.close()
+            del x, y, b
+            torch.cuda.empty_cache()
+        out[name] = entry
+    return out
+
+
 def load_bf16_peak():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -461,6 +527,7 @@ def main():
         cb = cpu_baseline(n_inst, cores=os.cpu_count(), keep_solutions=True)
     res = run_ours(args, rank, world)
     tensor = tensor_roofline(rank) if rank == 0 else None
+    per_config = configs_sweep(rank) if rank == 0 else None
     if rank != 0:
         return
     accuracy = None
@@ -490,6 +557,7 @@ def main():
         "gpu_launches": args.steps,
         "roofline": res["roofline"],
         "roofline_tensor": tensor,
+        "configs": per_config,
         "clocks": res["clk"],
         "cpu_baseline": cb,
         "accuracy": accuracy,

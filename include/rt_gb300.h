@@ -62,6 +62,8 @@ enum { RT_OP_A = 0,      /* y = x - Lambda Sigma x          (eq. RT_sys_algebrai
        RT_OP_LAMBDA = 1, /* y = Lambda x, zero inflow       (eq. lambda_block)     */
        RT_OP_SIGMA = 2,  /* y = Sigma x, no thermal term    (eq. Sigma)            */
        RT_OP_RHS = 3 };  /* y = Lambda t + I_in; x unused   (eq. RT_sys_algebraic) */
+enum { RT_KRYLOV_GMRES = 0,      /* GMRES (fp64) / flexible GMRES + inner cycles (mixed) */
+       RT_KRYLOV_BICGSTAB = 1 }; /* BiCGStab in float64, either handle precision     */
 
 /* ---- one problem: a 1D column or a 3D box ----------------------------- */
 typedef struct rt_desc {
@@ -101,6 +103,11 @@ typedef struct rt_solve_opts {
   int32_t max_outer;     /* restart cycles allowed                                      */
   int32_t use_x0;        /* 1: x holds the initial guess on entry; 0: start from x = 0  */
   int32_t inner_restart; /* RT_P_MIXED: inner float32 GMRES cycle length (0 -> 20)      */
+  int32_t method;        /* RT_KRYLOV_GMRES (0) or RT_KRYLOV_BICGSTAB (1)               */
+  int32_t max_iter;      /* BiCGStab: iteration cap per instance (0 -> 10000); with
+                            BiCGStab, max_outer bounds the restarts from the true
+                            residual (taken when the recursive residual drifted or a
+                            coefficient broke down) and restart is ignored          */
 } rt_solve_opts;
 
 typedef struct rt_info {
@@ -192,16 +199,24 @@ int rt_autotune(rt_handle *h, int32_t flags, rt_tune_info *out, void *stream);
 int rt_apply_noalloc(rt_handle *h, int32_t op, int32_t fp64, const double *x, double *y, void *stream);
 
 /* Solve A_N x = b for all instances (eq. RT_sys_algebraic; the Krylov solvers
- * of Sec. 5, unpreconditioned).  b == NULL uses the internal right-hand side
- * Lambda t + I_in for every rhs.  RT_P_FP64: restarted GMRES(m) in float64
- * (classical Gram-Schmidt with the DGKS re-orthogonalisation test, Givens
- * rotations).  RT_P_MIXED: flexible GMRES(m) in float64 (Arnoldi,
- * Givens, the residual b - A x and x all float64) whose directions are refined
- * by one float32 GMRES(inner_restart) cycle on the float32 operator -- mixed
- * precision iterative refinement with a float64 Krylov outer loop.  Batches:
- * one persistent launch, a CTA per (column, rhs) instance; boxes: grid-wide
- * kernels.  x0 = 0 unless opts->use_x0.  Synchronises the stream and fills
- * *info (may be NULL).  Returns RT_ERR_NOCONV if any instance missed opts->tol
+ * of Sec. 5, GMRES and BiCGStab, unpreconditioned).  b == NULL uses the
+ * internal right-hand side Lambda t + I_in for every rhs.
+ * opts->method == RT_KRYLOV_GMRES:
+ *   RT_P_FP64: restarted GMRES(m) in float64 (classical Gram-Schmidt with the
+ *   DGKS re-orthogonalisation test, Givens rotations).  RT_P_MIXED: flexible
+ *   GMRES(m) in float64 (Arnoldi, Givens, the residual b - A x and x all
+ *   float64) whose directions come from one float32 GMRES(inner_restart)
+ *   cycle on the float32 operator (basis stored in binary16 for 1D batches)
+ *   -- a float64 Krylov loop around low-precision inner solves.
+ * opts->method == RT_KRYLOV_BICGSTAB: BiCGStab (van der Vorst) in float64
+ *   with the float64 operator on either handle precision; six float64 vectors
+ *   of workspace per instance (create the handle with max_restart >= 5 for
+ *   RT_P_FP64, >= 3 for RT_P_MIXED batches, >= 11 for RT_P_MIXED boxes), else
+ *   RT_ERR_ARG.  Converged only when the true residual b - A x meets tol.
+ * Batches: one persistent launch, a CTA per (column, rhs) instance; boxes:
+ * grid-wide kernels.  x0 = 0 unless opts->use_x0.  Synchronises the stream and
+ * fills *info (may be NULL; for BiCGStab max_inner counts iterations and
+ * max_outer restarts).  Returns RT_ERR_NOCONV if any instance missed opts->tol
  * (x still holds the last iterate). */
 int rt_solve(rt_handle *h, const double *b, double *x, const rt_solve_opts *opts,
              rt_info *info, void *stream);

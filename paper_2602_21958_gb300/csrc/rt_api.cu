@@ -885,12 +885,23 @@ int rt_autotune(rt_handle *h, int32_t flags, rt_tune_info *out, void *stream) {
 int rt_solve(rt_handle *h, const double *b, double *x, const rt_solve_opts *o, rt_info *info,
              void *stream) {
   if (!h || !x || !o) return fail(RT_ERR_ARG, "null handle, x or options");
-  if (o->restart < 1 || o->restart > h->ws.m) return fail(RT_ERR_ARG, "restart outside [1, max_restart]");
+  if (o->method != RT_KRYLOV_GMRES && o->method != RT_KRYLOV_BICGSTAB)
+    return fail(RT_ERR_ARG, "method must be RT_KRYLOV_GMRES or RT_KRYLOV_BICGSTAB");
+  const bool bicg = o->method == RT_KRYLOV_BICGSTAB;
   if (!(o->tol > 0.0) || o->max_outer < 1) return fail(RT_ERR_ARG, "need tol > 0 and max_outer >= 1");
-  if (h->precision == RT_P_MIXED && !(o->tol_inner > 0.0 && o->tol_inner < 1.0))
-    return fail(RT_ERR_ARG, "mixed precision needs 0 < tol_inner < 1");
-  if (o->inner_restart < 0 || o->inner_restart > h->ws.m)
-    return fail(RT_ERR_ARG, "inner_restart outside [0, max_restart]");
+  if (bicg) {
+    if (o->max_iter < 0) return fail(RT_ERR_ARG, "max_iter must be >= 0");
+    const bool fits = h->dims == 3 ? rt::grid_bicgstab_fits(h) : rt::bicgstab_fits(h);
+    if (!fits)
+      return fail(RT_ERR_ARG, "BiCGStab needs six float64 vectors of workspace per instance: "
+                              "create the handle with a larger max_restart");
+  } else {
+    if (o->restart < 1 || o->restart > h->ws.m) return fail(RT_ERR_ARG, "restart outside [1, max_restart]");
+    if (h->precision == RT_P_MIXED && !(o->tol_inner > 0.0 && o->tol_inner < 1.0))
+      return fail(RT_ERR_ARG, "mixed precision needs 0 < tol_inner < 1");
+    if (o->inner_restart < 0 || o->inner_restart > h->ws.m)
+      return fail(RT_ERR_ARG, "inner_restart outside [0, max_restart]");
+  }
   cudaStream_t s = (cudaStream_t)stream;
   const int64_t len = h->E * h->n_rhs;
   const bool bd = b ? is_device_ptr(b) : true, xd = is_device_ptr(x);
@@ -915,8 +926,10 @@ int rt_solve(rt_handle *h, const double *b, double *x, const rt_solve_opts *o, r
     RT_CUDA(cudaEventCreate(&e0));
     RT_CUDA(cudaEventCreate(&e1));
     RT_CUDA(cudaEventRecord(e0, s));
-    const int e = rt::launch_grid_solve(h, bin ? bin : h->b_int, xio, o->tol, o->tol_inner, o->restart,
-                                        o->max_outer, o->use_x0, s, outer, inner, relres, status, bytes);
+    const int e = bicg ? rt::launch_grid_bicgstab(h, bin ? bin : h->b_int, xio, o->tol, o->max_outer, o->max_iter,
+                                                  o->use_x0, s, outer, inner, relres, status, bytes)
+                       : rt::launch_grid_solve(h, bin ? bin : h->b_int, xio, o->tol, o->tol_inner, o->restart,
+                                               o->max_outer, o->use_x0, s, outer, inner, relres, status, bytes);
     RT_CUDA(cudaEventRecord(e1, s));
     if (e != 0) {
       cudaEventDestroy(e0);
@@ -961,7 +974,7 @@ int rt_solve(rt_handle *h, const double *b, double *x, const rt_solve_opts *o, r
   // the launch (queue reset + persistent kernel) is captured once into a CUDA
   // graph and replayed while (b, x, options) stay the same
   const int m_in = o->inner_restart > 0 ? o->inner_restart : 20;
-  unsigned long long key[8];
+  unsigned long long key[10];
   key[0] = (unsigned long long)(uintptr_t)bin;
   key[1] = (unsigned long long)(uintptr_t)xio;
   std::memcpy(&key[2], &o->tol, 8);
@@ -970,6 +983,8 @@ int rt_solve(rt_handle *h, const double *b, double *x, const rt_solve_opts *o, r
   key[5] = (unsigned long long)o->max_outer;
   key[6] = (unsigned long long)o->use_x0;
   key[7] = (unsigned long long)m_in;
+  key[8] = (unsigned long long)o->method;
+  key[9] = (unsigned long long)o->max_iter;
   int e = 0;
   if (!h->solve_graph || std::memcmp(key, h->graph_key, sizeof key) != 0) {
     if (h->solve_graph) {
@@ -979,8 +994,9 @@ int rt_solve(rt_handle *h, const double *b, double *x, const rt_solve_opts *o, r
     if (!h->capture_stream) RT_CUDA(cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking));
     cudaGraph_t graph = nullptr;
     RT_CUDA(cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeThreadLocal));
-    e = rt::launch_solve(h, bin, xio, o->tol, o->tol_inner, o->restart, o->max_outer, o->use_x0,
-                         h->capture_stream, m_in);
+    e = bicg ? rt::launch_bicgstab(h, bin, xio, o->tol, o->max_outer, o->max_iter, o->use_x0, h->capture_stream)
+             : rt::launch_solve(h, bin, xio, o->tol, o->tol_inner, o->restart, o->max_outer, o->use_x0,
+                                h->capture_stream, m_in);
     const cudaError_t ce = cudaStreamEndCapture(h->capture_stream, &graph);
     if (e == 0 && ce != cudaSuccess) e = (int)ce;
     if (e == 0) e = (int)cudaGraphInstantiate(&h->solve_graph, graph, 0);

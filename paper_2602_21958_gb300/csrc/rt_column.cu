@@ -109,6 +109,7 @@ struct SolveParams {
   double tol, tol_inner;
   int m, max_outer, use_x0;
   int m_in;             // mixed precision: inner float32 GMRES cycle length
+  int max_iter;         // BiCGStab: iteration cap
   void *V;              // [slots][cap] Krylov bases of one slot
   int64_t cap;          // fp64 path: basis capacity of one slot in elements; mixed: bytes
   double *S;            // [slots][ld] float64 scratch: source function / residual
@@ -1052,6 +1053,308 @@ __global__ void __launch_bounds__(kNT, 1) k_solve_nested(SolveParams p) {
   }
 }
 
+// ----------------------------------------------------------------- BiCGStab
+// BiCGStab (van der Vorst), float64 vectors and the float64 operator, one CTA
+// per (column, rhs) instance as k_solve.  Per iteration two operator
+// applications and four fused vector passes:
+//   p = r + beta (p - omega v)            (bicg_dir)
+//   v = A p;  alpha = rho / (r^, v)
+//   s = r - alpha v, ||s||^2              (bicg_s)
+//   t = A s;  omega = (t, s) / (t, t)
+//   x += alpha p + omega s; r = s - omega t; ||r||^2 and (r^, r)  (bicg_xr)
+// Convergence is declared only on the true residual b - A x; when the
+// recursive residual has drifted, or rho / (r^, v) / omega break down, the
+// iteration restarts from the true residual (at most max_outer times).
+// Every loop handles kU elements per thread with all loads issued first.
+__device__ __noinline__ void bicg_dir(double *__restrict__ p, const double *__restrict__ r,
+                                      const double *__restrict__ v, double beta, double omega, int64_t n) {
+  for (int64_t k0 = threadIdx.x; k0 < n; k0 += (int64_t)kU * blockDim.x) {
+    double a[kU], b[kU], c[kU];
+#pragma unroll
+    for (int e = 0; e < kU; ++e) {
+      const int64_t k = k0 + (int64_t)e * blockDim.x;
+      const bool in = k < n;
+      a[e] = in ? r[k] : 0.0;
+      b[e] = in ? p[k] : 0.0;
+      c[e] = in ? v[k] : 0.0;
+    }
+#pragma unroll
+    for (int e = 0; e < kU; ++e) {
+      const int64_t k = k0 + (int64_t)e * blockDim.x;
+      if (k < n) p[k] = a[e] + beta * (b[e] - omega * c[e]);
+    }
+  }
+  __syncthreads();
+}
+
+// (a, b) and, when c is given, (c, d), float64 block sums
+__device__ __noinline__ void bicg_dots(const double *__restrict__ a, const double *__restrict__ b,
+                                       const double *__restrict__ c, const double *__restrict__ d, int64_t n,
+                                       double *red, double *outb, double &ab, double &cd) {
+  double acc[2] = {0.0, 0.0};
+  for (int64_t k0 = threadIdx.x; k0 < n; k0 += (int64_t)kU * blockDim.x) {
+    double x0[kU], x1[kU], y0[kU], y1[kU];
+#pragma unroll
+    for (int e = 0; e < kU; ++e) {
+      const int64_t k = k0 + (int64_t)e * blockDim.x;
+      const bool in = k < n;
+      x0[e] = in ? a[k] : 0.0;
+      x1[e] = in ? b[k] : 0.0;
+      y0[e] = in && c ? c[k] : 0.0;
+      y1[e] = in && c ? d[k] : 0.0;
+    }
+#pragma unroll
+    for (int e = 0; e < kU; ++e) {
+      acc[0] = fma(x0[e], x1[e], acc[0]);
+      acc[1] = fma(y0[e], y1[e], acc[1]);
+    }
+  }
+  block_sum<2>(acc, red, outb);
+  ab = acc[0];
+  cd = acc[1];
+}
+
+// s = r - alpha v; returns ||s||^2
+__device__ __noinline__ double bicg_s(double *__restrict__ s, const double *__restrict__ r,
+                                      const double *__restrict__ v, double alpha, int64_t n, double *red,
+                                      double *outb) {
+  double acc[1] = {0.0};
+  for (int64_t k0 = threadIdx.x; k0 < n; k0 += (int64_t)kU * blockDim.x) {
+    double a[kU], c[kU];
+#pragma unroll
+    for (int e = 0; e < kU; ++e) {
+      const int64_t k = k0 + (int64_t)e * blockDim.x;
+      const bool in = k < n;
+      a[e] = in ? r[k] : 0.0;
+      c[e] = in ? v[k] : 0.0;
+    }
+#pragma unroll
+    for (int e = 0; e < kU; ++e) {
+      const int64_t k = k0 + (int64_t)e * blockDim.x;
+      const double sv = a[e] - alpha * c[e];
+      if (k < n) s[k] = sv;
+      acc[0] = fma(sv, sv, acc[0]);
+    }
+  }
+  block_sum<1>(acc, red, outb);
+  return acc[0];
+}
+
+// x += alpha p + omega s (p only when s is null); r = s - omega t (when t is
+// given) with ||r||^2 and (r^, r) returned through rr, rhr
+__device__ __noinline__ void bicg_xr(double *__restrict__ x, const double *__restrict__ p,
+                                     const double *__restrict__ s, const double *__restrict__ t,
+                                     double *__restrict__ r, const double *__restrict__ rh, double alpha,
+                                     double omega, int64_t n, double *red, double *outb, double &rr,
+                                     double &rhr) {
+  double acc[2] = {0.0, 0.0};
+  for (int64_t k0 = threadIdx.x; k0 < n; k0 += (int64_t)kU * blockDim.x) {
+    double xv[kU], pv[kU], sv[kU], tv[kU], hv[kU];
+#pragma unroll
+    for (int e = 0; e < kU; ++e) {
+      const int64_t k = k0 + (int64_t)e * blockDim.x;
+      const bool in = k < n;
+      xv[e] = in ? x[k] : 0.0;
+      pv[e] = in ? p[k] : 0.0;
+      sv[e] = in && s ? s[k] : 0.0;
+      tv[e] = in && t ? t[k] : 0.0;
+      hv[e] = in && t ? rh[k] : 0.0;
+    }
+#pragma unroll
+    for (int e = 0; e < kU; ++e) {
+      const int64_t k = k0 + (int64_t)e * blockDim.x;
+      if (k < n) x[k] = xv[e] + alpha * pv[e] + omega * sv[e];
+      if (t) {
+        const double rv = sv[e] - omega * tv[e];
+        if (k < n) r[k] = rv;
+        acc[0] = fma(rv, rv, acc[0]);
+        acc[1] = fma(hv[e], rv, acc[1]);
+      }
+    }
+  }
+  block_sum<2>(acc, red, outb);
+  rr = acc[0];
+  rhr = acc[1];
+}
+
+__global__ void __launch_bounds__(kNT, 1) k_solve_bicgstab(SolveParams p) {
+  __shared__ double sm[4 * kSigBuf];
+  __shared__ double red[(kNT / 32) * (kDots + 1)];
+  __shared__ double outb[kDots + 1];
+  __shared__ int s_q;
+  double *slot = reinterpret_cast<double *>(p.V) + (int64_t)blockIdx.x * p.cap;  // cap in float64 elements
+  double *S64 = p.S + (int64_t)blockIdx.x * p.ld;
+  for (;;) {
+    const int q = next_instance(p.queue, &s_q);
+    if (q >= p.n_inst) break;
+    const int inst = p.order[q];
+    const int ci = inst % p.n_cols, rhs = inst / p.n_cols;
+    const ColDev c = p.cm.cols[ci];
+    const int64_t n = (int64_t)c.nz * c.nr;
+    const int64_t ldv = (n + 31) / 32 * 32;
+    double *r = slot, *rh = r + ldv, *pv = rh + ldv, *v = pv + ldv, *sv = v + ldv, *t = sv + ldv;
+    const double *bv = p.b + (p.b_shared ? 0 : rhs * p.E) + c.x_off;
+    double *x = p.x + rhs * p.E + c.x_off;
+    auto apply = [&](const double *X, double *Y) {  // Y = A X, float64
+      sigma_column<double, double>(c, p.t64, X, S64, sm, 4 * kSigBuf);
+      sweep_column<double, double, double, 2>(c, p.t64, p.cm, S64, nullptr, X, nullptr, Y, kOutAminus, false);
+      __syncthreads();
+    };
+    auto true_resid = [&]() -> double {  // r = b - A x, returns ||r||
+      sigma_column<double, double>(c, p.t64, x, S64, sm, 4 * kSigBuf);
+      double a[1] = {sweep_column<double, double, double, 2>(c, p.t64, p.cm, S64, nullptr, x, bv, r, kOutResid,
+                                                             false)};
+      block_sum<1>(a, red, outb);
+      return sqrt(a[0]);
+    };
+    const double bn = sqrt(cta_norm2(bv, n, red, outb));
+    double bpe = 8.0;
+    int status = kNoConv, it = 0, restarts = 0;
+    double rn;
+    if (!p.use_x0) {
+      for (int64_t k = threadIdx.x; k < n; k += blockDim.x) {
+        x[k] = 0.0;
+        r[k] = bv[k];
+      }
+      __syncthreads();
+      rn = bn;
+      bpe += 24.0;
+    } else {
+      rn = true_resid();
+      bpe += 48.0;
+    }
+    double rho = 0.0, rho_old = 1.0, alpha = 1.0, omega = 1.0;
+    auto reset = [&]() {  // shadow residual = current residual, empty search space
+      for (int64_t k = threadIdx.x; k < n; k += blockDim.x) {
+        rh[k] = r[k];
+        pv[k] = 0.0;
+        v[k] = 0.0;
+      }
+      __syncthreads();
+      rho = rn * rn;
+      rho_old = alpha = omega = 1.0;
+      bpe += 32.0;
+    };
+    const int max_iter = p.max_iter > 0 ? p.max_iter : 10000;
+    const bool bad_b = !(bn == bn) || bn > 1e300;
+    if (bad_b) status = kNonFinite;
+    else if (bn == 0.0) { status = kConverged; rn = 0.0; }
+    else reset();
+    bool rn_true = false;  // rn is the true residual norm (not the recursive one)
+    while (!bad_b && bn > 0.0) {
+      if (!(rn == rn) || rn > 1e300) { status = kNonFinite; break; }
+      int restart = 0;  // 1: recursive residual drifted, 2: a coefficient broke down
+      if (rn <= p.tol * bn) {  // confirm on the true residual
+        rn = true_resid();
+        rn_true = true;
+        bpe += 48.0;
+        if (rn <= p.tol * bn) { status = kConverged; break; }
+        restart = 1;
+      } else if (it >= max_iter) {
+        break;
+      } else if (!(rho != 0.0 && rho == rho) || !(omega != 0.0)) {
+        rn = true_resid();
+        rn_true = true;
+        bpe += 48.0;
+        restart = 2;
+      }
+      if (restart) {
+        if (restarts >= p.max_outer) { status = restart == 2 ? kBreakdown : kNoConv; break; }
+        ++restarts;
+        reset();
+        continue;
+      }
+      const double beta = (rho / rho_old) * (alpha / omega);
+      bicg_dir(pv, r, v, beta, omega, n);
+      apply(pv, v);
+      double rv = 0.0, unused = 0.0;
+      bicg_dots(rh, v, nullptr, nullptr, n, red, outb, rv, unused);
+      bpe += 32.0 + 40.0 + 16.0;
+      ++it;
+      if (!(rv != 0.0 && rv == rv)) {
+        rn = true_resid();
+        rn_true = true;
+        bpe += 48.0;
+        if (rn <= p.tol * bn) { status = kConverged; break; }
+        if (restarts >= p.max_outer) { status = kBreakdown; break; }
+        ++restarts;
+        reset();
+        continue;
+      }
+      alpha = rho / rv;
+      const double sn = sqrt(bicg_s(sv, r, v, alpha, n, red, outb));
+      bpe += 24.0;
+      if (sn <= p.tol * bn) {  // half step: x += alpha p, then the true-residual check
+        double d0 = 0.0, d1 = 0.0;
+        bicg_xr(x, pv, nullptr, nullptr, nullptr, nullptr, alpha, 0.0, n, red, outb, d0, d1);
+        bpe += 24.0;
+        rn = sn;
+        rn_true = false;
+        continue;
+      }
+      apply(sv, t);
+      double ts = 0.0, tt = 0.0;
+      bicg_dots(t, sv, t, t, n, red, outb, ts, tt);
+      omega = tt > 0.0 ? ts / tt : 0.0;
+      double rr = 0.0, rhr = 0.0;
+      bicg_xr(x, pv, sv, t, r, rh, alpha, omega, n, red, outb, rr, rhr);
+      bpe += 40.0 + 16.0 + 56.0;
+      rn = sqrt(rr);
+      rn_true = false;
+      rho_old = rho;
+      rho = rhr;
+    }
+    if (status != kConverged && status != kNonFinite && !rn_true && bn > 0.0) {  // report the true residual
+      rn = true_resid();
+      bpe += 48.0;
+    }
+    if (threadIdx.x == 0) {
+      p.out.outer[inst] = restarts;
+      p.out.inner[inst] = it;
+      p.out.status[inst] = status;
+      p.out.relres[inst] = bn > 0.0 ? rn / bn : 0.0;
+      p.out.bytes[inst] = bpe * (double)n;
+    }
+    __syncthreads();
+  }
+}
+
+int launch_bicgstab(rt_handle *h, const double *b, double *x, double tol, int max_outer, int max_iter,
+                    int use_x0, cudaStream_t s) {
+  SolveParams p;
+  p.cm = Common{h->d_cols, h->d_dir_cls, h->d_dir_up, h->d_tsrc, h->d_Itop, h->d_Ibot};
+  p.t64 = Tables<double>{h->E64, h->A64, h->B64, h->Uw64, h->Ul64, h->Rw64, h->Psi64, h->gam64};
+  p.t32 = Tables<float>{h->E32, h->A32, h->B32, h->Uw32, h->Ul32, h->Rw32, h->Psi32, h->gam32};
+  p.order = h->d_order;
+  p.n_cols = h->n_cols;
+  p.n_inst = h->n_cols * h->n_rhs;
+  p.E = h->E;
+  p.b = b ? b : h->b_int;
+  p.b_shared = b ? 0 : 1;
+  p.x = x;
+  p.tol = tol;
+  p.tol_inner = 0.0;
+  p.m = 0;
+  p.max_outer = max_outer;
+  p.max_iter = max_iter;
+  p.use_x0 = use_x0;
+  p.V = h->ws.V;
+  p.cap = h->ws.cap_bytes / 8;  // float64 elements per slot
+  p.m_in = 0;
+  p.S = h->ws.S;
+  p.ld = h->ws.ld;
+  p.H = h->ws.H;
+  p.hld = h->ws.hld;
+  p.queue = h->d_queue + 1;
+  p.out = h->so;
+  cudaError_t e = cudaMemsetAsync(h->d_queue + 1, 0, sizeof(int), s);
+  if (e != cudaSuccess) return (int)e;
+  k_solve_bicgstab<<<h->ws.slots, kNT, 0, s>>>(p);
+  return (int)cudaGetLastError();
+}
+
+bool bicgstab_fits(const rt_handle *h) { return h->ws.cap_bytes >= 6 * h->ws.ld * 8; }
+
 int launch_solve(rt_handle *h, const double *b, double *x, double tol, double tol_inner, int m,
                  int max_outer, int use_x0, cudaStream_t s, int m_in) {
   SolveParams p;
@@ -1073,6 +1376,7 @@ int launch_solve(rt_handle *h, const double *b, double *x, double tol, double to
   p.V = h->ws.V;
   p.cap = h->precision == 0 ? h->ws.cap_bytes / 8 : h->ws.cap_bytes;
   p.m_in = m_in;
+  p.max_iter = 0;
   p.S = h->ws.S;
   p.ld = h->ws.ld;
   p.H = h->ws.H;

@@ -286,6 +286,194 @@ static int grid_solve(rt_handle *h, const double *b, double *x, double tol, doub
   }
 }
 
+// ------------------------------------------------------- BiCGStab (grid-wide)
+// The float64 BiCGStab of k_solve_bicgstab for one big problem: the same
+// recurrences, each fused vector pass one grid-wide kernel, the scalars on
+// the host.  Partial sums per CTA, reduced by k_greduce.
+__global__ void __launch_bounds__(kGT) k_gb_dir(double *p, const double *r, const double *v, double beta,
+                                                double omega, int64_t n) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+    p[k] = r[k] + beta * (p[k] - omega * v[k]);
+}
+
+// partial[blk][0] = (a, b), partial[blk][1] = (c, d) (0 when c is null)
+__global__ void __launch_bounds__(kGT) k_gb_dots(const double *a, const double *b, const double *c,
+                                                 const double *d, int64_t n, double *partial) {
+  __shared__ double red[(kGT / 32) * 2];
+  __shared__ double outb[2];
+  double acc[2] = {0.0, 0.0};
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+    acc[0] = fma(a[k], b[k], acc[0]);
+    if (c) acc[1] = fma(c[k], d[k], acc[1]);
+  }
+  block_sum<2>(acc, red, outb);
+  if (threadIdx.x < 2) partial[(int64_t)blockIdx.x * 2 + threadIdx.x] = acc[threadIdx.x];
+}
+
+// s = r - alpha v, partial ||s||^2
+__global__ void __launch_bounds__(kGT) k_gb_s(double *s, const double *r, const double *v, double alpha,
+                                              int64_t n, double *partial) {
+  __shared__ double red[kGT / 32];
+  __shared__ double outb[1];
+  double acc[1] = {0.0};
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+    const double sv = r[k] - alpha * v[k];
+    s[k] = sv;
+    acc[0] = fma(sv, sv, acc[0]);
+  }
+  block_sum<1>(acc, red, outb);
+  if (threadIdx.x == 0) partial[blockIdx.x] = acc[0];
+}
+
+// x += alpha p + omega s; r = s - omega t; partial ||r||^2, (r^, r)
+__global__ void __launch_bounds__(kGT) k_gb_xr(double *x, const double *p, const double *s, const double *t,
+                                               double *r, const double *rh, double alpha, double omega, int64_t n,
+                                               double *partial) {
+  __shared__ double red[(kGT / 32) * 2];
+  __shared__ double outb[2];
+  double acc[2] = {0.0, 0.0};
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+    const double sv = s[k];
+    x[k] += alpha * p[k] + omega * sv;
+    const double rv = sv - omega * t[k];
+    r[k] = rv;
+    acc[0] = fma(rv, rv, acc[0]);
+    acc[1] = fma(rh[k], rv, acc[1]);
+  }
+  block_sum<2>(acc, red, outb);
+  if (threadIdx.x < 2) partial[(int64_t)blockIdx.x * 2 + threadIdx.x] = acc[threadIdx.x];
+}
+
+__global__ void k_gb_axpy(double *x, const double *p, double alpha, int64_t n) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+    x[k] += alpha * p[k];
+}
+
+int launch_grid_bicgstab(rt_handle *h, const double *b, double *x, double tol, int max_outer, int max_iter,
+                         int use_x0, cudaStream_t s, int &restarts, int &iters, double &relres, int &status,
+                         double &bytes) {
+  const int64_t n = h->E;
+  const int64_t ldv = (n + 31) / 32 * 32;
+  GridCtx g{h, s, grid_ctas(h), h->g_part, h->g_red, h->g_coef, {}};
+  double *r = static_cast<double *>(h->ws.V);
+  double *rh = r + ldv, *pv = rh + ldv, *v = pv + ldv, *sv = v + ldv, *t = sv + ldv;
+  auto apply = [&](const double *X, double *Y) -> int { return apply_box(h, 0, true, X, false, Y, false, s); };
+  auto true_resid = [&](double &rn) -> int {  // r = b - A x
+    int e = apply(x, r);
+    if (e) return e;
+    k_gresid<<<g.G, kGT, 0, s>>>(b, r, n, g.part);
+    double rn2 = 0.0;
+    e = reduce_to_host(g, 1, &rn2);
+    rn = std::sqrt(rn2);
+    bytes += 64.0 * n;
+    return e;
+  };
+  bytes = 0.0;
+  restarts = iters = 0;
+  status = 4;
+  k_gnorm<<<g.G, kGT, 0, s>>>(b, n, g.part);
+  double bn2 = 0.0;
+  int e = reduce_to_host(g, 1, &bn2);
+  if (e) return e;
+  const double bn = std::sqrt(bn2);
+  bytes += 8.0 * n;
+  relres = 1.0;
+  if (!std::isfinite(bn)) { status = 6; return 0; }
+  if (!use_x0) cudaMemsetAsync(x, 0, n * sizeof(double), s);
+  if (bn == 0.0) { status = 0; relres = 0.0; return 0; }
+  double rn = bn;
+  if (use_x0) {
+    if ((e = true_resid(rn))) return e;
+  } else {
+    cudaMemcpyAsync(r, b, n * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    bytes += 16.0 * n;
+  }
+  double rho = 0.0, rho_old = 1.0, alpha = 1.0, omega = 1.0;
+  auto reset = [&]() {
+    cudaMemcpyAsync(rh, r, n * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    cudaMemsetAsync(pv, 0, n * sizeof(double), s);
+    cudaMemsetAsync(v, 0, n * sizeof(double), s);
+    rho = rn * rn;
+    rho_old = alpha = omega = 1.0;
+    bytes += 32.0 * n;
+  };
+  reset();
+  const int cap = max_iter > 0 ? max_iter : 10000;
+  bool rn_true = use_x0;
+  for (;;) {
+    if (!std::isfinite(rn)) { status = 6; break; }
+    int restart = 0;
+    if (rn <= tol * bn) {
+      if ((e = true_resid(rn))) return e;
+      rn_true = true;
+      if (rn <= tol * bn) { status = 0; break; }
+      restart = 1;
+    } else if (iters >= cap) {
+      break;
+    } else if (!(rho != 0.0 && std::isfinite(rho)) || omega == 0.0) {
+      if ((e = true_resid(rn))) return e;
+      rn_true = true;
+      restart = 2;
+    }
+    if (restart) {
+      if (restarts >= max_outer) { status = restart == 2 ? 5 : 4; break; }
+      ++restarts;
+      reset();
+      continue;
+    }
+    const double beta = (rho / rho_old) * (alpha / omega);
+    k_gb_dir<<<g.G, kGT, 0, s>>>(pv, r, v, beta, omega, n);
+    if ((e = apply(pv, v))) return e;
+    double d2[2];
+    k_gb_dots<<<g.G, kGT, 0, s>>>(rh, v, nullptr, nullptr, n, g.part);
+    if ((e = reduce_to_host(g, 2, d2))) return e;
+    bytes += (32.0 + 40.0 + 16.0) * n;
+    ++iters;
+    const double rv = d2[0];
+    if (!(rv != 0.0 && std::isfinite(rv))) {
+      if ((e = true_resid(rn))) return e;
+      rn_true = true;
+      if (rn <= tol * bn) { status = 0; break; }
+      if (restarts >= max_outer) { status = 5; break; }
+      ++restarts;
+      reset();
+      continue;
+    }
+    alpha = rho / rv;
+    k_gb_s<<<g.G, kGT, 0, s>>>(sv, r, v, alpha, n, g.part);
+    double sn2 = 0.0;
+    if ((e = reduce_to_host(g, 1, &sn2))) return e;
+    bytes += 24.0 * n;
+    if (std::sqrt(sn2) <= tol * bn) {
+      k_gb_axpy<<<g.G, kGT, 0, s>>>(x, pv, alpha, n);
+      bytes += 24.0 * n;
+      rn = std::sqrt(sn2);
+      rn_true = false;
+      continue;
+    }
+    if ((e = apply(sv, t))) return e;
+    k_gb_dots<<<g.G, kGT, 0, s>>>(t, sv, t, t, n, g.part);
+    if ((e = reduce_to_host(g, 2, d2))) return e;
+    omega = d2[1] > 0.0 ? d2[0] / d2[1] : 0.0;
+    k_gb_xr<<<g.G, kGT, 0, s>>>(x, pv, sv, t, r, rh, alpha, omega, n, g.part);
+    if ((e = reduce_to_host(g, 2, d2))) return e;
+    bytes += (40.0 + 16.0 + 56.0) * n;
+    rn = std::sqrt(d2[0]);
+    rn_true = false;
+    rho_old = rho;
+    rho = d2[1];
+  }
+  if (status != 0 && status != 6 && !rn_true)
+    if ((e = true_resid(rn))) return e;
+  relres = rn / bn;
+  return (int)cudaGetLastError();
+}
+
+bool grid_bicgstab_fits(const rt_handle *h) {
+  const int64_t ldv = (h->E + 31) / 32 * 32;
+  return h->ws.cap_bytes >= 6 * ldv * 8;
+}
+
 int launch_grid_solve(rt_handle *h, const double *b, double *x, double tol, double tol_inner, int m,
                       int max_outer, int use_x0, cudaStream_t s, int &outer, int &inner, double &relres,
                       int &status, double &bytes) {

@@ -83,7 +83,7 @@ struct rt_handle {
   // while the call signature (b, x, options) repeats
   cudaGraphExec_t solve_graph = nullptr;
   cudaStream_t capture_stream = nullptr;
-  unsigned long long graph_key[8] = {};
+  unsigned long long graph_key[10] = {};
   int graph_replays = 0;
   rt::Tune tune{};
   rt::BoxDev box{};
@@ -113,6 +113,13 @@ int tc_prepare(rt_handle *h, const std::vector<double> &psiwT);
 int launch_sweep3d(rt_handle *h, bool fp64, const void *S, const double *tsrc, const void *x, bool xf,
                    void *y, bool yf, int out, bool inflow, cudaStream_t s);
 int apply_box(rt_handle *h, int op, bool fp64, const void *x, bool xf, void *y, bool yf, cudaStream_t s);
+int launch_bicgstab(rt_handle *h, const double *b, double *x, double tol, int max_outer, int max_iter,
+                    int use_x0, cudaStream_t s);
+bool bicgstab_fits(const rt_handle *h);
+int launch_grid_bicgstab(rt_handle *h, const double *b, double *x, double tol, int max_outer, int max_iter,
+                         int use_x0, cudaStream_t s, int &restarts, int &iters, double &relres, int &status,
+                         double &bytes);
+bool grid_bicgstab_fits(const rt_handle *h);
 int launch_grid_solve(rt_handle *h, const double *b, double *x, double tol, double tol_inner, int m,
                       int max_outer, int use_x0, cudaStream_t s, int &outer, int &inner, double &relres,
                       int &status, double &bytes);

@@ -22,6 +22,7 @@ RT_OK, RT_ERR_ARG, RT_ERR_CUDA, RT_ERR_OOM, RT_ERR_NOCONV, RT_ERR_BREAKDOWN, RT_
 RT_FS_SCL, RT_FS_IE = 0, 1
 RT_P_FP64, RT_P_MIXED = 0, 1
 RT_OP_A, RT_OP_LAMBDA, RT_OP_SIGMA, RT_OP_RHS = 0, 1, 2, 3
+RT_KRYLOV_GMRES, RT_KRYLOV_BICGSTAB = 0, 1
 
 _dp = C.POINTER(C.c_double)
 
@@ -36,7 +37,8 @@ class rt_desc(C.Structure):
 
 class rt_solve_opts(C.Structure):
     _fields_ = [("tol", C.c_double), ("tol_inner", C.c_double), ("restart", C.c_int32),
-                ("max_outer", C.c_int32), ("use_x0", C.c_int32), ("inner_restart", C.c_int32)]
+                ("max_outer", C.c_int32), ("use_x0", C.c_int32), ("inner_restart", C.c_int32),
+                ("method", C.c_int32), ("max_iter", C.c_int32)]
 
 
 class rt_info(C.Structure):
@@ -203,8 +205,10 @@ class Handle:
 
     def rt_solve(self, b, x, tol: float = 1e-11, tol_inner: float = 0.1, restart: Optional[int] = None,
                  max_outer: int = 50, use_x0: bool = False, stream=None, per_instance: bool = False,
-                 raise_on_noconv: bool = False, inner_restart: int = 0) -> dict:
-        o = rt_solve_opts(tol, tol_inner, restart or self.max_restart, max_outer, int(use_x0), inner_restart)
+                 raise_on_noconv: bool = False, inner_restart: int = 0, method: int = RT_KRYLOV_GMRES,
+                 max_iter: int = 0) -> dict:
+        o = rt_solve_opts(tol, tol_inner, restart or self.max_restart, max_outer, int(use_x0), inner_restart,
+                          method, max_iter)
         info = rt_info()
         n_inst = len(self.problems) * self.n_rhs
         arrs = None
