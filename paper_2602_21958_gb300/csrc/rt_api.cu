@@ -521,6 +521,17 @@ int create_columns(const rt_desc *descs, int n_cols, int n_rhs, int precision, i
     free_handle(h);
     return fail(RT_ERR_CUDA, std::string("internal rhs: ") + cudaGetErrorString(ce));
   }
+  if (rt::single_instance(h)) {  // one (column, rhs): solved by the grid-wide kernels
+    const int G = rt::grid_ctas(h);
+    ce = cudaMalloc(&h->g_r, (size_t)h->ws.ld * sizeof(double));
+    if (ce == cudaSuccess) ce = cudaMalloc(&h->g_part, (size_t)G * 16 * sizeof(double));
+    if (ce == cudaSuccess) ce = cudaMalloc(&h->g_red, 64 * sizeof(double));
+    if (ce == cudaSuccess) ce = cudaMalloc(&h->g_coef, 1024 * sizeof(double));
+    if (ce != cudaSuccess) {
+      free_handle(h);
+      return fail(RT_ERR_OOM, "grid solve buffers");
+    }
+  }
   *out = h;
   return RT_OK;
 }
@@ -919,7 +930,10 @@ int rt_solve(rt_handle *h, const double *b, double *x, const rt_solve_opts *o, r
       xio = h->stage_x;
     }
   }
-  if (h->dims == 3) {
+  // boxes, and single 1D instances with a float64 Krylov loop, run on the
+  // grid-wide kernels; a single mixed instance keeps the nested solver (one
+  // CTA), whose inner Krylov spaces survive the refinement steps
+  if (h->dims == 3 || (rt::single_instance(h) && (bicg || h->precision == RT_P_FP64))) {
     int outer = 0, inner = 0, status = 0;
     double relres = 1.0, bytes = 0.0;
     cudaEvent_t e0, e1;

@@ -5,6 +5,7 @@
 // by one CTA), fused update + normalisation.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -170,13 +171,14 @@ static int update(GridCtx &g, const TL *V, int64_t ldv, const std::vector<double
 
 // Restarted GMRES(m) with float64 refinement for one big problem (n_rhs == 1).
 // apply64(x, y) writes y = A x in float64; applyL(v, w) writes w = A v in TL.
+// mixed: applyL is the low-precision operator, each inner cycle stops at a
+// reduction of tol_inner (else at the final tolerance).
 template <typename TL, typename F64, typename FL>
 static int grid_solve(rt_handle *h, const double *b, double *x, double tol, double tol_inner, int m,
-                      int max_outer, int use_x0, cudaStream_t s, F64 apply64, FL applyL, int &outer_out,
-                      int &inner_out, double &relres_out, int &status, double &bytes) {
+                      int max_outer, int use_x0, cudaStream_t s, F64 apply64, FL applyL, bool mixed,
+                      int &outer_out, int &inner_out, double &relres_out, int &status, double &bytes) {
   const int64_t n = h->E;
   const int64_t ldv = (n + 31) / 32 * 32;
-  const bool mixed = sizeof(TL) == 4;
   GridCtx g{h, s, grid_ctas(h), h->g_part, h->g_red, h->g_coef, {}};
   TL *V = static_cast<TL *>(h->ws.V);
   double *r = h->g_r;  // float64 residual
@@ -357,7 +359,9 @@ int launch_grid_bicgstab(rt_handle *h, const double *b, double *x, double tol, i
   GridCtx g{h, s, grid_ctas(h), h->g_part, h->g_red, h->g_coef, {}};
   double *r = static_cast<double *>(h->ws.V);
   double *rh = r + ldv, *pv = rh + ldv, *v = pv + ldv, *sv = v + ldv, *t = sv + ldv;
-  auto apply = [&](const double *X, double *Y) -> int { return apply_box(h, 0, true, X, false, Y, false, s); };
+  auto apply = [&](const double *X, double *Y) -> int {
+    return h->dims == 3 ? apply_box(h, 0, true, X, false, Y, false, s) : launch_apply(h, 0, true, X, Y, s, false);
+  };
   auto true_resid = [&](double &rn) -> int {  // r = b - A x
     int e = apply(x, r);
     if (e) return e;
@@ -477,14 +481,22 @@ bool grid_bicgstab_fits(const rt_handle *h) {
 int launch_grid_solve(rt_handle *h, const double *b, double *x, double tol, double tol_inner, int m,
                       int max_outer, int use_x0, cudaStream_t s, int &outer, int &inner, double &relres,
                       int &status, double &bytes) {
+  if (h->dims == 1) {  // one 1D instance, float64 GMRES: the batched apply kernels over the whole GPU
+    const int64_t ldv = (h->E + 31) / 32 * 32;
+    m = std::min<int64_t>(m, h->ws.cap_bytes / (8 * ldv) - 1);
+    if (m < 1) return (int)cudaErrorInvalidValue;
+    auto apply64 = [&](const double *xx, double *yy) -> int { return launch_apply(h, 0, true, xx, yy, s, false); };
+    return grid_solve<double>(h, b, x, tol, tol_inner, m, max_outer, use_x0, s, apply64, apply64, false, outer,
+                              inner, relres, status, bytes);
+  }
   auto apply64 = [&](const double *xx, double *yy) -> int { return apply_box(h, 0, true, xx, false, yy, false, s); };
   if (h->precision == 0) {
     auto applyL = [&](const double *v, double *w) -> int { return apply_box(h, 0, true, v, false, w, false, s); };
-    return grid_solve<double>(h, b, x, tol, tol_inner, m, max_outer, use_x0, s, apply64, applyL, outer, inner,
-                              relres, status, bytes);
+    return grid_solve<double>(h, b, x, tol, tol_inner, m, max_outer, use_x0, s, apply64, applyL, false, outer,
+                              inner, relres, status, bytes);
   }
   auto applyL = [&](const float *v, float *w) -> int { return apply_box(h, 0, false, v, true, w, true, s); };
-  return grid_solve<float>(h, b, x, tol, tol_inner, m, max_outer, use_x0, s, apply64, applyL, outer, inner,
+  return grid_solve<float>(h, b, x, tol, tol_inner, m, max_outer, use_x0, s, apply64, applyL, true, outer, inner,
                            relres, status, bytes);
 }
 

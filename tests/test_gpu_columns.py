@@ -114,31 +114,37 @@ def test_host_buffers_match_device_buffers(rt):
     assert np.array_equal(y_host, y_dev.cpu().numpy())
 
 
+# n_rhs = 1: one instance, solved by the grid-wide kernels; n_rhs = 2: two
+# instances, one CTA each (the batched solve kernels)
+@pytest.mark.parametrize("n_rhs", [1, 2])
 @pytest.mark.parametrize("name", ["crd", "r2_ragged", "mono_ie", "iso_coh", "dense", "minimal"])
-def test_solve_fp64_matches_lu(rt, name):
+def test_solve_fp64_matches_lu(rt, name, n_rhs):
     p = small_problems()[name]
-    h = rt.Handle(p, precision=rt.RT_P_FP64, max_restart=64)
+    h = rt.Handle(p, n_rhs=n_rhs, precision=rt.RT_P_FP64, max_restart=64)
     b = O.rhs(p) if p.t_src is not None else np.ones(p.n)
-    x = torch.zeros(p.n, dtype=torch.float64, device="cuda:0")
-    info = h.rt_solve(dev(b), x, tol=1e-14, restart=64, max_outer=20)
+    x = torch.zeros(n_rhs * p.n, dtype=torch.float64, device="cuda:0")
+    info = h.rt_solve(dev(np.tile(b, n_rhs)), x, tol=1e-14, restart=64, max_outer=20)
     torch.cuda.synchronize()
     xref = np.linalg.solve(O.assemble_A(p), b)
-    a, _ = rel(x.cpu().numpy(), xref)
-    assert a < FP64_TOL * 10, (a, info)
+    for r in range(n_rhs):
+        a, _ = rel(x.cpu().numpy()[r * p.n:(r + 1) * p.n], xref)
+        assert a < FP64_TOL * 10, (a, info)
 
 
+@pytest.mark.parametrize("n_rhs", [1, 2])
 @pytest.mark.parametrize("name", ["crd", "r2_ragged", "iso_coh", "dense"])
-def test_solve_mixed_refinement_matches_lu(rt, name):
+def test_solve_mixed_refinement_matches_lu(rt, name, n_rhs):
     p = small_problems()[name]
-    h = rt.Handle(p, precision=rt.RT_P_MIXED, max_restart=64)
+    h = rt.Handle(p, n_rhs=n_rhs, precision=rt.RT_P_MIXED, max_restart=64)
     b = O.rhs(p)
-    x = torch.zeros(p.n, dtype=torch.float64, device="cuda:0")
-    info = h.rt_solve(dev(b), x, tol=1e-12, tol_inner=1e-4, restart=64, max_outer=30)
+    x = torch.zeros(n_rhs * p.n, dtype=torch.float64, device="cuda:0")
+    info = h.rt_solve(dev(np.tile(b, n_rhs)), x, tol=1e-12, tol_inner=1e-4, restart=64, max_outer=30)
     torch.cuda.synchronize()
     assert info["status"] == 0, info
     xref = O.solve_dense(p)
-    a, _ = rel(x.cpu().numpy(), xref)
-    assert a < 1e-10, (a, info)
+    for r in range(n_rhs):
+        a, _ = rel(x.cpu().numpy()[r * p.n:(r + 1) * p.n], xref)
+        assert a < 1e-10, (a, info)
 
 
 def test_batch_solve_internal_rhs_and_instances(rt):
@@ -228,21 +234,23 @@ def test_invalid_arguments_are_rejected(rt):
     assert e.value.code == rt.RT_ERR_ARG
 
 
-def test_nonfinite_rhs_reports_status(rt):
+@pytest.mark.parametrize("n_rhs", [1, 2])
+def test_nonfinite_rhs_reports_status(rt, n_rhs):
     p = small_problems()["crd"]
-    h = rt.Handle(p, precision=rt.RT_P_FP64, max_restart=8)
-    b = O.rhs(p)
+    h = rt.Handle(p, n_rhs=n_rhs, precision=rt.RT_P_FP64, max_restart=8)
+    b = np.tile(O.rhs(p), n_rhs)
     b[5] = np.nan
-    x = torch.zeros(p.n, dtype=torch.float64, device="cuda:0")
+    x = torch.zeros(n_rhs * p.n, dtype=torch.float64, device="cuda:0")
     info = h.rt_solve(dev(b), x, tol=1e-10, max_outer=3)
     assert info["status"] == rt.RT_ERR_NONFINITE
 
 
-def test_iteration_count_reported_and_noconv(rt):
+@pytest.mark.parametrize("n_rhs", [1, 2])
+def test_iteration_count_reported_and_noconv(rt, n_rhs):
     p = W.config_c1()
-    h = rt.Handle(p, precision=rt.RT_P_FP64, max_restart=4)
-    x = torch.zeros(p.n, dtype=torch.float64, device="cuda:0")
-    info = h.rt_solve(dev(O.rhs(p)), x, tol=1e-12, restart=4, max_outer=2)
+    h = rt.Handle(p, n_rhs=n_rhs, precision=rt.RT_P_FP64, max_restart=4)
+    x = torch.zeros(n_rhs * p.n, dtype=torch.float64, device="cuda:0")
+    info = h.rt_solve(dev(np.tile(O.rhs(p), n_rhs)), x, tol=1e-12, restart=4, max_outer=2)
     assert info["status"] == rt.RT_ERR_NOCONV and info["max_outer"] == 2 and info["max_inner"] == 8
 
 
