@@ -930,10 +930,11 @@ int rt_solve(rt_handle *h, const double *b, double *x, const rt_solve_opts *o, r
       xio = h->stage_x;
     }
   }
-  // boxes, and single 1D instances with a float64 Krylov loop, run on the
-  // grid-wide kernels; a single mixed instance keeps the nested solver (one
-  // CTA), whose inner Krylov spaces survive the refinement steps
-  if (h->dims == 3 || (rt::single_instance(h) && (bicg || h->precision == RT_P_FP64))) {
+  // boxes and single 1D instances run on the grid-wide kernels; a small single
+  // mixed instance stays on one CTA (the host-driven grid loop's per-step
+  // synchronisation outweighs a 1-SM inner cycle below ~64k dofs)
+  const bool grid_1d = rt::single_instance(h) && (bicg || h->precision == RT_P_FP64 || h->E >= 65536);
+  if (h->dims == 3 || grid_1d) {
     int outer = 0, inner = 0, status = 0;
     double relres = 1.0, bytes = 0.0;
     cudaEvent_t e0, e1;
@@ -943,7 +944,8 @@ int rt_solve(rt_handle *h, const double *b, double *x, const rt_solve_opts *o, r
     const int e = bicg ? rt::launch_grid_bicgstab(h, bin ? bin : h->b_int, xio, o->tol, o->max_outer, o->max_iter,
                                                   o->use_x0, s, outer, inner, relres, status, bytes)
                        : rt::launch_grid_solve(h, bin ? bin : h->b_int, xio, o->tol, o->tol_inner, o->restart,
-                                               o->max_outer, o->use_x0, s, outer, inner, relres, status, bytes);
+                                               o->max_outer, o->use_x0, s, outer, inner, relres, status, bytes,
+                                               o->inner_restart > 0 ? o->inner_restart : 20);
     RT_CUDA(cudaEventRecord(e1, s));
     if (e != 0) {
       cudaEventDestroy(e0);

@@ -478,9 +478,180 @@ bool grid_bicgstab_fits(const rt_handle *h) {
   return h->ws.cap_bytes >= 6 * ldv * 8;
 }
 
+// Nested solve for one 1D instance on the grid kernels (mixed handles):
+// float64 flexible GMRES(kout) whose directions come from one GMRES(m_in)
+// cycle on the float32 operator (stopped at a reduction of tol_inner), as the
+// batched k_solve_nested does per CTA.  The operator reads and writes float64
+// vectors, so all bases are float64 here: Vo [kout+1] | Z [kout] | U [m_in+1]
+// in the handle's workspace (kout shrinks to what it holds).
+static int grid_fgmres(rt_handle *h, const double *b, double *x, double tol, double tol_inner, int kout,
+                       int m_in, int max_outer, int use_x0, cudaStream_t s, int &outer_out, int &inner_out,
+                       double &relres_out, int &status, double &bytes) {
+  const int64_t n = h->E;
+  const int64_t ldv = (n + 31) / 32 * 32;
+  const int64_t per = h->ws.cap_bytes / (8 * ldv);  // float64 vectors the workspace holds
+  kout = (int)std::min<int64_t>(kout, (per - m_in - 2) / 2);
+  if (kout < 1) return (int)cudaErrorInvalidValue;
+  GridCtx g{h, s, grid_ctas(h), h->g_part, h->g_red, h->g_coef, {}};
+  auto apply64 = [&](const double *xx, double *yy) -> int { return launch_apply(h, 0, true, xx, yy, s, false); };
+  auto apply32 = [&](const double *xx, double *yy) -> int { return launch_apply(h, 0, false, xx, yy, s, false); };
+  double *Vo = static_cast<double *>(h->ws.V);
+  double *Z = Vo + (int64_t)(kout + 1) * ldv;
+  double *U = Z + (int64_t)kout * ldv;
+  double *r = h->g_r;
+  bytes = 0.0;
+  k_gnorm<<<g.G, kGT, 0, s>>>(b, n, g.part);
+  double bn2;
+  int e = reduce_to_host(g, 1, &bn2);
+  if (e) return e;
+  const double bn = std::sqrt(bn2);
+  bytes += 8.0 * n;
+  status = 4;
+  relres_out = 1.0;
+  outer_out = inner_out = 0;
+  if (!std::isfinite(bn)) { status = 6; return 0; }
+  if (!use_x0) cudaMemsetAsync(x, 0, n * sizeof(double), s);
+  if (bn == 0.0) { status = 0; relres_out = 0.0; return 0; }
+  // Givens least squares of one Hessenberg column (column-major, leading dim ld)
+  auto givens = [](std::vector<double> &H, int ld, std::vector<double> &cs, std::vector<double> &sn,
+                   std::vector<double> &gv, int j, const std::vector<double> &hv, const std::vector<double> &h2,
+                   double hn) {
+    double *col = H.data() + (size_t)j * ld;
+    for (int i = 0; i <= j; ++i) col[i] = hv[i] + (h2.empty() ? 0.0 : h2[i]);
+    col[j + 1] = hn;
+    for (int i = 0; i < j; ++i) {
+      const double t0 = cs[i] * col[i] + sn[i] * col[i + 1];
+      col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
+      col[i] = t0;
+    }
+    const double den = std::hypot(col[j], col[j + 1]);
+    double cj = 1.0, sj = 0.0;
+    if (den > 0.0) { cj = col[j] / den; sj = col[j + 1] / den; }
+    cs[j] = cj;
+    sn[j] = sj;
+    col[j] = den;
+    col[j + 1] = 0.0;
+    gv[j + 1] = -sj * gv[j];
+    gv[j] = cj * gv[j];
+    return den;
+  };
+  auto trisolve = [](const std::vector<double> &H, int ld, const std::vector<double> &gv, int k) {
+    std::vector<double> y(k);
+    for (int i = k - 1; i >= 0; --i) {
+      double acc = gv[i];
+      for (int q = i + 1; q < k; ++q) acc -= H[(size_t)q * ld + i] * y[q];
+      y[i] = acc / H[(size_t)i * ld + i];
+    }
+    return y;
+  };
+  // one Gram-Schmidt step of w = V[j+1] against V[0..j]; second projection when
+  // ||w - V h||^2 <= eta2 ||w||^2; returns ||w - V h|| and normalises w
+  auto orth = [&](double *V, int j, std::vector<double> &hv, std::vector<double> &h2, double eta2,
+                  double &hn) -> int {
+    double *w = V + (int64_t)(j + 1) * ldv;
+    double ww = 0.0;
+    int e2 = dots<double>(g, V, ldv, j, w, n, hv, &ww);
+    if (e2) return e2;
+    double hh = 0.0;
+    for (double v : hv) hh += v * v;
+    h2.assign(j + 1, 0.0);
+    bytes += 8.0 * (j + 2) * n;
+    if (ww - hh > eta2 * ww) {
+      hn = std::sqrt(ww - hh);
+      bytes += 8.0 * (j + 3) * n;
+      return update<double>(g, V, ldv, hv, w, n, hn > 0 ? 1.0 / hn : 0.0, nullptr);
+    }
+    if ((e2 = update<double>(g, V, ldv, hv, w, n, 1.0, nullptr))) return e2;
+    if ((e2 = dots<double>(g, V, ldv, j, w, n, h2, nullptr))) return e2;
+    double n2 = 0.0;
+    if ((e2 = update<double>(g, V, ldv, h2, w, n, 1.0, &n2))) return e2;
+    hn = std::sqrt(n2);
+    std::vector<double> none;
+    bytes += 8.0 * (3.0 * j + 10.0) * n;
+    return update<double>(g, V, ldv, none, w, n, hn > 0 ? 1.0 / hn : 0.0, nullptr);
+  };
+  std::vector<double> Ho((size_t)(kout + 1) * kout), cso(kout + 1), sno(kout + 1), go(kout + 2);
+  std::vector<double> Hi((size_t)(m_in + 1) * m_in), csi(m_in + 1), sni(m_in + 1), gi(m_in + 2), hv, h2;
+  for (int cycle = 0;; ++cycle) {
+    double rn;
+    const double *rsrc;
+    if (cycle == 0 && !use_x0) {
+      rsrc = b;
+      rn = bn;
+    } else {
+      if ((e = apply64(x, r))) return e;
+      k_gresid<<<g.G, kGT, 0, s>>>(b, r, n, g.part);
+      double rn2;
+      if ((e = reduce_to_host(g, 1, &rn2))) return e;
+      rn = std::sqrt(rn2);
+      rsrc = r;
+      bytes += 64.0 * n;
+    }
+    relres_out = rn / bn;
+    if (!std::isfinite(rn)) { status = 6; return 0; }
+    if (relres_out <= tol) { status = 0; return 0; }
+    if (cycle >= max_outer) { status = 4; return 0; }
+    k_gscale<double><<<g.G, kGT, 0, s>>>(rsrc, Vo, n, 1.0 / rn);
+    bytes += 16.0 * n;
+    go.assign(kout + 2, 0.0);
+    go[0] = rn;
+    int idone = 0;
+    for (int i = 0; i < kout; ++i) {
+      // inner: GMRES(m_in) on the float32 operator from Vo[i] (unit norm)
+      double *vi = Vo + (int64_t)i * ldv;
+      cudaMemcpyAsync(U, vi, n * sizeof(double), cudaMemcpyDeviceToDevice, s);
+      gi.assign(m_in + 2, 0.0);
+      gi[0] = 1.0;
+      int jdone = 0;
+      for (int j = 0; j < m_in; ++j) {
+        if ((e = apply32(U + (int64_t)j * ldv, U + (int64_t)(j + 1) * ldv))) return e;
+        double hn = 0.0;
+        if ((e = orth(U, j, hv, h2, 1e-4, hn))) return e;
+        bytes += 40.0 * n;
+        const double den = givens(Hi, m_in + 1, csi, sni, gi, j, hv, h2, hn);
+        jdone = j + 1;
+        if (den == 0.0) { jdone = j; break; }
+        if (!(hn > 1e-30)) break;
+        if (std::fabs(gi[j + 1]) <= tol_inner) break;
+      }
+      inner_out += jdone;
+      double *zi = Z + (int64_t)i * ldv;
+      cudaMemsetAsync(zi, 0, n * sizeof(double), s);
+      if (jdone > 0) {
+        const std::vector<double> y = trisolve(Hi, m_in + 1, gi, jdone);
+        cudaMemcpyAsync(g.coef, y.data(), jdone * sizeof(double), cudaMemcpyHostToDevice, s);
+        k_gxupdate<double><<<g.G, kGT, 0, s>>>(U, ldv, jdone, g.coef, zi, n);
+        bytes += (8.0 * jdone + 16.0) * n;
+      }
+      // outer: w = A z_i in float64, orthogonalised against Vo (DGKS)
+      if ((e = apply64(zi, Vo + (int64_t)(i + 1) * ldv))) return e;
+      double hn = 0.0;
+      if ((e = orth(Vo, i, hv, h2, 0.5, hn))) return e;
+      bytes += 40.0 * n;
+      const double den = givens(Ho, kout + 1, cso, sno, go, i, hv, h2, hn);
+      idone = i + 1;
+      ++outer_out;
+      if (den == 0.0) { idone = i; break; }
+      if (!(hn > 1e-300 * rn)) break;
+      if (std::fabs(go[i + 1]) <= 0.3 * tol * bn) break;
+    }
+    if (idone > 0) {
+      const std::vector<double> y = trisolve(Ho, kout + 1, go, idone);
+      cudaMemcpyAsync(g.coef, y.data(), idone * sizeof(double), cudaMemcpyHostToDevice, s);
+      k_gxupdate<double><<<g.G, kGT, 0, s>>>(Z, ldv, idone, g.coef, x, n);
+      bytes += (8.0 * idone + 16.0) * n;
+    }
+    if ((e = (int)cudaGetLastError())) return e;
+    if (idone == 0) { status = 5; return 0; }
+  }
+}
+
 int launch_grid_solve(rt_handle *h, const double *b, double *x, double tol, double tol_inner, int m,
                       int max_outer, int use_x0, cudaStream_t s, int &outer, int &inner, double &relres,
-                      int &status, double &bytes) {
+                      int &status, double &bytes, int m_in) {
+  if (h->dims == 1 && h->precision != 0)  // one 1D instance, mixed: nested solve on the grid kernels
+    return grid_fgmres(h, b, x, tol, tol_inner, m, m_in, max_outer, use_x0, s, outer, inner, relres, status,
+                       bytes);
   if (h->dims == 1) {  // one 1D instance, float64 GMRES: the batched apply kernels over the whole GPU
     const int64_t ldv = (h->E + 31) / 32 * 32;
     m = std::min<int64_t>(m, h->ws.cap_bytes / (8 * ldv) - 1);

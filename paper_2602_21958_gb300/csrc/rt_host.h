@@ -120,12 +120,12 @@ int launch_grid_bicgstab(rt_handle *h, const double *b, double *x, double tol, i
                          int use_x0, cudaStream_t s, int &restarts, int &iters, double &relres, int &status,
                          double &bytes);
 bool grid_bicgstab_fits(const rt_handle *h);
-// One 1D (column, rhs) instance: its float64 GMRES and BiCGStab solves run on
-// the grid-wide kernels (all SMs) instead of one CTA.
+// One 1D (column, rhs) instance: its solves run on the grid-wide kernels (all
+// SMs) instead of one CTA.
 inline bool single_instance(const rt_handle *h) { return h->dims == 1 && h->n_cols * h->n_rhs == 1; }
 int launch_grid_solve(rt_handle *h, const double *b, double *x, double tol, double tol_inner, int m,
                       int max_outer, int use_x0, cudaStream_t s, int &outer, int &inner, double &relres,
-                      int &status, double &bytes);
+                      int &status, double &bytes, int m_in = 20);
 int grid_ctas(const rt_handle *h);
 // allocation-free apply: scratch in a static device array of this many bytes
 constexpr long long kNoAllocScratchBytes = 16ll << 20;
