@@ -359,6 +359,34 @@ def gmres(matvec, b: np.ndarray, tol: float = 1e-10, restart: int = 30,
     return GmresResult(x, total, restarts, beta / bn, hist)
 
 
+def arnoldi(matvec, v0: np.ndarray, m: int) -> np.ndarray:
+    """m steps of the Arnoldi process (modified Gram-Schmidt, applied twice:
+    one pass alone loses orthogonality as the space nears invariance) from
+    v0: returns the (k+1) x k upper Hessenberg H with A V_k = V_{k+1} H, k = m
+    unless the space became invariant (happy breakdown).  The eigenvalues of
+    H[:k, :k] (Ritz values) approximate the spectrum whose clustering Sec. 4
+    studies."""
+    v0 = np.asarray(v0, dtype=float)
+    n = v0.size
+    V = np.zeros((m + 1, n))
+    H = np.zeros((m + 1, m))
+    V[0] = v0 / np.linalg.norm(v0)
+    k = 0
+    for j in range(m):
+        w = matvec(V[j])
+        for _ in range(2):
+            for i in range(j + 1):
+                c = V[i] @ w
+                H[i, j] += c
+                w = w - c * V[i]
+        H[j + 1, j] = np.linalg.norm(w)
+        k = j + 1
+        if H[j + 1, j] <= 1e-14 * abs(H[: j + 1, j]).max():
+            break
+        V[j + 1] = w / H[j + 1, j]
+    return H[: k + 1, :k]
+
+
 def solve_gmres(prob: Problem, b: np.ndarray | None = None, tol: float = 1e-13,
                 restart: int = 60, max_iter: int = 5000) -> GmresResult:
     """Matrix-free solve of A_N I = b with the oracle's own GMRES."""

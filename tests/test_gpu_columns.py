@@ -179,6 +179,25 @@ def test_c1_full_size_solves(rt):
         assert info["status"] == 0 and a < 1e-10, (prec, a, info)
 
 
+def test_c2_single_column_solves_meet_the_oracle_residual(rt):
+    """C2 (131072 dofs, one column): the grid-wide routes (float64 GMRES, the
+    nested mixed solve, BiCGStab) reach the tolerance on the oracle's own
+    residual b - A x."""
+    p = W.config_c2()
+    b = O.rhs(p)
+    bd = dev(b)
+    cases = ((rt.RT_P_FP64, dict(restart=256)), (rt.RT_P_MIXED, dict(restart=64, tol_inner=0.1)),
+             (rt.RT_P_FP64, dict(method=rt.RT_KRYLOV_BICGSTAB)))
+    for prec, kw in cases:
+        h = rt.Handle(p, precision=prec, max_restart=256 if prec == rt.RT_P_FP64 else 64)
+        x = torch.zeros(p.n, dtype=torch.float64, device="cuda:0")
+        info = h.rt_solve(bd, x, tol=1e-11, max_outer=80, **kw)
+        torch.cuda.synchronize()
+        assert info["status"] == 0, (prec, kw, info)
+        r = np.linalg.norm(b - O.apply_A(p, x.cpu().numpy())) / np.linalg.norm(b)
+        assert r < 2e-11, (prec, kw, r)
+
+
 def test_c2_full_size_apply(rt):
     p = W.config_c2()
     x = W.random_vectors(p.n, 1, 11)[0]

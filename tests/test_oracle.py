@@ -180,6 +180,34 @@ def test_lu_equals_bicgstab():
     assert np.linalg.norm(r.x - x_lu) <= 1e-11 * np.linalg.norm(x_lu)
 
 
+def test_arnoldi_full_space_gives_the_eigenvalues():
+    # library eigenvalues as the independent reference; Arnoldi relation A V = V H
+    rng = np.random.default_rng(9)
+    A = np.eye(40) + 0.4 * rng.standard_normal((40, 40)) / np.sqrt(40)
+    H = O.arnoldi(lambda v: A @ v, rng.standard_normal(40), 40)
+    assert H.shape == (41, 40)
+    ritz = np.sort_complex(np.linalg.eigvals(H[:40, :40]))
+    lam = np.sort_complex(np.linalg.eigvals(A))
+    assert np.abs(ritz - lam).max() < 1e-9
+    assert np.allclose(np.tril(H, -2), 0.0)
+
+
+def test_arnoldi_ritz_values_reproduce_table_mono():
+    # full Arnoldi on the Sec. 5.1 operator: the Ritz values are the spectrum,
+    # so the printed cluster fraction (Table mono) comes back
+    p = W.paper_mono(10, 12)
+    H = O.arnoldi(lambda v: O.apply_A(p, v), np.ones(p.n), p.n)
+    k = H.shape[1]
+    ritz = np.linalg.eigvals(H[:k, :k])
+    lam = np.linalg.eigvals(O.assemble_A(p))
+    frac = lambda z: np.mean((np.abs(z) >= 0.999) & (np.abs(z) <= 1 + 1e-12))
+    if k == p.n:
+        assert abs(frac(ritz) - frac(lam)) < 1e-12
+    # a Krylov space that became invariant early holds exact eigenvalues
+    d = np.abs(ritz[:, None] - lam[None, :]).min(axis=1)
+    assert d.max() < 1e-8
+
+
 def test_reduced_crd_system_equals_full_solve():
     """Independent route at full C1 size: the N_z x N_z reduced CRD system."""
     p = W.config_c1()
