@@ -377,6 +377,35 @@ def configs_sweep(rank: int = 0) -> dict:
     return out
 
 
+def spectral_sweep(rank: int = 0) -> dict:
+    """Spectral diagnostics on the GPU (rt_arnoldi): m Arnoldi steps on the
+    float64 operator from the internal right-hand side, Ritz values on the
+    host.  Reports the time, the share of Ritz values with |theta| in
+    [0.999, 1] (the cluster of Tables mono/iso) and the smallest |theta| (the
+    paper's lower bound |lambda|_min > 0.7), at sizes beyond dense eigensolvers."""
+    import torch
+
+    from paper_2602_21958_gb300 import rt, workloads as W
+
+    out = {}
+    for name, make, m in (("C1", W.config_c1, 200), ("C2", W.config_c2, 200), ("C3", W.config_c3, 80)):
+        p = make()
+        h = rt.Handle(p, precision=rt.RT_P_FP64, max_restart=m + 1)
+        h.rt_arnoldi(4)  # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        H = h.rt_arnoldi(m)
+        ms = (time.perf_counter() - t0) * 1e3
+        th = rt.ritz_values(H)
+        a = np.abs(th)
+        out[name] = {"dofs": int(p.n), "m": int(H.shape[1]), "ms": ms,
+                     "ritz_frac_abs_in_0.999_1": float(np.mean((a >= 0.999) & (a <= 1 + 1e-12))),
+                     "ritz_min_abs": float(a.min()), "ritz_max_abs": float(a.max())}
+        h.close()
+        torch.cuda.empty_cache()
+    return out
+
+
 def load_bf16_peak():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -528,6 +557,7 @@ def main():
     res = run_ours(args, rank, world)
     tensor = tensor_roofline(rank) if rank == 0 else None
     per_config = configs_sweep(rank) if rank == 0 else None
+    spectral = spectral_sweep(rank) if rank == 0 else None
     if rank != 0:
         return
     accuracy = None
@@ -558,6 +588,7 @@ def main():
         "roofline": res["roofline"],
         "roofline_tensor": tensor,
         "configs": per_config,
+        "spectral": spectral,
         "clocks": res["clk"],
         "cpu_baseline": cb,
         "accuracy": accuracy,

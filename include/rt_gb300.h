@@ -221,6 +221,22 @@ int rt_apply_noalloc(rt_handle *h, int32_t op, int32_t fp64, const double *x, do
 int rt_solve(rt_handle *h, const double *b, double *x, const rt_solve_opts *opts,
              rt_info *info, void *stream);
 
+/* Spectral diagnostics: m steps of the Arnoldi process on A_N (float64
+ * operator) for a handle holding ONE instance (a 3D box, or one 1D column with
+ * n_rhs = 1), from v0 (device pointer, the instance's length; NULL: the
+ * internal right-hand side Lambda t + I_in).  Classical Gram-Schmidt with the
+ * DGKS second projection, grid-wide kernels.  The eigenvalues of the leading
+ * m_done x m_done block of H (Ritz values) approximate the spectrum of A_N
+ * whose clustering at 1 and lower bound Sec. 4 proves and Sec. 5 measures
+ * (Tables mono, iso; Thm main4); computing them is the caller's (the library
+ * returns H).
+ *   H      : host array, (m+1) x m, column-major; zero where unused
+ *   m_done : host int, steps taken (< m when the Krylov space became invariant)
+ * Errors: RT_ERR_ARG for a batch handle, m < 1, a workspace holding fewer than
+ * m+1 float64 vectors (create the handle with a larger max_restart), a zero or
+ * non-finite v0; RT_ERR_CUDA on a CUDA failure.  Synchronises the stream. */
+int rt_arnoldi(rt_handle *h, const double *v0, int32_t m, double *H, int32_t *m_done, void *stream);
+
 /* Release every device and host resource of the handle (NULL is a no-op). */
 void rt_destroy(rt_handle *h);
 

@@ -893,6 +893,26 @@ int rt_autotune(rt_handle *h, int32_t flags, rt_tune_info *out, void *stream) {
   return RT_OK;
 }
 
+int rt_arnoldi(rt_handle *h, const double *v0, int32_t m, double *H, int32_t *m_done, void *stream) {
+  if (!h || !H || !m_done) return fail(RT_ERR_ARG, "null handle, H or m_done");
+  if (h->dims != 3 && !rt::single_instance(h))
+    return fail(RT_ERR_ARG, "rt_arnoldi needs a handle with one instance (a box or one column, n_rhs = 1)");
+  if (m < 1) return fail(RT_ERR_ARG, "need m >= 1");
+  const int64_t ldv = (h->E + 31) / 32 * 32;
+  if ((int64_t)(m + 1) * ldv * 8 > h->ws.cap_bytes)
+    return fail(RT_ERR_ARG, "workspace holds fewer than m+1 float64 vectors: create the handle with a larger max_restart");
+  if (v0 && !is_device_ptr(v0)) return fail(RT_ERR_ARG, "v0 must be a device pointer");
+  if (!h->g_part) return fail(RT_ERR_ARG, "handle has no grid-solve buffers");
+  cudaStream_t s = (cudaStream_t)stream;
+  int done = 0;
+  const int e = rt::launch_grid_arnoldi(h, v0 ? v0 : h->b_int, m, H, done, s);
+  *m_done = done;
+  if (e == -1) return fail(RT_ERR_ARG, "v0 is zero or not finite");
+  if (e != 0) return fail(RT_ERR_CUDA, std::string("arnoldi: ") + cudaGetErrorString((cudaError_t)e));
+  RT_CUDA(cudaStreamSynchronize(s));
+  return RT_OK;
+}
+
 int rt_solve(rt_handle *h, const double *b, double *x, const rt_solve_opts *o, rt_info *info,
              void *stream) {
   if (!h || !x || !o) return fail(RT_ERR_ARG, "null handle, x or options");

@@ -646,6 +646,62 @@ static int grid_fgmres(rt_handle *h, const double *b, double *x, double tol, dou
   }
 }
 
+// ------------------------------------------------------ Arnoldi (spectra)
+// m steps of the Arnoldi process on the float64 operator of one instance
+// (a box or a single 1D column), classical Gram-Schmidt with the DGKS second
+// projection; H (host, column-major (m+1) x m) receives the Hessenberg
+// matrix, m_done the steps taken (fewer on an invariant subspace).
+int launch_grid_arnoldi(rt_handle *h, const double *v0, int m, double *H, int &m_done, cudaStream_t s) {
+  const int64_t n = h->E;
+  const int64_t ldv = (n + 31) / 32 * 32;
+  GridCtx g{h, s, grid_ctas(h), h->g_part, h->g_red, h->g_coef, {}};
+  double *V = static_cast<double *>(h->ws.V);
+  auto apply = [&](const double *X, double *Y) -> int {
+    return h->dims == 3 ? apply_box(h, 0, true, X, false, Y, false, s) : launch_apply(h, 0, true, X, Y, s, false);
+  };
+  std::fill(H, H + (size_t)(m + 1) * m, 0.0);
+  m_done = 0;
+  k_gnorm<<<g.G, kGT, 0, s>>>(v0, n, g.part);
+  double nv2 = 0.0;
+  int e = reduce_to_host(g, 1, &nv2);
+  if (e) return e;
+  const double nv = std::sqrt(nv2);
+  if (!(nv > 0.0) || !std::isfinite(nv)) return -1;
+  k_gscale<double><<<g.G, kGT, 0, s>>>(v0, V, n, 1.0 / nv);
+  std::vector<double> hv, h2;
+  for (int j = 0; j < m; ++j) {
+    double *w = V + (int64_t)(j + 1) * ldv;
+    if ((e = apply(V + (int64_t)j * ldv, w))) return e;
+    double ww = 0.0;
+    if ((e = dots<double>(g, V, ldv, j, w, n, hv, &ww))) return e;
+    double hh = 0.0, hmax = 0.0;
+    for (double v : hv) {
+      hh += v * v;
+      hmax = std::max(hmax, std::fabs(v));
+    }
+    double hn;
+    h2.assign(j + 1, 0.0);
+    if (ww - hh > 0.5 * ww) {
+      hn = std::sqrt(ww - hh);
+      if ((e = update<double>(g, V, ldv, hv, w, n, hn > 0 ? 1.0 / hn : 0.0, nullptr))) return e;
+    } else {
+      if ((e = update<double>(g, V, ldv, hv, w, n, 1.0, nullptr))) return e;
+      if ((e = dots<double>(g, V, ldv, j, w, n, h2, nullptr))) return e;
+      double n2 = 0.0;
+      if ((e = update<double>(g, V, ldv, h2, w, n, 1.0, &n2))) return e;
+      hn = std::sqrt(n2);
+      std::vector<double> none;
+      if ((e = update<double>(g, V, ldv, none, w, n, hn > 0 ? 1.0 / hn : 0.0, nullptr))) return e;
+    }
+    double *col = H + (size_t)j * (m + 1);
+    for (int i = 0; i <= j; ++i) col[i] = hv[i] + h2[i];
+    col[j + 1] = hn;
+    m_done = j + 1;
+    if (!(hn > 1e-14 * hmax)) break;
+  }
+  return (int)cudaGetLastError();
+}
+
 int launch_grid_solve(rt_handle *h, const double *b, double *x, double tol, double tol_inner, int m,
                       int max_outer, int use_x0, cudaStream_t s, int &outer, int &inner, double &relres,
                       int &status, double &bytes, int m_in) {

@@ -120,6 +120,7 @@ int launch_grid_bicgstab(rt_handle *h, const double *b, double *x, double tol, i
                          int use_x0, cudaStream_t s, int &restarts, int &iters, double &relres, int &status,
                          double &bytes);
 bool grid_bicgstab_fits(const rt_handle *h);
+int launch_grid_arnoldi(rt_handle *h, const double *v0, int m, double *H, int &m_done, cudaStream_t s);
 // One 1D (column, rhs) instance: its solves run on the grid-wide kernels (all
 // SMs) instead of one CTA.
 inline bool single_instance(const rt_handle *h) { return h->dims == 1 && h->n_cols * h->n_rhs == 1; }

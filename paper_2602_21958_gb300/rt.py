@@ -49,7 +49,7 @@ class rt_info(C.Structure):
 
 
 EXPORTS = ("rt_create", "rt_create_batch", "rt_vector_length", "rt_apply", "rt_apply_noalloc",
-           "rt_autotune", "rt_solve", "rt_destroy", "rt_last_error", "rt_version")
+           "rt_autotune", "rt_solve", "rt_arnoldi", "rt_destroy", "rt_last_error", "rt_version")
 
 
 class rt_tune_info(C.Structure):
@@ -79,6 +79,7 @@ def load(path: Optional[str] = None) -> C.CDLL:
     lib.rt_autotune.argtypes = [vp, C.c_int32, C.POINTER(rt_tune_info), vp]
     lib.rt_autotune.restype = C.c_int
     lib.rt_solve.argtypes = [vp, vp, vp, C.POINTER(rt_solve_opts), C.POINTER(rt_info), vp]
+    lib.rt_arnoldi.argtypes = [vp, vp, C.c_int32, vp, C.POINTER(C.c_int32), vp]
     lib.rt_destroy.argtypes = [vp]
     lib.rt_destroy.restype = None
     lib.rt_last_error.restype = C.c_char_p
@@ -228,6 +229,24 @@ class Handle:
         if arrs is not None:
             out.update(inst_outer=arrs[0], inst_inner=arrs[1], inst_relres=arrs[2])
         return out
+
+
+    def rt_arnoldi(self, m: int, v0=None, stream=None) -> np.ndarray:
+        """m Arnoldi steps on A_N (float64 operator) from v0 (device tensor; None:
+        the internal right-hand side); returns the (k+1) x k Hessenberg matrix,
+        k the steps taken.  Ritz values: ``ritz_values(H)``."""
+        H = np.zeros((m + 1) * m)
+        done = C.c_int32(0)
+        _check(load().rt_arnoldi(self._h, _ptr(v0), m, H.ctypes.data_as(C.c_void_p), C.byref(done),
+                                 _stream_ptr(stream)))
+        k = done.value
+        return H.reshape(m, m + 1).T[:k + 1, :k].copy()
+
+
+def ritz_values(H: np.ndarray) -> np.ndarray:
+    """Eigenvalues of the square part of an Arnoldi Hessenberg matrix."""
+    k = H.shape[1]
+    return np.linalg.eigvals(H[:k, :k])
 
 
 def version() -> str:
