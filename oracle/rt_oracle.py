@@ -26,7 +26,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from paper_2602_21958_gb300.workloads import FS_IE, FS_SCL, Problem
+from paper_2602_21958_gb300.workloads import FS_IE, FS_QSC, FS_SCL, Problem
 
 SERIES_CUT = 0.1
 
@@ -73,6 +73,51 @@ def step_coefficients(dtau: np.ndarray, formal_solver: str):
     return e, w0 - beta, beta
 
 
+def qsc_moments(d: np.ndarray):
+    """W1 = int_0^d s e^-(d-s) ds = d - (1 - e^-d) and W2 = int_0^d s^2 e^-(d-s) ds
+    = d^2 - 2 W1, returned as W1/d^2 and W2/d^3.  Below d = 0.1 the cancelling
+    closed forms are replaced by their series, W1/d^2 = sum_{k>=0} (-1)^k
+    d^k/(k+2)! and W2/d^3 = 2 sum_{k>=0} (-1)^k d^k/(k+3)! (18 terms)."""
+    d = np.asarray(d, dtype=float)
+    a = np.empty_like(d)
+    b = np.empty_like(d)
+    small = d < SERIES_CUT
+    ds = d[small]
+    sa = np.zeros_like(ds)
+    sb = np.zeros_like(ds)
+    for k in range(18):
+        sa += (-1) ** k * ds ** k / math.factorial(k + 2)
+        sb += (-1) ** k * ds ** k / math.factorial(k + 3)
+    a[small] = sa
+    b[small] = 2.0 * sb
+    dl = d[~small]
+    w1 = dl + np.expm1(-dl)
+    a[~small] = w1 / dl ** 2
+    b[~small] = (dl ** 2 - 2.0 * w1) / dl ** 3
+    return a, b
+
+
+def qsc_coefficients(du: np.ndarray, dd: np.ndarray):
+    """Quadratic short-characteristics step (Sec. 3.2 allows any formal solver;
+    the paper's 3D runs use a quadratic exponential integrator, Sec. 5.3):
+    S is the parabola through the upwind (u), current (c) and downwind (d)
+    points, at path depths s = 0, du, du + dd from u, integrated exactly
+    against e^-(du - s):  I_c = e I_u + psi_u S_u + psi_c S_c + psi_d S_d with
+        psi_c = (W1 (du + dd) - W2) / (du dd)
+        psi_d = (W2 - du W1) / (dd (du + dd))
+        psi_u = w0 - psi_c - psi_d          (the weights integrate 1 to w0)
+    (Lagrange weights integrated with the moments W0 = w0, W1, W2)."""
+    du = np.asarray(du, dtype=float)
+    dd = np.asarray(dd, dtype=float)
+    a, b = qsc_moments(du)          # W1 = du^2 a, W2 = du^3 b
+    e = np.exp(-du)
+    w0 = -np.expm1(-du)
+    pc = du * ((du + dd) * a - du * b) / dd
+    pd = du ** 3 * (b - a) / (dd * (du + dd))
+    pu = w0 - pc - pd
+    return e, pu, pc, pd
+
+
 # ---------------------------------------------------------------- 1D transfer
 def dtau_1d(prob: Problem) -> np.ndarray:
     """Delta tau_i(mu, nu) between depth points i and i+1: [nz-1, n_dir, n_nu].
@@ -95,6 +140,8 @@ def lambda_1d(prob: Problem, S: np.ndarray, with_inflow: bool = False) -> np.nda
     """
     nz, nd, nn = prob.nz, prob.n_dir, prob.n_nu
     S = np.asarray(S, dtype=float).reshape(nz, nd, nn)
+    if prob.formal_solver == FS_QSC:
+        return _lambda_1d_qsc(prob, S, with_inflow)
     e, al, be = step_coefficients(dtau_1d(prob), prob.formal_solver)
     I = np.zeros_like(S)
     down = prob.mu < 0
@@ -111,12 +158,47 @@ def lambda_1d(prob: Problem, S: np.ndarray, with_inflow: bool = False) -> np.nda
     return I.reshape(-1)
 
 
+def _lambda_1d_qsc(prob: Problem, S: np.ndarray, with_inflow: bool) -> np.ndarray:
+    """Quadratic short characteristics along every ray: each step uses the
+    upwind, current and downwind points (qsc_coefficients); the last step of a
+    ray, which has no downwind point, is the linear SC-L step."""
+    nz = prob.nz
+    dt = dtau_1d(prob)                               # [nz-1, n_dir, n_nu]
+    I = np.zeros_like(S)
+    down = prob.mu < 0
+    up = ~down
+    if with_inflow:
+        I[0, down, :] = prob.I_top[None, :]
+        I[nz - 1, up, :] = prob.I_bot[None, :]
+    for i in range(1, nz):                           # mu < 0: u = i-1, c = i, d = i+1
+        du = dt[i - 1, down]
+        if i < nz - 1:
+            e, pu, pc, pd = qsc_coefficients(du, dt[i, down])
+            src = pu * S[i - 1, down] + pc * S[i, down] + pd * S[i + 1, down]
+        else:
+            e, al, be = step_coefficients(du, FS_SCL)
+            src = al * S[i - 1, down] + be * S[i, down]
+        I[i, down] = e * I[i - 1, down] + src
+    for i in range(nz - 2, -1, -1):                  # mu > 0: u = i+1, c = i, d = i-1
+        du = dt[i, up]
+        if i > 0:
+            e, pu, pc, pd = qsc_coefficients(du, dt[i - 1, up])
+            src = pu * S[i + 1, up] + pc * S[i, up] + pd * S[i - 1, up]
+        else:
+            e, al, be = step_coefficients(du, FS_SCL)
+            src = al * S[i + 1, up] + be * S[i, up]
+        I[i, up] = e * I[i + 1, up] + src
+    return I.reshape(-1)
+
+
 def lambda_matrix_1d(prob: Problem) -> np.ndarray:
     """Dense Lambda_N (N x N) assembled from the step recurrence, ray by ray,
     in the space-based ordering (Lambda_N = P^T blockdiag(Lambda_[k]) P)."""
     nz, nd, nn = prob.nz, prob.n_dir, prob.n_nu
-    e, al, be = step_coefficients(dtau_1d(prob), prob.formal_solver)
     N = prob.n
+    if prob.formal_solver == FS_QSC:  # columns of the matrix-free operator
+        return np.stack([lambda_1d(prob, np.eye(1, N, k).ravel()) for k in range(N)], axis=1)
+    e, al, be = step_coefficients(dtau_1d(prob), prob.formal_solver)
     L = np.zeros((N, N))
     for d in range(nd):
         for f in range(nn):

@@ -38,6 +38,7 @@ SEED_BASE = 20262195
 
 FS_SCL = "scl"  # linear short-characteristics exponential integrator
 FS_IE = "ie"    # implicit Euler (eqs. ie_1, ie_2)
+FS_QSC = "qsc"  # quadratic short-characteristics exponential integrator (1D)
 
 
 @dataclasses.dataclass

@@ -47,6 +47,57 @@ def test_scl_inflow_equal_to_source_is_invariant():
     assert np.abs(I[:, p.mu > 0] - 1.0).max() < 1e-14
 
 
+@pytest.mark.parametrize("du", [1e-6, 1e-3, 0.05, 0.0999, 0.1, 0.3, 1.0, 4.0, 30.0])
+@pytest.mark.parametrize("ratio", [0.1, 1.0, 7.0])
+def test_qsc_step_is_exact_for_quadratic_sources(du, ratio):
+    # independent reference: adaptive quadrature of the formal-solution integral
+    from scipy.integrate import quad
+    dd = ratio * du
+    e, pu, pc, pd = O.qsc_coefficients(np.array([du]), np.array([dd]))
+    assert abs(e[0] - math.exp(-du)) <= 1e-15
+    for p0, p1, p2 in ((1.0, 0.0, 0.0), (0.3, -1.7, 0.0), (0.2, 0.9, -2.3)):
+        S = lambda s: p0 + p1 * s + p2 * s * s
+        ref = quad(lambda s: S(s) * math.exp(-(du - s)), 0.0, du, epsabs=0.0, epsrel=2e-14, limit=200)[0]
+        got = pu[0] * S(0.0) + pc[0] * S(du) + pd[0] * S(du + dd)
+        scale = max(abs(p0), abs(p1) * du, abs(p2) * du * du) * -math.expm1(-du)
+        assert abs(got - ref) <= 1e-12 * scale + 1e-300, (p0, p1, p2, got, ref)
+
+
+def test_qsc_constant_source_closed_form():
+    # S = B, zero inflow: I(tau) = B (1 - e^-tau) exactly along every ray
+    t = np.logspace(-3, 3, 25)
+    q = W.two_level_column(t, 4, 1, 5, "crd", 1.0, 1.0, formal_solver=W.FS_QSC)
+    B = 1.7
+    I = O.lambda_op(q, np.full(q.n, B)).reshape(q.nz, q.n_dir, q.n_nu)
+    tau = np.concatenate([np.zeros((1, q.n_dir, q.n_nu)), np.cumsum(O.dtau_1d(q), axis=0)])
+    down = q.mu < 0
+    assert np.allclose(I[:, down], B * -np.expm1(-tau[:, down]), rtol=1e-13, atol=1e-15)
+
+
+def test_qsc_converges_at_higher_order_than_scl():
+    # smooth source along a constant-opacity slab: quadratic step error falls
+    # faster under refinement than the linear one (exact integral as reference)
+    errs = {}
+    for fs in (W.FS_SCL, W.FS_QSC):
+        e = []
+        for nz in (41, 81, 161):
+            t = np.linspace(0.0, 4.0, nz)
+            q = W.two_level_column(t, 2, 1, 1, "crd", 1.0, 1.0, formal_solver=fs)
+            tau_pts = np.cumsum(np.concatenate([[0.0], O.dtau_1d(q)[:, 0, 0]]))  # down ray 0
+            src = np.sin(1.3 * tau_pts) + 2.0
+            S = np.repeat(src[:, None], q.n_r, axis=1).ravel()
+            I = O.lambda_op(q, S).reshape(nz, q.n_dir, q.n_nu)[:, 0, 0]
+            mid = (nz - 1) // 2          # an interior point: every step before it is quadratic
+            T = tau_pts[mid]
+            ex = lambda s: (np.sin(1.3 * s) + 2.0) * np.exp(-(T - s))
+            from scipy.integrate import quad
+            ref = quad(ex, 0.0, T, epsabs=0, epsrel=1e-13, limit=400)[0]
+            e.append(abs(I[mid] - ref))
+        errs[fs] = e
+    assert errs[W.FS_QSC][-1] < errs[W.FS_SCL][-1] / 10
+    assert errs[W.FS_QSC][1] / errs[W.FS_QSC][2] > 6.0   # about third order
+
+
 def test_ie_recurrence_equals_closed_form_entries():
     """Dense Lambda from the recurrence (eqs. ie_1, ie_2) equals the closed-form
     entries of eqs. ie_mono3, ie_mono4, including the zero first row of
