@@ -54,7 +54,11 @@ enum {
 
 /* ---- enumerations ---------------------------------------------------- */
 enum { RT_FS_SCL = 0,    /* linear short-characteristics exponential step       */
-       RT_FS_IE = 1 };   /* implicit Euler, eqs. ie_1, ie_2                      */
+       RT_FS_IE = 1,     /* implicit Euler, eqs. ie_1, ie_2                      */
+       RT_FS_QSC = 2 };  /* quadratic short characteristics (upwind, current and
+                            downwind points; 1D columns only; the last step of a
+                            ray is linear) -- the quadratic exponential integrator
+                            of the paper's 3D runs (Sec. 5.3), restated for 1D    */
 enum { RT_P_FP64 = 0,    /* every stage in float64                              */
        RT_P_MIXED = 1 }; /* Sigma and sweep in float32 (bf16 tensor cores for the
                             dense kernel), Krylov and refinement in float64     */

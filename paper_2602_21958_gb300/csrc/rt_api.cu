@@ -115,7 +115,7 @@ void free_handle(rt_handle *h) {
                   h->so.outer, h->so.inner, h->so.status, h->so.relres, h->so.bytes,
                   h->stage_x, h->stage_y, h->d_sig_tiles, h->d_sw_tiles, h->apply_S,
                   h->d_tc_jobs, h->d_tc_off, h->d_tc_tiles, h->d_tc_xb, h->d_err, h->d_geo,
-                  h->chi64, h->chi32, h->g_part, h->g_red, h->g_coef, h->g_r};
+                  h->chi64, h->chi32, h->g_part, h->g_red, h->g_coef, h->g_r, h->Q64, h->Q32};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (h->solve_graph) cudaGraphExecDestroy(h->solve_graph);
@@ -124,7 +124,7 @@ void free_handle(rt_handle *h) {
 }
 
 struct ColumnHost {
-  rt::ColDev c;
+  rt::ColDev c{};
   std::vector<double> mu_cls;
   std::vector<int32_t> dir_cls, dir_up;
   std::vector<double> Uw, Ul, Rw, Psi;
@@ -142,8 +142,10 @@ int check_desc(const rt_desc *d, int idx) {
   if (!d->z || !d->dir || !d->w_dir || !d->w_nu || !d->chi || !d->gamma)
     return fail(RT_ERR_ARG, std::string(pre) + "missing z, dir, w_dir, w_nu, chi or gamma");
   if (!d->Psi && (!d->P || !d->R)) return fail(RT_ERR_ARG, std::string(pre) + "need Psi or both P and R");
-  if (d->formal_solver != RT_FS_SCL && d->formal_solver != RT_FS_IE)
+  if (d->formal_solver != RT_FS_SCL && d->formal_solver != RT_FS_IE && d->formal_solver != RT_FS_QSC)
     return fail(RT_ERR_ARG, std::string(pre) + "unknown formal_solver");
+  if (d->formal_solver == RT_FS_QSC && d->dims != 1)
+    return fail(RT_ERR_ARG, std::string(pre) + "quadratic short characteristics are for 1D columns");
   for (int i = 0; i + 1 < d->nz; ++i)
     if (!(d->z[i + 1] > d->z[i])) return fail(RT_ERR_ARG, std::string(pre) + "z must increase strictly");
   for (int k = 0; k < d->n_dir; ++k)
@@ -384,6 +386,7 @@ int create_columns(const rt_desc *descs, int n_cols, int n_rhs, int precision, i
     c.u_off = u_off;
     c.d_off = d_off;
     c.in_off = in_off;
+    c.fs = d->formal_solver;
     cols[i] = c;
     const int64_t ncol = (int64_t)c.nz * c.nr;
     h->nmax = std::max(h->nmax, ncol);
@@ -459,25 +462,29 @@ int create_columns(const rt_desc *descs, int n_cols, int n_rhs, int precision, i
   // step coefficients on the device (float64 exp / expm1)
   double *d_z = nullptr, *d_chi = nullptr, *d_mu = nullptr;
   int64_t *d_zoff = nullptr;
-  int32_t *d_clsoff = nullptr, *d_fs = nullptr;
+  int32_t *d_clsoff = nullptr;
   auto cleanup_tmp = [&]() {
-    cudaFree(d_z); cudaFree(d_chi); cudaFree(d_mu); cudaFree(d_zoff); cudaFree(d_clsoff); cudaFree(d_fs);
+    cudaFree(d_z); cudaFree(d_chi); cudaFree(d_mu); cudaFree(d_zoff); cudaFree(d_clsoff);
   };
   if ((rc = dev_upload(&d_z, z)) || (rc = dev_upload(&d_chi, chi)) || (rc = dev_upload(&d_mu, mu_cls)) ||
-      (rc = dev_upload(&d_zoff, zoff)) || (rc = dev_upload(&d_clsoff, cls_off)) || (rc = dev_upload(&d_fs, fs))) {
+      (rc = dev_upload(&d_zoff, zoff)) || (rc = dev_upload(&d_clsoff, cls_off))) {
     cleanup_tmp();
     free_handle(h);
     return rc;
   }
   const size_t nc = (size_t)std::max<int64_t>(c_off, 1);
+  h->n_coef = (int64_t)nc;
+  const bool any_qsc = std::find(fs.begin(), fs.end(), (int32_t)RT_FS_QSC) != fs.end();
   cudaError_t ce = cudaSuccess;
+  if (any_qsc && ce == cudaSuccess) ce = cudaMalloc(&h->Q64, 4 * nc * 8);
+  if (any_qsc && ce == cudaSuccess) ce = cudaMalloc(&h->Q32, 4 * nc * 4);
   if (ce == cudaSuccess) ce = cudaMalloc(&h->E64, nc * 8);
   if (ce == cudaSuccess) ce = cudaMalloc(&h->A64, nc * 8);
   if (ce == cudaSuccess) ce = cudaMalloc(&h->B64, nc * 8);
   if (ce == cudaSuccess) ce = cudaMalloc(&h->E32, nc * 4);
   if (ce == cudaSuccess) ce = cudaMalloc(&h->A32, nc * 4);
   if (ce == cudaSuccess) ce = cudaMalloc(&h->B32, nc * 4);
-  if (ce == cudaSuccess) ce = (cudaError_t)rt::launch_coefficients(h, d_z, d_zoff, d_chi, d_mu, d_clsoff, d_fs, 0);
+  if (ce == cudaSuccess) ce = (cudaError_t)rt::launch_coefficients(h, d_z, d_zoff, d_chi, d_mu, d_clsoff, 0);
   if (ce == cudaSuccess) ce = cudaDeviceSynchronize();
   cleanup_tmp();
   if (ce != cudaSuccess) {

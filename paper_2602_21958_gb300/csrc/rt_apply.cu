@@ -43,8 +43,12 @@ __global__ void __launch_bounds__(RB) k_sweep_tiles(Common cm, Tables<T> tb, con
   if (r >= c.nr) return;
   const int64_t base = rhs * E + c.x_off;
   const double *ts = use_tsrc ? cm.tsrc + c.g_off : nullptr;
-  sweep_ray<T, double, double, AH>(c, tb, cm, S ? S + base : nullptr, ts, x ? x + base : nullptr, nullptr,
-                                   y + base, out, inflow != 0, r);
+  if (c.fs == 2)
+    sweep_ray<T, double, double, AH, true>(c, tb, cm, S ? S + base : nullptr, ts, x ? x + base : nullptr, nullptr,
+                                           y + base, out, inflow != 0, r);
+  else
+    sweep_ray<T, double, double, AH, false>(c, tb, cm, S ? S + base : nullptr, ts, x ? x + base : nullptr,
+                                            nullptr, y + base, out, inflow != 0, r);
 }
 
 template <typename T>
@@ -156,11 +160,11 @@ static int box_apply_t(rt_handle *h, const Tables<T> &tb, int op, const TX *x, v
 static int apply_box_s(rt_handle *h, int op, bool fp64, const void *x, bool xf, void *y, bool yf, cudaStream_t s,
                        void *scratch) {
   if (fp64 || h->precision == 0) {
-    const Tables<double> tb{h->E64, h->A64, h->B64, h->Uw64, h->Ul64, h->Rw64, h->Psi64, h->gam64};
+    const Tables<double> tb = tables64(h);
     if (xf) return (int)cudaErrorInvalidValue;
     return box_apply_t<double, double>(h, tb, op, static_cast<const double *>(x), y, yf, s, scratch);
   }
-  const Tables<float> tb{h->E32, h->A32, h->B32, h->Uw32, h->Ul32, h->Rw32, h->Psi32, h->gam32};
+  const Tables<float> tb = tables32(h);
   if (xf) return box_apply_t<float, float>(h, tb, op, static_cast<const float *>(x), y, yf, s, scratch);
   return box_apply_t<float, double>(h, tb, op, static_cast<const double *>(x), y, yf, s, scratch);
 }
@@ -173,10 +177,10 @@ static int launch_apply_s(rt_handle *h, int op, bool fp64, const double *x, doub
                           bool first_rhs_only, void *scratch) {
   if (h->dims == 3) return apply_box_s(h, op, fp64, x, false, y, false, s, scratch);
   if (fp64 || h->precision == 0) {
-    const Tables<double> tb{h->E64, h->A64, h->B64, h->Uw64, h->Ul64, h->Rw64, h->Psi64, h->gam64};
+    const Tables<double> tb = tables64(h);
     return run_apply<double>(h, tb, op, x, y, s, first_rhs_only, scratch);
   }
-  const Tables<float> tb{h->E32, h->A32, h->B32, h->Uw32, h->Ul32, h->Rw32, h->Psi32, h->gam32};
+  const Tables<float> tb = tables32(h);
   return run_apply<float>(h, tb, op, x, y, s, first_rhs_only, scratch);
 }
 

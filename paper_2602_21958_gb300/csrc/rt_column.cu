@@ -26,64 +26,122 @@ int solve_block_threads() { return kNT; }
 // optical depth of layer l is 0.5 (chi_l + chi_{l+1}) (z_{l+1} - z_l) / |mu|.
 // SC-L step: e = e^-d, w0 = -expm1(-d), beta = w1/d (series below d = 0.1),
 // alpha = w0 - beta.  Implicit Euler: e = 1/(1+d), alpha = 0, beta = d/(1+d).
+// Quadratic SC (fs == 2): the parabola through upwind u, current c and
+// downwind point at path depths 0, du, du + dd, integrated against
+// e^-(du - s) with the moments W1/du^2 and W2/du^3 (series below 0.1):
+//   psi_c = du ((du + dd) W1/du^2 - du W2/du^3) / dd
+//   psi_d = du^3 (W2/du^3 - W1/du^2) / (dd (du + dd)),  psi_u = w0 - psi_c - psi_d;
+// a ray's last step (no downwind point) is SC-L with psi_d = 0.  Rays going
+// down take dd from layer l+1, rays going up from layer l-1.
+struct CoefOut {
+  double *E, *A, *B, *C, *A2, *B2, *C2;
+  float *Ef, *Af, *Bf, *Cf, *A2f, *B2f, *C2f;
+};
+
+__device__ __forceinline__ void scl_step(double d, double &e, double &a, double &b) {
+  e = exp(-d);
+  const double w0 = -expm1(-d);
+  double beta;
+  if (d < 0.1) {
+    // w1/d = sum_{k>=1} (-1)^(k+1) d^k/(k+1)! = (d/2)(1 - (d/3)(1 - (d/4)(1 - ...)))
+    // 16 terms, nested from the innermost factor d/17
+    double s = 1.0;
+    for (int j = 17; j >= 3; --j) s = 1.0 - (d / j) * s;
+    beta = 0.5 * d * s;
+  } else {
+    beta = (d - w0) / d;
+  }
+  b = beta;
+  a = w0 - beta;
+}
+
+// quadratic step weights for depths du (u -> c) and dd (c -> d)
+__device__ __forceinline__ void qsc_step(double du, double dd, double &pu, double &pc, double &pd) {
+  double m1, m2;  // W1/du^2, W2/du^3
+  if (du < 0.1) {
+    // W1/du^2 = sum_{k>=0} (-1)^k du^k/(k+2)!,  W2/du^3 = 2 sum_{k>=0} (-1)^k du^k/(k+3)!
+    // nested: 1/2 (1 - du/3 (1 - du/4 (...))), 1/3 (1 - du/4 (1 - du/5 (...)))
+    double s1 = 1.0, s2 = 1.0;
+    for (int j = 19; j >= 3; --j) s1 = 1.0 - (du / j) * s1;
+    for (int j = 20; j >= 4; --j) s2 = 1.0 - (du / j) * s2;
+    m1 = 0.5 * s1;
+    m2 = s2 / 3.0;
+  } else {
+    const double w1 = du + expm1(-du);
+    m1 = w1 / (du * du);
+    m2 = (du * du - 2.0 * w1) / (du * du * du);
+  }
+  const double w0 = -expm1(-du);
+  pc = du * ((du + dd) * m1 - du * m2) / dd;
+  pd = du * du * du * (m2 - m1) / (dd * (du + dd));
+  pu = w0 - pc - pd;
+}
+
 __global__ void k_coefficients(const ColDev *__restrict__ cols, const double *__restrict__ z,
                                const int64_t *__restrict__ zoff, const double *__restrict__ chi,
                                const double *__restrict__ mu_cls, const int32_t *__restrict__ cls_off,
-                               const int32_t *__restrict__ fs, double *E, double *A, double *B,
-                               float *Ef, float *Af, float *Bf) {
+                               CoefOut o) {
   const int col = blockIdx.y;
   const ColDev c = cols[col];
   const int64_t count = (int64_t)(c.nz - 1) * c.ncls * c.nn;
+  auto dtau = [&](int layer, int f, int cl) {
+    const double dz = z[zoff[col] + layer + 1] - z[zoff[col] + layer];
+    const double cbar = 0.5 * (chi[c.g_off + (int64_t)layer * c.nn + f] +
+                               chi[c.g_off + (int64_t)(layer + 1) * c.nn + f]);
+    return cbar * dz / mu_cls[cls_off[col] + cl];
+  };
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int f = (int)(i % c.nn);
     const int cl = (int)((i / c.nn) % c.ncls);
     const int layer = (int)(i / ((int64_t)c.nn * c.ncls));
-    const double dz = z[zoff[col] + layer + 1] - z[zoff[col] + layer];
-    const double cbar = 0.5 * (chi[c.g_off + (int64_t)layer * c.nn + f] +
-                               chi[c.g_off + (int64_t)(layer + 1) * c.nn + f]);
-    const double d = cbar * dz / mu_cls[cls_off[col] + cl];
+    const double d = dtau(layer, f, cl);
     double e, a, b;
-    if (fs[col] == 1) {
+    if (c.fs == 1) {
       e = 1.0 / (1.0 + d);
       a = 0.0;
       b = d * e;
     } else {
-      e = exp(-d);
-      const double w0 = -expm1(-d);
-      double beta;
-      if (d < 0.1) {
-        // w1/d = sum_{k>=1} (-1)^(k+1) d^k/(k+1)! = (d/2)(1 - (d/3)(1 - (d/4)(1 - ...)))
-        // 16 terms, nested from the innermost factor d/17
-        double s = 1.0;
-        for (int j = 17; j >= 3; --j) s = 1.0 - (d / j) * s;
-        beta = 0.5 * d * s;
-      } else {
-        beta = (d - w0) / d;
-      }
-      b = beta;
-      a = w0 - beta;
+      scl_step(d, e, a, b);
     }
-    const int64_t o = c.c_off + i;
-    E[o] = e;
-    A[o] = a;
-    B[o] = b;
-    Ef[o] = (float)e;
-    Af[o] = (float)a;
-    Bf[o] = (float)b;
+    const int64_t k = c.c_off + i;
+    o.E[k] = e;
+    o.Ef[k] = (float)e;
+    if (c.fs != 2) {
+      o.A[k] = a;
+      o.B[k] = b;
+      o.Af[k] = (float)a;
+      o.Bf[k] = (float)b;
+      continue;
+    }
+    double pu, pc, pd;
+    // going down: u = layer, c = layer + 1, downwind layer + 2
+    if (layer + 1 < c.nz - 1) qsc_step(d, dtau(layer + 1, f, cl), pu, pc, pd);
+    else { pu = a; pc = b; pd = 0.0; }
+    o.A[k] = pu; o.B[k] = pc; o.C[k] = pd;
+    o.Af[k] = (float)pu; o.Bf[k] = (float)pc; o.Cf[k] = (float)pd;
+    // going up: u = layer + 1, c = layer, downwind layer - 1
+    if (layer >= 1) qsc_step(d, dtau(layer - 1, f, cl), pu, pc, pd);
+    else { pu = a; pc = b; pd = 0.0; }
+    o.A2[k] = pu; o.B2[k] = pc; o.C2[k] = pd;
+    o.A2f[k] = (float)pu; o.B2f[k] = (float)pc; o.C2f[k] = (float)pd;
   }
 }
 
-
 int launch_coefficients(rt_handle *h, const double *d_z, const int64_t *d_zoff,
-                        const double *d_chi, const double *d_mu_cls, const int32_t *d_cls_off,
-                        const int32_t *d_fs, cudaStream_t s) {
+                        const double *d_chi, const double *d_mu_cls, const int32_t *d_cls_off, cudaStream_t s) {
   int64_t most = 1;
   for (const ColDev &c : h->h_cols) most = std::max<int64_t>(most, (int64_t)(c.nz - 1) * c.ncls * c.nn);
   const int bx = (int)std::min<int64_t>((most + 255) / 256, 4096);
   dim3 grid(bx, h->n_cols);
-  k_coefficients<<<grid, 256, 0, s>>>(h->d_cols, d_z, d_zoff, d_chi, d_mu_cls, d_cls_off, d_fs, h->E64,
-                                      h->A64, h->B64, h->E32, h->A32, h->B32);
+  const int64_t nc = h->n_coef;
+  CoefOut o{h->E64, h->A64, h->B64, nullptr, nullptr, nullptr, nullptr,
+            h->E32, h->A32, h->B32, nullptr, nullptr, nullptr, nullptr};
+  if (h->Q64) {
+    o.C = h->Q64; o.A2 = h->Q64 + nc; o.B2 = h->Q64 + 2 * nc; o.C2 = h->Q64 + 3 * nc;
+    o.Cf = h->Q32; o.A2f = h->Q32 + nc; o.B2f = h->Q32 + 2 * nc; o.C2f = h->Q32 + 3 * nc;
+  }
+  k_coefficients<<<grid, 256, 0, s>>>(h->d_cols, d_z, d_zoff, d_chi, d_mu_cls, d_cls_off, o);
   return (int)cudaGetLastError();
 }
 
@@ -1323,8 +1381,8 @@ int launch_bicgstab(rt_handle *h, const double *b, double *x, double tol, int ma
                     int use_x0, cudaStream_t s) {
   SolveParams p;
   p.cm = Common{h->d_cols, h->d_dir_cls, h->d_dir_up, h->d_tsrc, h->d_Itop, h->d_Ibot};
-  p.t64 = Tables<double>{h->E64, h->A64, h->B64, h->Uw64, h->Ul64, h->Rw64, h->Psi64, h->gam64};
-  p.t32 = Tables<float>{h->E32, h->A32, h->B32, h->Uw32, h->Ul32, h->Rw32, h->Psi32, h->gam32};
+  p.t64 = tables64(h);
+  p.t32 = tables32(h);
   p.order = h->d_order;
   p.n_cols = h->n_cols;
   p.n_inst = h->n_cols * h->n_rhs;
@@ -1359,8 +1417,8 @@ int launch_solve(rt_handle *h, const double *b, double *x, double tol, double to
                  int max_outer, int use_x0, cudaStream_t s, int m_in) {
   SolveParams p;
   p.cm = Common{h->d_cols, h->d_dir_cls, h->d_dir_up, h->d_tsrc, h->d_Itop, h->d_Ibot};
-  p.t64 = Tables<double>{h->E64, h->A64, h->B64, h->Uw64, h->Ul64, h->Rw64, h->Psi64, h->gam64};
-  p.t32 = Tables<float>{h->E32, h->A32, h->B32, h->Uw32, h->Ul32, h->Rw32, h->Psi32, h->gam32};
+  p.t64 = tables64(h);
+  p.t32 = tables32(h);
   p.order = h->d_order;
   p.n_cols = h->n_cols;
   p.n_inst = h->n_cols * h->n_rhs;

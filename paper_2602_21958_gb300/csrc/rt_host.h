@@ -58,6 +58,11 @@ struct rt_handle {
   // float32 tables (mixed precision)
   float *E32 = nullptr, *A32 = nullptr, *B32 = nullptr, *Uw32 = nullptr, *Ul32 = nullptr,
         *Rw32 = nullptr, *Psi32 = nullptr, *gam32 = nullptr;
+  // quadratic short characteristics: C | A2 | B2 | C2, each n_coef long (null
+  // when no column uses it)
+  double *Q64 = nullptr;
+  float *Q32 = nullptr;
+  int64_t n_coef = 0;           // entries of each step-coefficient array
   double *b_int = nullptr;       // internal right-hand side [E]
   int32_t *d_order = nullptr;    // instance order, largest first
   int *d_queue = nullptr;        // work-queue counters (2 ints)
@@ -98,8 +103,28 @@ struct rt_handle {
 namespace rt {
 // launchers (defined in rt_column.cu); all return a cudaError_t as int
 int launch_coefficients(rt_handle *h, const double *d_z, const int64_t *d_zoff,
-                        const double *d_chi, const double *d_mu_cls, const int32_t *d_cls_off,
-                        const int32_t *d_fs, cudaStream_t s);
+                        const double *d_chi, const double *d_mu_cls, const int32_t *d_cls_off, cudaStream_t s);
+// the handle's tables in one precision (quadratic-SC arrays when present)
+inline Tables<double> tables64(const rt_handle *h) {
+  Tables<double> t{h->E64, h->A64, h->B64, h->Uw64, h->Ul64, h->Rw64, h->Psi64, h->gam64};
+  if (h->Q64) {
+    t.C = h->Q64;
+    t.A2 = h->Q64 + h->n_coef;
+    t.B2 = h->Q64 + 2 * h->n_coef;
+    t.C2 = h->Q64 + 3 * h->n_coef;
+  }
+  return t;
+}
+inline Tables<float> tables32(const rt_handle *h) {
+  Tables<float> t{h->E32, h->A32, h->B32, h->Uw32, h->Ul32, h->Rw32, h->Psi32, h->gam32};
+  if (h->Q32) {
+    t.C = h->Q32;
+    t.A2 = h->Q32 + h->n_coef;
+    t.B2 = h->Q32 + 2 * h->n_coef;
+    t.C2 = h->Q32 + 3 * h->n_coef;
+  }
+  return t;
+}
 int launch_apply(rt_handle *h, int op, bool fp64, const double *x, double *y, cudaStream_t s,
                  bool first_rhs_only = false);
 int launch_solve(rt_handle *h, const double *b, double *x, double tol, double tol_inner, int m,

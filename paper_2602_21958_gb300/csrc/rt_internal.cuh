@@ -29,6 +29,7 @@ struct ColDev {
   int32_t ncls;     // number of distinct |mu|
   int32_t rp;       // rank of the angular factor
   int32_t rdiag;    // 1: frequency kernel is diagonal (coherent scattering)
+  int32_t fs;       // formal solver: 0 SC-L, 1 implicit Euler, 2 quadratic SC
 };
 
 // Arrays in one arithmetic precision T (double: fp64 path; float: mixed path).
@@ -40,6 +41,10 @@ struct Tables {
   const T *RwT;         // [nn'][nn] (R w_nu)^T, or [nn] diagonal when rdiag
   const T *PsiwT;       // [nr'][nr] (Psi diag(w_r))^T for dense kernels
   const T *gamma;       // [nz][nn]
+  // quadratic short characteristics (fs == 2): I_c = E I_u + A S_u + B S_c + C S_d
+  // with (A, B, C) for rays going down (mu < 0) and (A2, B2, C2) going up,
+  // indexed like E by the layer between u and c (C = 0 on a ray's last step)
+  const T *C = nullptr, *A2 = nullptr, *B2 = nullptr, *C2 = nullptr;
 };
 
 struct Common {
@@ -355,15 +360,18 @@ enum SweepOut : int {
 // for kOutResid (0 otherwise).  y may alias S: each thread reads S and writes y
 // only at the points of its own rays, the source value is read before the
 // output at the same point is written.
-template <typename T, typename TX, typename TY, int kAhead = 4>
+template <typename T, typename TX, typename TY, int kAhead = 4, bool kQuad = false>
 __device__ double sweep_ray(const ColDev &c, const Tables<T> &tb, const Common &cm, const T *S,
                             const double *__restrict__ tsrc, const TX *__restrict__ x,
                             const double *__restrict__ bv, TY *y, int out, bool inflow, int r) {
   const int nz = c.nz, nn = c.nn, nr = c.nr, ncls = c.ncls;
-  const T *E = tb.E + c.c_off, *A = tb.A + c.c_off, *B = tb.B + c.c_off;
-  double ss = 0.0;
   const int d = r / nn, f = r - d * nn;
   const int up = cm.dir_up[c.d_off + d];
+  constexpr bool quad = kQuad;  // quadratic SC (c.fs == 2): a downwind source term
+  const T *E = tb.E + c.c_off;
+  const T *A = (quad && up ? tb.A2 : tb.A) + c.c_off, *B = (quad && up ? tb.B2 : tb.B) + c.c_off;
+  const T *Cq = quad ? (up ? tb.C2 : tb.C) + c.c_off : nullptr;
+  double ss = 0.0;
   const int cls = cm.dir_cls[c.d_off + d];
   const int step = up ? -1 : 1;
   const int i0 = up ? nz - 1 : 0;
@@ -390,8 +398,8 @@ __device__ double sweep_ray(const ColDev &c, const Tables<T> &tb, const Common &
   };
   // loads of the points i+step .. i+cnt*step (cnt <= kAhead); indices past
   // the column are clamped to its last point (the values are not used)
-  auto load = [&](int i, int cnt, T (&e)[kAhead], T (&a)[kAhead], T (&b)[kAhead], T (&sc)[kAhead],
-                  TX (&xv)[kAhead]) {
+  auto load = [&](int i, int cnt, T (&e)[kAhead], T (&a)[kAhead], T (&b)[kAhead], T (&cq)[kAhead],
+                  T (&sc)[kAhead], TX (&xv)[kAhead]) {
 #pragma unroll
     for (int u = 0; u < kAhead; ++u) {
       int ic = i + (u + 1) * step;
@@ -401,6 +409,7 @@ __device__ double sweep_ray(const ColDev &c, const Tables<T> &tb, const Common &
       e[u] = E[ci];
       a[u] = A[ci];
       b[u] = B[ci];
+      cq[u] = quad ? Cq[ci] : T(0);
       sc[u] = src(ic);
       xv[u] = want_x ? x[(int64_t)ic * nr + r] : TX(0);
     }
@@ -409,21 +418,25 @@ __device__ double sweep_ray(const ColDev &c, const Tables<T> &tb, const Common &
   emit(i0, Iu, want_x ? x[(int64_t)i0 * nr + r] : TX(0));
   // chunks of kAhead points; the next chunk's loads are issued before the
   // current chunk's recurrence (2 kAhead points of loads in flight)
-  T e0[kAhead], a0[kAhead], b0[kAhead], s0[kAhead];
+  T e0[kAhead], a0[kAhead], b0[kAhead], c0[kAhead], s0[kAhead];
   TX x0[kAhead];
   int i = i0;
   int cnt = min(kAhead, nz - 1);
-  if (cnt > 0) load(i, cnt, e0, a0, b0, s0, x0);
+  if (cnt > 0) load(i, cnt, e0, a0, b0, c0, s0, x0);
   for (int done = 1; done < nz; done += kAhead) {
     const int inext = i + cnt * step;
     const int cnext = min(kAhead, nz - done - cnt);
-    T e1[kAhead], a1[kAhead], b1[kAhead], s1[kAhead];
+    T e1[kAhead], a1[kAhead], b1[kAhead], c1[kAhead], s1[kAhead];
     TX x1[kAhead];
-    if (cnext > 0) load(inext, cnext, e1, a1, b1, s1, x1);
+    if (cnext > 0) load(inext, cnext, e1, a1, b1, c1, s1, x1);
 #pragma unroll
     for (int u = 0; u < kAhead; ++u) {
       if (u < cnt) {
-        const T Ic = fma(e0[u], Iu, fma(a0[u], Su, b0[u] * s0[u]));
+        T Ic = fma(e0[u], Iu, fma(a0[u], Su, b0[u] * s0[u]));
+        if (quad) {  // downwind source: next point of this chunk, or the next chunk's first
+          const T Sd = u + 1 < cnt ? s0[u + 1 < kAhead ? u + 1 : 0] : (cnext > 0 ? s1[0] : T(0));
+          Ic = fma(c0[u], Sd, Ic);
+        }
         emit(i + (u + 1) * step, Ic, x0[u]);
         Iu = Ic;
         Su = s0[u];
@@ -434,6 +447,7 @@ __device__ double sweep_ray(const ColDev &c, const Tables<T> &tb, const Common &
       e0[u] = e1[u];
       a0[u] = a1[u];
       b0[u] = b1[u];
+      c0[u] = c1[u];
       s0[u] = s1[u];
       x0[u] = x1[u];
     }
@@ -458,8 +472,13 @@ __device__ __noinline__ double sweep_column(const ColDev &c, const Tables<T> &tb
                                const TX *__restrict__ x, const double *__restrict__ bv,
                                TY *y, int out, bool inflow) {
   double ss = 0.0;
-  for (int r = threadIdx.x; r < c.nr; r += blockDim.x)
-    ss += sweep_ray<T, TX, TY, kAhead>(c, tb, cm, S, tsrc, x, bv, y, out, inflow, r);
+  if (c.fs == 2) {
+    for (int r = threadIdx.x; r < c.nr; r += blockDim.x)
+      ss += sweep_ray<T, TX, TY, kAhead, true>(c, tb, cm, S, tsrc, x, bv, y, out, inflow, r);
+  } else {
+    for (int r = threadIdx.x; r < c.nr; r += blockDim.x)
+      ss += sweep_ray<T, TX, TY, kAhead, false>(c, tb, cm, S, tsrc, x, bv, y, out, inflow, r);
+  }
   return ss;
 }
 

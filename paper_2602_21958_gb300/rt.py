@@ -13,13 +13,13 @@ from typing import Optional, Sequence
 
 import numpy as np
 
-from .workloads import FS_IE, Problem
+from .workloads import FS_IE, FS_QSC, Problem
 
 _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "librt_gb300.so")
 
 RT_OK, RT_ERR_ARG, RT_ERR_CUDA, RT_ERR_OOM, RT_ERR_NOCONV, RT_ERR_BREAKDOWN, RT_ERR_NONFINITE, \
     RT_ERR_TIMEOUT = range(8)
-RT_FS_SCL, RT_FS_IE = 0, 1
+RT_FS_SCL, RT_FS_IE, RT_FS_QSC = 0, 1, 2
 RT_P_FP64, RT_P_MIXED = 0, 1
 RT_OP_A, RT_OP_LAMBDA, RT_OP_SIGMA, RT_OP_RHS = 0, 1, 2, 3
 RT_KRYLOV_GMRES, RT_KRYLOV_BICGSTAB = 0, 1
@@ -151,7 +151,7 @@ def make_desc(p: Problem, keep: list) -> rt_desc:
     d.n_dir, d.n_nu = p.n_dir, p.n_nu
     for k, v in arrs.items():
         setattr(d, k, v.ctypes.data_as(_dp) if v is not None else _dp())
-    d.formal_solver = RT_FS_IE if p.formal_solver == FS_IE else RT_FS_SCL
+    d.formal_solver = {FS_IE: RT_FS_IE, FS_QSC: RT_FS_QSC}.get(p.formal_solver, RT_FS_SCL)
     return d
 
 

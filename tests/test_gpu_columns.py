@@ -46,6 +46,9 @@ def small_problems():
         "iso_crd_ie": W.paper_iso(6, 5, "crd"),
         "dense": W.two_level_column(np.logspace(-2, 2, 6), 4, 2, 5, "r2", 1e-2, 1.0).with_dense_kernel(),
         "minimal": W.two_level_column(np.array([0.1, 2.0]), 2, 1, 1, "crd", 0.5, 1.0),
+        "qsc": W.two_level_column(np.logspace(-3, 3, 17), 4, 2, 9, "r2", 1e-3, 1.0, formal_solver=W.FS_QSC),
+        "qsc_short": W.two_level_column(np.array([0.05, 0.4, 3.0]), 2, 1, 3, "crd", 0.1, 1.0,
+                                        formal_solver=W.FS_QSC),
     }
 
 
@@ -117,7 +120,7 @@ def test_host_buffers_match_device_buffers(rt):
 # n_rhs = 1: one instance, solved by the grid-wide kernels; n_rhs = 2: two
 # instances, one CTA each (the batched solve kernels)
 @pytest.mark.parametrize("n_rhs", [1, 2])
-@pytest.mark.parametrize("name", ["crd", "r2_ragged", "mono_ie", "iso_coh", "dense", "minimal"])
+@pytest.mark.parametrize("name", ["crd", "r2_ragged", "mono_ie", "iso_coh", "dense", "minimal", "qsc"])
 def test_solve_fp64_matches_lu(rt, name, n_rhs):
     p = small_problems()[name]
     h = rt.Handle(p, n_rhs=n_rhs, precision=rt.RT_P_FP64, max_restart=64)
@@ -132,7 +135,7 @@ def test_solve_fp64_matches_lu(rt, name, n_rhs):
 
 
 @pytest.mark.parametrize("n_rhs", [1, 2])
-@pytest.mark.parametrize("name", ["crd", "r2_ragged", "iso_coh", "dense"])
+@pytest.mark.parametrize("name", ["crd", "r2_ragged", "iso_coh", "dense", "qsc"])
 def test_solve_mixed_refinement_matches_lu(rt, name, n_rhs):
     p = small_problems()[name]
     h = rt.Handle(p, n_rhs=n_rhs, precision=rt.RT_P_MIXED, max_restart=64)
@@ -148,7 +151,8 @@ def test_solve_mixed_refinement_matches_lu(rt, name, n_rhs):
 
 
 def test_batch_solve_internal_rhs_and_instances(rt):
-    probs = [small_problems()[k] for k in ("crd", "r2_ragged", "minimal")]
+    # columns with different formal solvers (SC-L, quadratic SC) in one batch
+    probs = [small_problems()[k] for k in ("crd", "r2_ragged", "minimal", "qsc", "qsc_short")]
     n_rhs = 2
     E = sum(p.n for p in probs)
     h = rt.Handle(probs, n_rhs=n_rhs, precision=rt.RT_P_MIXED, max_restart=48)
