@@ -114,7 +114,7 @@ void free_handle(rt_handle *h) {
                   h->b_int, h->d_order, h->d_queue, h->ws.V, h->ws.S, h->ws.H,
                   h->so.outer, h->so.inner, h->so.status, h->so.relres, h->so.bytes,
                   h->stage_x, h->stage_y, h->d_sig_tiles, h->d_sw_tiles, h->apply_S,
-                  h->d_tc_jobs, h->d_tc_off, h->d_tc_tiles, h->d_tc_xb, h->d_err, h->d_geo,
+                  h->d_tc_jobs, h->d_tc_off, h->d_tc_tiles, h->d_tc_xb, h->d_tc_maps, h->d_err, h->d_geo,
                   h->chi64, h->chi32, h->g_part, h->g_red, h->g_coef, h->g_r, h->Q64, h->Q32};
   for (void *p : ptrs)
     if (p) cudaFree(p);

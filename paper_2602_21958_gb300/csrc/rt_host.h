@@ -81,7 +81,8 @@ struct rt_handle {
   void *d_tc_jobs = nullptr;          // TcJob[n_tc_jobs]
   int64_t *d_tc_off = nullptr;        // per column offset into the bf16 tiles
   uint16_t *d_tc_tiles = nullptr;     // pre-tiled bf16 PsiW
-  uint32_t *d_tc_xb = nullptr;        // X packed to bf16 (A operand), n_rhs*E values
+  uint32_t *d_tc_xb = nullptr;        // X packed to bf16 (A operand), rows stacked per column
+  void *d_tc_maps = nullptr;          // TMA tensor maps over d_tc_xb, one per column
   int *d_err = nullptr;               // device error word (bounded waits)
   // 3D boxes: geometry, per-direction (sx, sy, ds, up), opacity, grid-solve scratch
   // CUDA graph of the batched solve (queue reset + persistent kernel), reused

@@ -1,22 +1,26 @@
 // rt_sigma_tc.cu -- Sigma with a dense kernel Psi on the 5th-generation tensor
 // cores (tcgen05, sm_103a):  S_p = Gamma_p Psi W X_p  (eq. Sigma), i.e. for one
-// column the GEMM  C[rows, r] = sum_q X[rows, q] PsiW[r, q]  with the rows the
-// points of every right-hand side stacked, then S = gamma * C.
+// column the GEMM  C[points, r] = sum_q X[points, q] PsiW[r, q]  per
+// right-hand side, then S = gamma * C.
 //
-//   operands  : bf16.  X is packed to bf16 once per apply (k_to_bf16); A tiles
-//               (128 rows x 64 q) arrive by 16-byte cp.async copies straight
-//               into the canonical no-swizzle K-major layout; B = PsiW is
-//               pre-tiled in global memory as the exact shared-memory image of
-//               each (256-ray, 64-q) block and fetched with one cp.async.bulk
-//               completing on an mbarrier.
-//   accumulate: fp32 in tensor memory (128 lanes x 256 columns), read back
+//   operands  : bf16.  X is packed to bf16 once per apply (k_to_bf16) with each
+//               column's (rhs, point) rows stacked; A boxes (8 q x 128 rows)
+//               arrive by TMA (a 2D tensor map per column) straight into the
+//               canonical no-swizzle K-major layout, zero-filled past the
+//               column; B = PsiW is pre-tiled in global memory as the exact
+//               shared-memory image of each (256-ray, 64-q) block, one
+//               cp.async.bulk.
+//   accumulate: fp32 in tensor memory, two 128 x 256 accumulators, read back
 //               with tcgen05.ld and scaled by Gamma in the epilogue.
-//   pipeline  : four stages; thread 0 issues tcgen05.mma (M=128, N<=256,
-//               K=16, four per 64-wide chunk) and commits each chunk to an
-//               mbarrier; the stage freed by chunk k-1 is refilled with chunk
-//               k+3 while the MMAs of chunk k run.
-// Every wait is bounded; on timeout the CTA raises an error flag, drains what
-// it issued (bounded), frees its tensor memory and returns.
+//   schedule  : persistent CTAs (one per SM) walk the tile list with
+//               specialised warps -- a TMA producer, an MMA issuer and four
+//               epilogue warps -- so a tile's epilogue overlaps the next
+//               tile's MMAs; stages and accumulators hand over through
+//               mbarriers (full/empty, accumulator full/empty).
+// Every wait is bounded; on timeout the CTA raises an error flag, lets the
+// other roles stop, drains what it issued (bounded), frees its tensor memory
+// and returns.
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -33,19 +37,8 @@ namespace rt {
 constexpr int kTcBM = 128;               // rows per tile (MMA M, TMEM lanes)
 constexpr int kTcBN = 256;               // rays per tile (MMA N max, TMEM columns)
 constexpr int kTcBK = 64;                // q per stage: four MMAs of K = 16
-constexpr int kTcThreads = 256;
 constexpr int kTcABytes = kTcBM * kTcBK * 2;   // 16 KB
 constexpr int kTcBBytes = kTcBN * kTcBK * 2;   // 32 KB
-constexpr int kTcStages = 4;
-constexpr int kTcLdt = kTcBN + 4;        // row stride (floats) of the epilogue tile in shared memory
-constexpr int kTcSmem = kTcStages * (kTcABytes + kTcBBytes) + 1024;
-
-struct TcJob {
-  int32_t col;  // column index
-  int32_t m0;   // first stacked row (rhs * nz + point)
-  int32_t n0;   // first ray
-  int32_t pad;
-};
 
 // Shared-memory matrix descriptor: no swizzle, K-major canonical layout of
 // 8-row x 16-byte core matrices; lbo = byte distance of K-adjacent core
@@ -96,49 +89,96 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
 }
 
 // ----------------------------------------------------------------- kernel
-// X -> bf16 (same layout), the A operand of the GEMM
+// X -> bf16, the A operand of the GEMM.  Column c's rows of all right-hand
+// sides are stacked: row m = rhs * nz + p at n_rhs * x_off + m * nr, so one 2D
+// TMA map per column covers every (rhs, point) row and a 128-row tile can
+// span two right-hand sides.  Block (x, col, rhs); dense tensor-core columns only.
 template <typename TX>
-__global__ void k_to_bf16(const TX *__restrict__ X, uint32_t *__restrict__ Xb, int64_t n2) {
+__global__ void k_to_bf16(const ColDev *__restrict__ cols, const TX *__restrict__ X, uint32_t *__restrict__ Xb,
+                          int64_t E, int n_rhs) {
+  const ColDev c = cols[blockIdx.y];
+  if (c.psi_off < 0 || c.nr % 16) return;
+  const int rhs = blockIdx.z;
+  const int64_t n2 = (int64_t)c.nz * c.nr / 2;
+  const TX *src = X + rhs * E + c.x_off;
+  uint32_t *dst = Xb + ((int64_t)n_rhs * c.x_off + (int64_t)rhs * c.nz * c.nr) / 2;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n2; i += (int64_t)gridDim.x * blockDim.x)
-    Xb[i] = pack_bf16((float)X[2 * i], (float)X[2 * i + 1]);
+    dst[i] = pack_bf16((float)src[2 * i], (float)src[2 * i + 1]);
 }
 
-// One (rows m0.., rays n0..) tile per CTA.  A (bf16 rows of X) arrives by
-// 16-byte cp.async copies straight into the core-matrix layout, B by one
-// cp.async.bulk per stage; kTcStages stages in flight.
+// Bounded mbarrier wait that also gives up once another role raised *abort.
+__device__ __forceinline__ bool tc_wait(uint64_t *bar, uint32_t par, volatile int *abort) {
+  const uint32_t a = smem_u32(bar);
+  for (long long it = 0; it < kSpinLimit; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(a), "r"(par)
+        : "memory");
+    if (done) return true;
+    if ((it & 1023) == 1023 && *abort) return false;
+  }
+  *abort = 1;
+  return false;
+}
+
+// Persistent, warp-specialised tile loop.  A CTA walks tiles (column, 128
+// stacked rhs/point rows, 256 rays) j = blockIdx.x, blockIdx.x + gridDim.x, ...:
+//   warp 0 (one thread): per 64-q chunk, 8 TMA boxes of A (8 q x 128 rows,
+//     straight into the no-swizzle K-major core-matrix layout, zero-filled
+//     past the column's edges) and one cp.async.bulk of the pre-tiled B into
+//     a ring of kT2Stages stages (full / empty mbarriers);
+//   warp 1 (one thread): tcgen05.mma (M=128, N<=256, K=16) into one of two
+//     TMEM accumulators (2 x 256 columns), releases each stage by
+//     tcgen05.commit, and the accumulator when the tile is complete;
+//   warps 2-5: epilogue of the previous tile while the next one is
+//     multiplied: TMEM (their 32-lane quarter) -> shared tile -> Gamma-scaled
+//     coalesced 16-byte stores, then the accumulator is handed back.
+constexpr int kT2Stages = 4;
+constexpr int kT2Threads = 192;
+constexpr int kT2Ld = 36;  // floats per row of a warp's epilogue slice (32 columns + 4)
+constexpr int kT2StageBytes = kTcABytes + kTcBBytes;
+constexpr int kT2EpiBytes = 4 * 32 * kT2Ld * 4;
+constexpr int kT2Smem = kT2Stages * kT2StageBytes + kT2EpiBytes + 1024;
+
+struct TcJob2 {
+  int32_t col, m0, n0, pad;  // rows m0.. of the column's stacked (rhs, point) rows, rays n0..
+};
+
 template <typename TS>
-__global__ void __launch_bounds__(kTcThreads, 1)
-    k_sigma_dense_tc(const ColDev *__restrict__ cols, const TcJob *__restrict__ jobs,
-                     const int64_t *__restrict__ btile_off, const uint16_t *__restrict__ btiles,
-                     const float *__restrict__ gamma, int n_rhs, int64_t E, const uint16_t *__restrict__ Xb,
-                     TS *__restrict__ S, int *err) {
+__global__ void __launch_bounds__(kT2Threads, 1)
+    k_sigma_dense_tc(const CUtensorMap *__restrict__ maps, const TcJob2 *__restrict__ jobs, int n_jobs,
+                     const ColDev *__restrict__ cols, const int64_t *__restrict__ btile_off,
+                     const uint16_t *__restrict__ btiles, const float *__restrict__ gamma, int64_t E,
+                     int n_rhs, TS *__restrict__ S, int *err) {
   extern __shared__ __align__(1024) uint8_t tc_smem[];
   uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(tc_smem) + 1023) & ~uintptr_t(1023));
-  __shared__ __align__(8) uint64_t bar_b[kTcStages], bar_mma[kTcStages];
+  __shared__ __align__(8) uint64_t full[kT2Stages], empty[kT2Stages], accf[2], acce[2];
   __shared__ uint32_t tmem_base;
-  auto sA = [&](int st) { return base + st * kTcABytes; };
-  auto sB = [&](int st) { return base + kTcStages * kTcABytes + st * kTcBBytes; };
-
-  const TcJob job = jobs[blockIdx.x];
-  const ColDev c = cols[job.col];
-  const int nr = c.nr, nn = c.nn, nz = c.nz;
-  const int M = n_rhs * nz;
-  const int n_valid = min(kTcBN, nr - job.n0);  // multiple of 16 (nr is)
-  const int nk = nr / 16;                        // MMA K-steps in total
-  const int nchunk = (nr + kTcBK - 1) / kTcBK;
-  const uint16_t *Bcol = btiles + btile_off[job.col] + (int64_t)(job.n0 / kTcBN) * nchunk * (kTcBN * kTcBK);
+  __shared__ volatile int abort_flag;
+  auto sA = [&](int st) { return base + st * kT2StageBytes; };
+  auto sB = [&](int st) { return base + st * kT2StageBytes + kTcABytes; };
+  float *epi = reinterpret_cast<float *>(base + kT2Stages * kT2StageBytes);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
   if (tid == 0) {
-    for (int i = 0; i < kTcStages; ++i) {
-      mbar_init(&bar_b[i], 1);
-      mbar_init(&bar_mma[i], 1);
+    for (int i = 0; i < kT2Stages; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], 1);
     }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&accf[i], 1);
+      mbar_init(&acce[i], 4);
+    }
+    abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 0) {
+  if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
-                 "r"(kTcBN)
+                 "r"(2 * kTcBN)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -146,144 +186,122 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_base;
-  const uint32_t idesc = tc_idesc(kTcBM, (n_valid + 15) / 16 * 16);
 
-  // A chunk = 128 rows x 8 groups of 8 bf16 (16 bytes).  Thread t copies row
-  // t/2, groups 2j + (t&1), j = 0..3: a lane pair reads one 32-byte sector.
-  const int arow = tid >> 1, akq = tid & 1;
-  const int agrow = job.m0 + arow;
-  const bool arow_ok = agrow < M;
-  int64_t arow_base = 0;
-  if (arow_ok) {
-    const int rhs = agrow / nz, p = agrow - rhs * nz;
-    arow_base = rhs * E + c.x_off + (int64_t)p * nr;
-  }
-  const uint32_t a_dst = (uint32_t)((arow >> 3) * 128 + (arow & 7) * 16);
-  int b_issued = 0;  // thread 0: B copies issued (chunks 0 .. b_issued-1)
-  auto issue = [&](int kc) {  // copies of chunk kc into stage kc % kTcStages
-    const int st = kc % kTcStages;
+  if (warp == 0) {
+    if (lane == 0) {  // ---- producer
+      int64_t g = 0;
+      for (int j = blockIdx.x; j < n_jobs && !abort_flag; j += gridDim.x) {
+        const TcJob2 J = jobs[j];
+        const ColDev c = cols[J.col];
+        const int nchunk = (c.nr + kTcBK - 1) / kTcBK;
+        const uint16_t *Bcol = btiles + btile_off[J.col] + (int64_t)(J.n0 / kTcBN) * nchunk * (kTcBN * kTcBK);
+        const CUtensorMap *map = maps + J.col;
+        for (int kc = 0; kc < nchunk; ++kc, ++g) {
+          const int st = (int)(g % kT2Stages);
+          if (g >= kT2Stages && !tc_wait(&empty[st], (uint32_t)((g / kT2Stages - 1) & 1), &abort_flag)) break;
+          mbar_expect_tx(&full[st], kT2StageBytes);
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int kq = 2 * j + akq;
-      const int q0 = kc * kTcBK + kq * 8;
-      const bool in = arow_ok && q0 < nr;
-      cp_async16(sA(st) + kq * (kTcBM / 8) * 128 + a_dst, Xb + (in ? arow_base + q0 : 0), in ? 16u : 0u);
+          for (int kq = 0; kq < 8; ++kq)  // 8 q x 128 rows per box: one K-group of core matrices
+            tma_load_2d(sA(st) + kq * (kTcBM / 8) * 128, map, kc * kTcBK + kq * 8, J.m0, &full[st]);
+          bulk_g2s(sB(st), Bcol + (int64_t)kc * (kTcBN * kTcBK), kTcBBytes, &full[st]);
+        }
+      }
+      // drain: every issued stage must have landed before the CTA leaves
+      for (int64_t q = (g > kT2Stages ? g - kT2Stages : 0); q < g; ++q)
+        tc_wait(&full[q % kT2Stages], (uint32_t)((q / kT2Stages) & 1), &abort_flag);
     }
-    cp_async_commit();
-    if (tid == 0) {
-      mbar_expect_tx(&bar_b[st], kTcBBytes);
-      bulk_g2s(sB(st), Bcol + (int64_t)kc * (kTcBN * kTcBK), kTcBBytes, &bar_b[st]);
-      b_issued = kc + 1;
-    }
-  };
-  const int pre = min(kTcStages - 1, nchunk);
-  for (int kc = 0; kc < pre; ++kc) issue(kc);
-  // Chunk kc: wait for its copies, MMAs by thread 0, then (while those run)
-  // refill the stage freed by chunk kc-1 with chunk kc+3.  A failed wait is
-  // made uniform by __syncthreads_or before anyone acts on it.
-  int committed = 0;  // chunks whose MMAs were committed
-  bool ok = true, bad = false;
-  for (int kc = 0; kc < nchunk; ++kc) {
-    const int st = kc % kTcStages;
-    const int later = min(nchunk - 1 - kc, kTcStages - 2);  // chunks issued after kc
-    if (later >= 2) cp_async_wait<2>();
-    else if (later == 1) cp_async_wait<1>();
-    else cp_async_wait<0>();
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    if (__syncthreads_or(bad ? 1 : 0)) {
-      ok = false;
-      break;
-    }
-    if (tid == 0) {
-      if (!mbar_wait(&bar_b[st], (kc / kTcStages) & 1)) {
-        bad = true;
-      } else {
+  } else if (warp == 1) {
+    if (lane == 0) {  // ---- MMA issuer
+      int64_t g = 0;
+      int t = 0;
+      bool any = false;
+      for (int j = blockIdx.x; j < n_jobs && !abort_flag; j += gridDim.x, ++t) {
+        const TcJob2 J = jobs[j];
+        const ColDev c = cols[J.col];
+        const int nchunk = (c.nr + kTcBK - 1) / kTcBK, nk = c.nr / 16;
+        const int n_valid = min(kTcBN, c.nr - J.n0);
+        const int b = t & 1;
+        if (t >= 2 && !tc_wait(&acce[b], (uint32_t)((t / 2 - 1) & 1), &abort_flag)) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t a0 = smem_u32(sA(st)), b0 = smem_u32(sB(st));
+        const uint32_t idesc = tc_idesc(kTcBM, (n_valid + 15) / 16 * 16);
+        const uint32_t dt = tmem + (uint32_t)(b * kTcBN);
+        for (int kc = 0; kc < nchunk; ++kc, ++g) {
+          const int st = (int)(g % kT2Stages);
+          if (!tc_wait(&full[st], (uint32_t)((g / kT2Stages) & 1), &abort_flag)) break;
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t a0 = smem_u32(sA(st)), b0 = smem_u32(sB(st));
 #pragma unroll
-        for (int ks = 0; ks < 4; ++ks) {
-          if (kc * 4 + ks < nk) {
-            const uint64_t ad = smem_desc(a0 + ks * 2 * (kTcBM / 8) * 128, (kTcBM / 8) * 128, 128);
-            const uint64_t bd = smem_desc(b0 + ks * 2 * (kTcBN / 8) * 128, (kTcBN / 8) * 128, 128);
-            tc_mma(tmem, ad, bd, idesc, (kc | ks) ? 1u : 0u);
+          for (int ks = 0; ks < 4; ++ks)
+            if (kc * 4 + ks < nk) {
+              const uint64_t ad = smem_desc(a0 + ks * 2 * (kTcBM / 8) * 128, (kTcBM / 8) * 128, 128);
+              const uint64_t bd = smem_desc(b0 + ks * 2 * (kTcBN / 8) * 128, (kTcBN / 8) * 128, 128);
+              tc_mma(dt, ad, bd, idesc, (kc | ks) ? 1u : 0u);
+            }
+          tc_commit(&empty[st]);
+          any = true;
+        }
+        tc_commit(&accf[b]);
+      }
+      // drain: the last commit completes after every earlier MMA of this thread
+      if (any && g > 0) tc_wait(&empty[(g - 1) % kT2Stages], (uint32_t)(((g - 1) / kT2Stages) & 1), &abort_flag);
+    }
+  } else {  // ---- epilogue warps 2..5
+    const int quarter = warp & 3;  // TMEM lanes 32*quarter.. (a warp's accessible quarter)
+    float *tile = epi + (warp - 2) * 32 * kT2Ld;
+    int t = 0;
+    for (int j = blockIdx.x; j < n_jobs && !abort_flag; j += gridDim.x, ++t) {
+      const TcJob2 J = jobs[j];
+      const ColDev c = cols[J.col];
+      const int nr = c.nr, nn = c.nn, nz = c.nz;
+      const int n_valid = min(kTcBN, nr - J.n0);
+      const int b = t & 1;
+      if (!tc_wait(&accf[b], (uint32_t)((t / 2) & 1), &abort_flag)) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      // 32-column slices: TMEM -> the warp's shared slice (row = lane) ->
+      // coalesced stores, 4 rows x 32 columns per warp instruction
+      for (int cs = 0; cs < n_valid; cs += 32) {
+        const int w = min(32, n_valid - cs);  // 16 or 32
+        const uint32_t taddr = tmem + (uint32_t)(b * kTcBN) + ((uint32_t)(quarter * 32) << 16) + (uint32_t)cs;
+        for (int h16 = 0; h16 < w; h16 += 16) {
+          float v[16];
+          tc_ld16(taddr + (uint32_t)h16, v);
+          float4 *dst = reinterpret_cast<float4 *>(tile + lane * kT2Ld + h16);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+        }
+        __syncwarp();
+#pragma unroll 2
+        for (int it = 0; it < 8; ++it) {
+          const int rr = it * 4 + (lane >> 3), ci = 4 * (lane & 7);
+          const int m = J.m0 + quarter * 32 + rr;
+          if (m < n_rhs * nz && ci < w) {
+            const int rhs = m / nz, p = m - rhs * nz;
+            const float4 v = *reinterpret_cast<const float4 *>(tile + rr * kT2Ld + ci);
+            const float *gp = gamma + c.g_off + (int64_t)p * nn;
+            const int r0 = J.n0 + cs + ci;
+            const float a0 = gp[r0 % nn] * v.x, a1 = gp[(r0 + 1) % nn] * v.y;
+            const float a2 = gp[(r0 + 2) % nn] * v.z, a3 = gp[(r0 + 3) % nn] * v.w;
+            TS *dst = S + rhs * E + c.x_off + (int64_t)p * nr + r0;
+            if (sizeof(TS) == 4) {
+              *reinterpret_cast<float4 *>(dst) = make_float4(a0, a1, a2, a3);
+            } else {
+              reinterpret_cast<double2 *>(dst)[0] = make_double2(a0, a1);
+              reinterpret_cast<double2 *>(dst)[1] = make_double2(a2, a3);
+            }
           }
         }
-        tc_commit(&bar_mma[st]);
+        __syncwarp();
       }
-    }
-    if (!bad) committed = kc + 1;  // thread 0's flag decides; others follow at the next barrier
-    const int nxt = kc + kTcStages - 1;
-    if (!bad && nxt < nchunk) {
-      // stage of chunk nxt was last read by the MMAs of chunk kc-1
-      if (kc >= 1 && !mbar_wait(&bar_mma[(kc - 1) % kTcStages], ((kc - 1) / kTcStages) & 1)) bad = true;
-      else issue(nxt);
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acce[b]);
     }
   }
-  if (__syncthreads_or(bad ? 1 : 0)) ok = false;
-  cp_async_wait<0>();
-  // drain: a commit completes after every earlier MMA of the issuing thread
-  bool drained = true;
-  {
-    __shared__ int s_committed;
-    if (tid == 0) s_committed = committed;
-    __syncthreads();
-    const int kl = s_committed - 1;
-    if (kl >= 0) drained = mbar_wait(&bar_mma[kl % kTcStages], (kl / kTcStages) & 1);
-    drained = !__syncthreads_or(drained ? 0 : 1);
-  }
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (ok && drained) {
-    // epilogue, two steps.  (1) TMEM -> shared tile ct[row][col] (the stage
-    // buffers are idle now): warp w reads TMEM lanes 32*(w%4).. and columns
-    // 128*(w/4)..; row stride kTcLdt floats keeps the 16-byte stores
-    // conflict-free.  (2) ct -> S with Gamma, a warp per row, lanes along
-    // the rays: coalesced 16-byte stores.
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    float *ct = reinterpret_cast<float *>(base);
-    const int quarter = warp & 3, half = warp >> 2;
-    const int row = quarter * 32 + lane;
-    for (int cc = 0; cc < kTcBN / 2; cc += 16) {
-      const int col0 = half * (kTcBN / 2) + cc;
-      if (col0 >= n_valid) break;  // uniform across the warp
-      float v[16];
-      tc_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)col0, v);
-      float4 *dst = reinterpret_cast<float4 *>(ct + row * kTcLdt + col0);
-#pragma unroll
-      for (int t = 0; t < 4; ++t) dst[t] = make_float4(v[4 * t], v[4 * t + 1], v[4 * t + 2], v[4 * t + 3]);
-    }
-    __syncthreads();
-    const int nwarps = kTcThreads / 32;
-    for (int r = warp; r < kTcBM; r += nwarps) {
-      const int grow = job.m0 + r;
-      if (grow >= M) break;  // uniform across the warp
-      const int rhs = grow / nz, p = grow - rhs * nz;
-      TS *srow = S + rhs * E + c.x_off + (int64_t)p * nr + job.n0;
-      const float *g = gamma + c.g_off + (int64_t)p * nn;
-      for (int ci = 4 * lane; ci < n_valid; ci += 128) {
-        const float4 v = *reinterpret_cast<const float4 *>(ct + r * kTcLdt + ci);
-        const int r0 = job.n0 + ci;
-        const float a0 = g[r0 % nn] * v.x, a1 = g[(r0 + 1) % nn] * v.y;
-        const float a2 = g[(r0 + 2) % nn] * v.z, a3 = g[(r0 + 3) % nn] * v.w;
-        if (sizeof(TS) == 4) {
-          *reinterpret_cast<float4 *>(srow + ci) = make_float4(a0, a1, a2, a3);
-        } else {
-          reinterpret_cast<double2 *>(srow + ci)[0] = make_double2(a0, a1);
-          reinterpret_cast<double2 *>(srow + ci)[1] = make_double2(a2, a3);
-        }
-      }
-    }
-  } else {
-    if (tid == 0) {
-      atomicOr(err, 1);
-      // B copies issued but never consumed may still be landing: wait (bounded)
-      for (int kc = committed; kc < b_issued; ++kc) mbar_wait(&bar_b[kc % kTcStages], (kc / kTcStages) & 1);
-    }
-    __syncthreads();
-  }
+  if (tid == 0 && abort_flag) atomicOr(err, 1);
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcBN) : "memory");
+  if (warp == 1)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kTcBN) : "memory");
 }
 
 // ------------------------------------------------------------ host side
@@ -323,38 +341,79 @@ void tc_build_tiles(const std::vector<ColDev> &cols, const std::vector<double> &
   }
 }
 
-void tc_build_jobs(const std::vector<ColDev> &cols, int n_rhs, std::vector<TcJob> &jobs) {
+// Tiles of 128 stacked (rhs, point) rows x 256 rays; the tail tile of a
+// column is zero-filled by TMA.
+void tc_build_jobs(const std::vector<ColDev> &cols, int n_rhs, std::vector<TcJob2> &jobs) {
   jobs.clear();
   for (size_t ci = 0; ci < cols.size(); ++ci) {
     const ColDev &c = cols[ci];
     if (c.psi_off < 0 || c.nr % 16) continue;
-    const int M = n_rhs * c.nz;
-    for (int m0 = 0; m0 < M; m0 += kTcBM)
-      for (int n0 = 0; n0 < c.nr; n0 += kTcBN) jobs.push_back(TcJob{(int32_t)ci, m0, n0, 0});
+    for (int m0 = 0; m0 < n_rhs * c.nz; m0 += kTcBM)
+      for (int n0 = 0; n0 < c.nr; n0 += kTcBN) jobs.push_back(TcJob2{(int32_t)ci, m0, n0, 0});
   }
 }
 
-// Builds the bf16 tiles and the job list of the tensor-core Sigma (mixed
-// precision handles with dense columns).  Returns a cudaError_t as int.
+// TMA maps over the bf16 copy of X, one per dense column: dims (q, row) =
+// (nr, n_rhs * nz), row stride nr elements, box 8 q x 128 rows (rows and q
+// past the column are zero-filled by the copy).
+static int tc_build_maps(rt_handle *h, std::vector<CUtensorMap> &maps) {
+  using EncodeFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+  static EncodeFn encode = nullptr;
+  if (!encode) {
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) return (int)cudaErrorNotSupported;
+    encode = reinterpret_cast<EncodeFn>(fn);
+  }
+  maps.assign(h->h_cols.size(), CUtensorMap{});
+  for (size_t ci = 0; ci < h->h_cols.size(); ++ci) {
+    const ColDev &c = h->h_cols[ci];
+    if (c.psi_off < 0 || c.nr % 16) continue;
+    const uint16_t *base = reinterpret_cast<const uint16_t *>(h->d_tc_xb) + (int64_t)h->n_rhs * c.x_off;
+    const cuuint64_t dims[2] = {(cuuint64_t)c.nr, (cuuint64_t)h->n_rhs * c.nz};
+    const cuuint64_t strides[1] = {(cuuint64_t)c.nr * 2};
+    const cuuint32_t box[2] = {8, (cuuint32_t)kTcBM};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = encode(&maps[ci], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<uint16_t *>(base), dims,
+                              strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return (int)cudaErrorInvalidValue;
+  }
+  return 0;
+}
+
+// Builds the bf16 B tiles, the job list and the TMA maps of the tensor-core
+// Sigma (mixed precision handles with dense columns).  Returns a cudaError_t.
 int tc_prepare(rt_handle *h, const std::vector<double> &psiwT) {
   std::vector<uint16_t> tiles;
   std::vector<int64_t> offs;
-  std::vector<TcJob> jobs;
+  std::vector<TcJob2> jobs;
   tc_build_tiles(h->h_cols, psiwT, tiles, offs);
   tc_build_jobs(h->h_cols, h->n_rhs, jobs);
-  // 16-byte cp.async of bf16 rows needs every row start on 8 elements
+  // 16-byte vector accesses of the epilogue need x_off and E multiples of 8
   bool aligned = h->E % 8 == 0;
   for (const ColDev &c : h->h_cols) aligned = aligned && c.x_off % 8 == 0;
   h->n_tc_jobs = aligned ? (int)jobs.size() : 0;
   if (h->n_tc_jobs == 0) return 0;
   cudaError_t ex = cudaMalloc(&h->d_tc_xb, (size_t)h->E * h->n_rhs * 2);
   if (ex != cudaSuccess) return (int)ex;
+  std::vector<CUtensorMap> maps;
+  if (tc_build_maps(h, maps) != 0) {
+    h->n_tc_jobs = 0;  // no TMA encoder: the CUDA-core Sigma handles the dense columns
+    return 0;
+  }
   cudaError_t e = cudaMalloc(&h->d_tc_tiles, tiles.size() * 2);
   if (e == cudaSuccess) e = cudaMemcpy(h->d_tc_tiles, tiles.data(), tiles.size() * 2, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMalloc(&h->d_tc_off, offs.size() * 8);
   if (e == cudaSuccess) e = cudaMemcpy(h->d_tc_off, offs.data(), offs.size() * 8, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMalloc(&h->d_tc_jobs, jobs.size() * sizeof(TcJob));
-  if (e == cudaSuccess) e = cudaMemcpy(h->d_tc_jobs, jobs.data(), jobs.size() * sizeof(TcJob), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMalloc(&h->d_tc_jobs, jobs.size() * sizeof(TcJob2));
+  if (e == cudaSuccess) e = cudaMemcpy(h->d_tc_jobs, jobs.data(), jobs.size() * sizeof(TcJob2), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMalloc(&h->d_tc_maps, maps.size() * sizeof(CUtensorMap));
+  if (e == cudaSuccess)
+    e = cudaMemcpy(h->d_tc_maps, maps.data(), maps.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice);
   return (int)e;
 }
 
@@ -365,22 +424,28 @@ int launch_sigma_dense_tc(rt_handle *h, bool x_is_float, const void *x, void *S,
   if (h->n_tc_jobs == 0) return 0;
   static bool attr_set = false;
   if (!attr_set) {
-    cudaFuncSetAttribute(k_sigma_dense_tc<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
-    cudaFuncSetAttribute(k_sigma_dense_tc<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
+    cudaFuncSetAttribute(k_sigma_dense_tc<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, kT2Smem);
+    cudaFuncSetAttribute(k_sigma_dense_tc<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, kT2Smem);
     attr_set = true;
   }
-  const int64_t n2 = h->E * h->n_rhs / 2;
-  const int g = (int)std::min<int64_t>((n2 + 255) / 256, 32 * 152);
-  if (x_is_float) k_to_bf16<float><<<g, 256, 0, s>>>(static_cast<const float *>(x), h->d_tc_xb, n2);
-  else k_to_bf16<double><<<g, 256, 0, s>>>(static_cast<const double *>(x), h->d_tc_xb, n2);
-  const TcJob *jobs = static_cast<const TcJob *>(h->d_tc_jobs);
-  const uint16_t *xb = reinterpret_cast<const uint16_t *>(h->d_tc_xb);
-  if (s_is_double)
-    k_sigma_dense_tc<double><<<h->n_tc_jobs, kTcThreads, kTcSmem, s>>>(
-        h->d_cols, jobs, h->d_tc_off, h->d_tc_tiles, h->gam32, h->n_rhs, h->E, xb, static_cast<double *>(S), h->d_err);
+  int64_t most = 1;
+  for (const ColDev &c : h->h_cols) most = std::max<int64_t>(most, (int64_t)c.nz * c.nr / 2);
+  const dim3 pg((unsigned)std::min<int64_t>((most + 255) / 256, 64), (unsigned)h->n_cols, (unsigned)h->n_rhs);
+  if (x_is_float)
+    k_to_bf16<float><<<pg, 256, 0, s>>>(h->d_cols, static_cast<const float *>(x), h->d_tc_xb, h->E, h->n_rhs);
   else
-    k_sigma_dense_tc<float><<<h->n_tc_jobs, kTcThreads, kTcSmem, s>>>(
-        h->d_cols, jobs, h->d_tc_off, h->d_tc_tiles, h->gam32, h->n_rhs, h->E, xb, static_cast<float *>(S), h->d_err);
+    k_to_bf16<double><<<pg, 256, 0, s>>>(h->d_cols, static_cast<const double *>(x), h->d_tc_xb, h->E, h->n_rhs);
+  const TcJob2 *jobs = static_cast<const TcJob2 *>(h->d_tc_jobs);
+  const CUtensorMap *maps = static_cast<const CUtensorMap *>(h->d_tc_maps);
+  const int ctas = std::min(h->n_tc_jobs, h->n_sm > 0 ? h->n_sm : 152);
+  if (s_is_double)
+    k_sigma_dense_tc<double><<<ctas, kT2Threads, kT2Smem, s>>>(maps, jobs, h->n_tc_jobs, h->d_cols, h->d_tc_off,
+                                                               h->d_tc_tiles, h->gam32, h->E, h->n_rhs,
+                                                               static_cast<double *>(S), h->d_err);
+  else
+    k_sigma_dense_tc<float><<<ctas, kT2Threads, kT2Smem, s>>>(maps, jobs, h->n_tc_jobs, h->d_cols, h->d_tc_off,
+                                                              h->d_tc_tiles, h->gam32, h->E, h->n_rhs,
+                                                              static_cast<float *>(S), h->d_err);
   return (int)cudaGetLastError();
 }
 
