@@ -48,6 +48,16 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
          ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
 }
 
+// K-major operand in the 128-byte swizzled layout written by a TMA box of 64
+// bf16 x rows (each row 128 bytes, 16-byte chunks permuted within 8-row
+// 1024-byte atoms): stride between 8-row groups 1024 bytes, layout type
+// 128B swizzle (bits 61-63 = 2); a K step of 16 inside the row advances the
+// start address by 32 bytes.  The tile must start on a 1024-byte boundary.
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr) {
+  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)(16u >> 4) << 16) | ((uint64_t)(1024u >> 4) << 32) |
+         (1ull << 46) | (2ull << 61);
+}
+
 // Instruction descriptor, kind::f16: bf16 x bf16 -> f32, both K-major.
 __host__ __device__ constexpr uint32_t tc_idesc(int m, int n) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
@@ -200,9 +210,7 @@ __global__ void __launch_bounds__(kT2Threads, 1)
           const int st = (int)(g % kT2Stages);
           if (g >= kT2Stages && !tc_wait(&empty[st], (uint32_t)((g / kT2Stages - 1) & 1), &abort_flag)) break;
           mbar_expect_tx(&full[st], kT2StageBytes);
-#pragma unroll
-          for (int kq = 0; kq < 8; ++kq)  // 8 q x 128 rows per box: one K-group of core matrices
-            tma_load_2d(sA(st) + kq * (kTcBM / 8) * 128, map, kc * kTcBK + kq * 8, J.m0, &full[st]);
+          tma_load_2d(sA(st), map, kc * kTcBK, J.m0, &full[st]);  // 64 q x 128 rows, 128-byte swizzle
           bulk_g2s(sB(st), Bcol + (int64_t)kc * (kTcBN * kTcBK), kTcBBytes, &full[st]);
         }
       }
@@ -233,7 +241,7 @@ __global__ void __launch_bounds__(kT2Threads, 1)
 #pragma unroll
           for (int ks = 0; ks < 4; ++ks)
             if (kc * 4 + ks < nk) {
-              const uint64_t ad = smem_desc(a0 + ks * 2 * (kTcBM / 8) * 128, (kTcBM / 8) * 128, 128);
+              const uint64_t ad = smem_desc_sw128(a0 + ks * 32);
               const uint64_t bd = smem_desc(b0 + ks * 2 * (kTcBN / 8) * 128, (kTcBN / 8) * 128, 128);
               tc_mma(dt, ad, bd, idesc, (kc | ks) ? 1u : 0u);
             }
@@ -375,10 +383,10 @@ static int tc_build_maps(rt_handle *h, std::vector<CUtensorMap> &maps) {
     const uint16_t *base = reinterpret_cast<const uint16_t *>(h->d_tc_xb) + (int64_t)h->n_rhs * c.x_off;
     const cuuint64_t dims[2] = {(cuuint64_t)c.nr, (cuuint64_t)h->n_rhs * c.nz};
     const cuuint64_t strides[1] = {(cuuint64_t)c.nr * 2};
-    const cuuint32_t box[2] = {8, (cuuint32_t)kTcBM};
+    const cuuint32_t box[2] = {(cuuint32_t)kTcBK, (cuuint32_t)kTcBM};
     const cuuint32_t estr[2] = {1, 1};
     const CUresult r = encode(&maps[ci], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<uint16_t *>(base), dims,
-                              strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                              strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                               CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return (int)cudaErrorInvalidValue;
   }
