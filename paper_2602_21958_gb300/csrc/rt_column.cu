@@ -1,11 +1,16 @@
 // rt_column.cu -- kernels for batches of 1D columns (Sec. 3.1-3.3):
-//   k_coefficients : per-layer step coefficients in float64 (exp / expm1)
-//   k_solve        : persistent per-instance solver: float64 iterative
-//                    refinement around GMRES(m) (CGS2 Arnoldi, Givens rotations)
+//   k_coefficients    : per-layer step coefficients in float64 (SC-L, implicit
+//                       Euler, quadratic SC), with float32 copies
+//   k_solve<double>   : float64 restarted GMRES(m) per (column, rhs) instance
+//                       (classical Gram-Schmidt with DGKS, Givens rotations)
+//   k_solve_nested    : mixed precision: float64 flexible GMRES whose
+//                       directions come from float32 GMRES cycles on a
+//                       binary16 basis
+//   k_solve_bicgstab  : float64 BiCGStab per instance
 //
-// Every kernel walks a work queue of (column, rhs) instances with one CTA per
-// instance at a time; all synchronisation is inside the CTA, no CTA ever waits
-// for another.
+// Every solve kernel walks a work queue of (column, rhs) instances with one
+// CTA per instance at a time; all synchronisation is inside the CTA, no CTA
+// ever waits for another.
 #include <algorithm>
 
 #include <cuda_runtime.h>

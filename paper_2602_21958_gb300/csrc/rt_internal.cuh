@@ -12,7 +12,6 @@
 
 namespace rt {
 
-constexpr int kMaxRank = 16;   // largest rank of the angular factor kept in registers
 constexpr int kSigBuf = 2048;  // elements of each shared buffer of the Sigma stage
 
 // Per-column metadata (device resident, one entry per column).
