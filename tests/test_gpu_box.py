@@ -112,3 +112,11 @@ def test_c3_physics_reduced_grid(rt):
     torch.cuda.synchronize()
     assert info["status"] == 0, info
     assert rel(x.cpu().numpy(), xref) < 1e-10
+
+
+def test_quadratic_formal_solver_is_rejected_for_boxes(rt):
+    # quadratic short characteristics are built for 1D columns only
+    p = dataclasses.replace(small_box(), formal_solver=W.FS_QSC)
+    with pytest.raises(rt.RTError) as e:
+        rt.Handle(p)
+    assert e.value.code == rt.RT_ERR_ARG
