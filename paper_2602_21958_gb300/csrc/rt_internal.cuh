@@ -347,7 +347,8 @@ __device__ __noinline__ void sigma_column(const ColDev &c, const Tables<T> &tb, 
 enum SweepOut : int {
   kOutAminus = 0,  // y = x - I            (A x with I = Lambda Sigma x)
   kOutI = 1,       // y = I                (Lambda S, or the right-hand side)
-  kOutResid = 2    // y = b - x + I        (b - A x), returns the squared norm
+  kOutResid = 2,   // y = b - x + I        (b - A x), returns the squared norm
+  kOutAminusB = 3  // y = x - I - b        (A x - b: a direction minus a known vector)
 };
 
 // Formal solution along every ray of one column (eqs. ie_1, ie_2 with the
@@ -387,6 +388,8 @@ __device__ double sweep_ray(const ColDev &c, const Tables<T> &tb, const Common &
       const double v = bv[k] - as_f64(xi) + (double)I;
       y[k] = (TY)v;
       ss += v * v;
+    } else if (out == kOutAminusB) {
+      y[k] = (TY)(as_f64(xi) - (double)I - bv[k]);
     } else if (out == kOutI) {
       y[k] = (TY)I;
     } else if (sizeof(TY) == 4 && sizeof(TX) <= 4) {
