@@ -311,6 +311,41 @@ def tensor_roofline(rank: int = 0) -> dict:
             "peak_source": peak[1], "workload": "C5 physics as dense Psi, 256 columns x 4 rhs, bf16 in / fp32 acc"}
 
 
+def sweep_roofline(rank: int = 0) -> dict:
+    """The Lambda sweep on its own: rt_apply(RT_OP_LAMBDA) on the C5 batch, 4 rhs,
+    mixed handle = k_convert (x float64 -> S float32) + k_sweep_tiles (float32
+    recurrence, I written in float64).  Algorithmic bytes per dof: convert
+    reads x (8) and writes S (4), the sweep reads S (4) and writes y (8): 24.
+    CUDA events on the launching stream over repeated applies."""
+    import torch
+
+    from paper_2602_21958_gb300 import rt
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    h = rt.Handle(workload(rank), n_rhs=N_RHS, precision=rt.RT_P_MIXED, max_restart=2)
+    x = torch.randn(h.length, dtype=torch.float64, device=dev)
+    y = torch.empty_like(x)
+    stream = torch.cuda.current_stream()
+    for _ in range(3):
+        h.rt_apply(rt.RT_OP_LAMBDA, x, y)
+    torch.cuda.synchronize()
+    k = 10
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(k):
+        h.rt_apply(rt.RT_OP_LAMBDA, x, y)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / k
+    peaks = load_peaks()
+    nbytes = 24.0 * h.length
+    gbs = nbytes / (ms * 1e-3) / 1e9
+    h.close()
+    return {"bound": "hbm", "kernel": "k_convert + k_sweep_tiles (Lambda x)", "achieved": gbs, "peak": peaks[0],
+            "unit": "GB/s", "frac": gbs / peaks[0], "traffic": None, "ms_per_apply": ms,
+            "bytes_per_apply": nbytes, "peak_source": peaks[1]}
+
+
 def configs_sweep(rank: int = 0) -> dict:
     """Per-configuration figures for the other workloads: C1 and C2 (one 1D
     column), C3 (3D box 32^3), C4 (3D box 64^3).  Apply latency in both
@@ -556,6 +591,7 @@ def main():
         cb = cpu_baseline(n_inst, cores=os.cpu_count(), keep_solutions=True)
     res = run_ours(args, rank, world)
     tensor = tensor_roofline(rank) if rank == 0 else None
+    sweep = sweep_roofline(rank) if rank == 0 else None
     per_config = configs_sweep(rank) if rank == 0 else None
     spectral = spectral_sweep(rank) if rank == 0 else None
     if rank != 0:
@@ -587,6 +623,7 @@ def main():
         "gpu_launches": args.steps,
         "roofline": res["roofline"],
         "roofline_tensor": tensor,
+        "roofline_sweep": sweep,
         "configs": per_config,
         "spectral": spectral,
         "clocks": res["clk"],
