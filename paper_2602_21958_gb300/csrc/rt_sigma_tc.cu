@@ -430,12 +430,11 @@ int tc_prepare(rt_handle *h, const std::vector<double> &psiwT) {
 int launch_sigma_dense_tc(rt_handle *h, bool x_is_float, const void *x, void *S, bool s_is_double,
                           cudaStream_t s) {
   if (h->n_tc_jobs == 0) return 0;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(k_sigma_dense_tc<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, kT2Smem);
-    cudaFuncSetAttribute(k_sigma_dense_tc<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, kT2Smem);
-    attr_set = true;
-  }
+  // the shared-memory opt-in belongs to the current device's context: set it
+  // on every launch (a host-side call), not once per process
+  const void *kern = s_is_double ? (const void *)k_sigma_dense_tc<double> : (const void *)k_sigma_dense_tc<float>;
+  cudaError_t ae = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kT2Smem);
+  if (ae != cudaSuccess) return (int)ae;
   int64_t most = 1;
   for (const ColDev &c : h->h_cols) most = std::max<int64_t>(most, (int64_t)c.nz * c.nr / 2);
   const dim3 pg((unsigned)std::min<int64_t>((most + 255) / 256, 64), (unsigned)h->n_cols, (unsigned)h->n_rhs);
