@@ -41,6 +41,42 @@ def test_scl_constant_source_closed_form():
     assert np.abs(I[:, ~down] - 2.5 * (1 - np.exp(-tau_up[:, ~down]))).max() < 1e-14 * 2.5
 
 
+@pytest.mark.parametrize("c", [0.0, 0.37])
+def test_pure_absorption_rhs_closed_form(c):
+    """eps = 1 (no scattering): A = Id and I = b = Lambda t + I_in. With
+    B = a + c t, constant chi = phi(nu), zero inflow at the top and B(t_N) at
+    the bottom, the formal-solution integral has a closed form along each ray;
+    SC-L integrates a source linear in optical depth exactly, so the oracle
+    must reproduce it to rounding. c = 0 is the textbook B (1 - e^{-tau/|mu|}).
+    Separates the upwind and current-point weights of the linear step (a
+    constant source only sees their sum)."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 40
+    a = 1.3
+    t = np.logspace(-3, np.log10(30.0), 48)
+    p = W.two_level_column(t, 4, 1, 9, "crd", 1.0, a + c * t)
+    I = O.rhs(p).reshape(p.nz, p.n_dir, p.n_nu)
+    A = O.assemble_A(dataclasses.replace(p, nz=6, z=t[:6], chi=p.chi[:6], gamma=p.gamma[:6],
+                                         t_src=p.t_src[:6]))
+    assert np.array_equal(A, np.eye(A.shape[0]))
+    phi = p.chi[0]
+    ref = np.empty_like(I)
+    for d, mu in enumerate(p.mu):
+        for f in range(p.n_nu):
+            k = mp.mpf(c) * abs(mu) / mp.mpf(phi[f])   # dS/d(optical depth along the ray)
+            for i, ti in enumerate(t):
+                S = mp.mpf(a) + mp.mpf(c) * mp.mpf(ti)
+                if mu < 0:   # from the surface down: S falls towards the upwind end
+                    D = mp.mpf(phi[f]) * (mp.mpf(ti) - mp.mpf(t[0])) / abs(mu)
+                    v = S * (1 - mp.exp(-D)) - k * (1 - (1 + D) * mp.exp(-D))
+                else:        # from the bottom up, entering with B(t_N)
+                    D = mp.mpf(phi[f]) * (mp.mpf(t[-1]) - mp.mpf(ti)) / abs(mu)
+                    v = (mp.mpf(a) + mp.mpf(c) * mp.mpf(t[-1])) * mp.exp(-D) \
+                        + S * (1 - mp.exp(-D)) + k * (1 - (1 + D) * mp.exp(-D))
+                ref[i, d, f] = float(v)
+    assert np.abs(I - ref).max() <= 1e-13 * np.abs(ref).max()
+
+
 def test_scl_inflow_equal_to_source_is_invariant():
     p = W.config_c1()
     I = O.lambda_1d(p, np.ones(p.n), with_inflow=True).reshape(p.nz, p.n_dir, p.n_nu)
