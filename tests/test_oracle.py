@@ -41,40 +41,65 @@ def test_scl_constant_source_closed_form():
     assert np.abs(I[:, ~down] - 2.5 * (1 - np.exp(-tau_up[:, ~down]))).max() < 1e-14 * 2.5
 
 
-@pytest.mark.parametrize("c", [0.0, 0.37])
-def test_pure_absorption_rhs_closed_form(c):
+@pytest.mark.parametrize("fs,c,q", [(W.FS_SCL, 0.0, 0.0), (W.FS_SCL, 0.37, 0.0),
+                                    (W.FS_QSC, 0.37, 0.0), (W.FS_QSC, 0.37, 0.011)])
+def test_pure_absorption_rhs_closed_form(fs, c, q):
     """eps = 1 (no scattering): A = Id and I = b = Lambda t + I_in. With
-    B = a + c t, constant chi = phi(nu), zero inflow at the top and B(t_N) at
-    the bottom, the formal-solution integral has a closed form along each ray;
-    SC-L integrates a source linear in optical depth exactly, so the oracle
-    must reproduce it to rounding. c = 0 is the textbook B (1 - e^{-tau/|mu|}).
-    Separates the upwind and current-point weights of the linear step (a
-    constant source only sees their sum)."""
+    B = a + c t + q t^2, constant chi = phi(nu), zero inflow at the top and
+    B(t_N) at the bottom, the formal-solution integral along each ray has a
+    closed form (evaluated here in 40-digit arithmetic). SC-L integrates a
+    source linear in optical depth exactly and QSC a quadratic one, except on
+    the last step of a ray, which is linear. c = q = 0 is the textbook
+    B (1 - e^{-tau/|mu|}). Separates the upwind, current and downwind weights
+    of a step (a constant source only sees their sum) and checks both sweep
+    senses."""
     mp = pytest.importorskip("mpmath")
     mp.mp.dps = 40
     a = 1.3
     t = np.logspace(-3, np.log10(30.0), 48)
-    p = W.two_level_column(t, 4, 1, 9, "crd", 1.0, a + c * t)
+    p = W.two_level_column(t, 4, 1, 9, "crd", 1.0, a + c * t + q * t * t, formal_solver=fs)
     I = O.rhs(p).reshape(p.nz, p.n_dir, p.n_nu)
-    A = O.assemble_A(dataclasses.replace(p, nz=6, z=t[:6], chi=p.chi[:6], gamma=p.gamma[:6],
-                                         t_src=p.t_src[:6]))
-    assert np.array_equal(A, np.eye(A.shape[0]))
-    phi = p.chi[0]
+    small = dataclasses.replace(p, nz=6, z=t[:6], chi=p.chi[:6], gamma=p.gamma[:6], t_src=p.t_src[:6])
+    assert np.array_equal(O.assemble_A(small), np.eye(small.n))
+    B = lambda x: mp.mpf(a) + mp.mpf(c) * x + mp.mpf(q) * x * x
     ref = np.empty_like(I)
     for d, mu in enumerate(p.mu):
+        sg = -1 if mu < 0 else 1            # t along the ray back from a point: t + sg s h
         for f in range(p.n_nu):
-            k = mp.mpf(c) * abs(mu) / mp.mpf(phi[f])   # dS/d(optical depth along the ray)
+            h = abs(mu) / mp.mpf(p.chi[0, f])       # depth per unit optical depth along the ray
             for i, ti in enumerate(t):
-                S = mp.mpf(a) + mp.mpf(c) * mp.mpf(ti)
-                if mu < 0:   # from the surface down: S falls towards the upwind end
-                    D = mp.mpf(phi[f]) * (mp.mpf(ti) - mp.mpf(t[0])) / abs(mu)
-                    v = S * (1 - mp.exp(-D)) - k * (1 - (1 + D) * mp.exp(-D))
-                else:        # from the bottom up, entering with B(t_N)
-                    D = mp.mpf(phi[f]) * (mp.mpf(t[-1]) - mp.mpf(ti)) / abs(mu)
-                    v = (mp.mpf(a) + mp.mpf(c) * mp.mpf(t[-1])) * mp.exp(-D) \
-                        + S * (1 - mp.exp(-D)) + k * (1 - (1 + D) * mp.exp(-D))
-                ref[i, d, f] = float(v)
-    assert np.abs(I - ref).max() <= 1e-13 * np.abs(ref).max()
+                x = mp.mpf(ti)
+                # S(t + sg s h) = s0 + s1 s + s2 s^2 in the ray's optical depth s
+                s0, s1, s2 = B(x), sg * h * (mp.mpf(c) + 2 * mp.mpf(q) * x), mp.mpf(q) * h * h
+                D = (x - mp.mpf(t[0])) / h if mu < 0 else (mp.mpf(t[-1]) - x) / h
+                ed = mp.exp(-D)
+                g0, g1, g2 = 1 - ed, 1 - (1 + D) * ed, 2 - (2 + 2 * D + D * D) * ed
+                inflow = 0 if mu < 0 else B(mp.mpf(t[-1]))
+                ref[i, d, f] = float(inflow * ed + s0 * g0 + s1 * g1 + s2 * g2)
+    exact = np.ones(I.shape, dtype=bool)
+    if q != 0.0:                            # linear last step of each QSC ray
+        exact[-1, p.mu < 0] = False
+        exact[0, p.mu > 0] = False
+    assert np.abs(I - ref)[exact].max() <= 1e-13 * np.abs(ref).max()
+    assert np.abs(I - ref)[~exact].max(initial=0.0) <= 1e-2 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("fs", [W.FS_SCL, W.FS_QSC])
+def test_depth_dependent_opacity_constant_source(fs):
+    """chi linear in depth: the optical depth of a step is the exact integral
+    of chi (trapezoid rule exact), so a constant source with no inflow gives
+    I = B (1 - e^{-tau/|mu|}), tau measured from the ray's entry point."""
+    z = np.linspace(0.0, 6.0, 31) ** 1.5
+    p = W.two_level_column(z, 4, 1, 5, "crd", 1.0, 1.0, formal_solver=fs)
+    c0, c1 = 0.2, 0.9
+    p = dataclasses.replace(p, chi=p.chi * (c0 + c1 * z)[:, None])
+    B = 0.8
+    I = O.lambda_op(p, np.full(p.n, B)).reshape(p.nz, p.n_dir, p.n_nu)
+    col = c0 * z + 0.5 * c1 * z * z                     # int_0^z (c0 + c1 z') dz'
+    phi = p.chi[0] / c0
+    for d, mu in enumerate(p.mu):
+        tau = (col if mu < 0 else col[-1] - col)[:, None] * phi[None, :] / abs(mu)
+        assert np.abs(I[:, d] - B * -np.expm1(-tau)).max() <= 1e-14
 
 
 def test_scl_inflow_equal_to_source_is_invariant():
@@ -197,6 +222,18 @@ def test_sigma_matches_assembled_block_diagonal():
     assert np.allclose(O.sigma_matrix(q) @ x, O.sigma_op(q, x), rtol=1e-14, atol=1e-14)
 
 
+def test_dense_kernel_equals_separable_kernel():
+    """Psi = P (x) R (the dense form, eq. Sigma) must give the factored
+    contraction's result, with non-uniform direction and frequency weights
+    (dipole x R_II-A, two azimuths)."""
+    q = W.two_level_column(np.logspace(-2, 2, 3), 4, 2, 6, "r2", 1e-2, 1.0)
+    dq = q.with_dense_kernel()
+    x = np.random.default_rng(2).standard_normal(q.n)
+    ref = O.sigma_op(q, x)
+    assert np.abs(O.sigma_op(dq, x) - ref).max() <= 1e-14 * np.abs(ref).max()
+    assert np.abs(O.sigma_matrix(dq) @ x - ref).max() <= 1e-14 * np.abs(ref).max()
+
+
 def test_crd_reduces_to_mean_intensity():
     """Isotropic CRD: S = (1 - eps) Jbar + eps B, Jbar = sum w w phi I."""
     p = W.config_c1()
@@ -258,6 +295,36 @@ def test_bicgstab_on_a_multiple_of_identity_takes_one_half_step():
     r = O.bicgstab(lambda v: 2.5 * v, b, tol=1e-14)
     assert r.iterations == 1
     assert np.allclose(r.x, b / 2.5, rtol=0, atol=1e-15)
+
+
+def test_bicgstab_terminates_after_as_many_iterations_as_distinct_eigenvalues():
+    """The BiCG polynomial of BiCGStab annihilates r0 once its degree reaches
+    that of the minimal polynomial of A with respect to r0: a diagonalisable
+    non-normal A with 3 distinct eigenvalues is solved in at most 3
+    iterations (any error in the direction recurrence loses this)."""
+    rng = np.random.default_rng(9)
+    n = 40
+    lam = np.repeat([1.0, 2.0, 3.5], [15, 15, 10])
+    X = np.eye(n) + 0.2 * rng.standard_normal((n, n)) / np.sqrt(n)
+    A = X @ np.diag(lam) @ np.linalg.inv(X)
+    b = rng.standard_normal(n)
+    r = O.bicgstab(lambda v: A @ v, b, tol=1e-11)
+    assert r.iterations <= 3 and r.relres <= 1e-11
+
+
+def test_bicgstab_first_iteration_is_galerkin_then_minimal_residual():
+    """x0 = 0: the first iterate is x1 = alpha b + omega s with s = b - alpha A b,
+    alpha fixed by the Petrov-Galerkin condition (b, s) = 0 and omega by the
+    least-squares problem min ||s - omega A s|| (solved here by lstsq)."""
+    rng = np.random.default_rng(10)
+    A = np.eye(25) + 0.4 * rng.standard_normal((25, 25)) / 5.0
+    b = rng.standard_normal(25)
+    x1 = O.bicgstab(lambda v: A @ v, b, tol=1e-300, max_iter=1).x
+    # alpha: the root of (b, b - alpha A b) = 0, found by lstsq on the 1x1 system
+    alpha = np.linalg.lstsq((b @ A @ b).reshape(1, 1), np.array([b @ b]), rcond=None)[0][0]
+    s = b - alpha * (A @ b)
+    omega = np.linalg.lstsq((A @ s).reshape(-1, 1), s, rcond=None)[0][0]
+    assert np.abs(x1 - (alpha * b + omega * s)).max() <= 1e-13 * np.abs(x1).max()
 
 
 def test_lu_equals_bicgstab():
@@ -350,6 +417,17 @@ def test_iso_crd_cluster_and_lower_bound(n_s, n_nu):
     assert lmin_c > GOLDEN["table_iso"]["abs_lambda_min_gt"]
 
 
+def test_cluster_fraction_counts_the_band():
+    """|lambda| in [0.999, 1 + 1e-12] (Tables mono and iso), on a non-normal
+    matrix with known eigenvalues: 0.9995 and 1 count; 1.0005, 1.5, 0.5 do not."""
+    rng = np.random.default_rng(11)
+    lam = np.array([0.9995, 1.0, 1.0005, 1.5, 0.5, 1.0, 0.9985, 0.9991])
+    X = np.eye(8) + 0.1 * rng.standard_normal((8, 8))
+    frac, lmin = O.cluster_fraction(X @ np.diag(lam) @ np.linalg.inv(X))
+    assert frac == 4 / 8
+    assert abs(lmin - 0.5) < 1e-12
+
+
 def test_cluster_fraction_grows_under_refinement():
     """Thm main4: the fraction in D(1, 1e-3) does not decrease as N_s, N_Omega grow."""
     f = [O.cluster_fraction(O.assemble_A(W.paper_mono(ns, 12)))[0] for ns in (10, 20, 40)]
@@ -436,6 +514,39 @@ def test_3d_half_offset_interpolates_two_cells():
             su = 0.5 * (Sg[1, (y - 1) % n, x] + Sg[1, y, x])
             ref = (1 - e - beta) * su + beta * Sg[0, y, x]
             assert abs(I[0, y, x] - ref) < 1e-14
+
+
+def test_3d_fractional_offset_bilinear_upwind_point():
+    """Upwind offset (0.3, 0.6) cells: I, S and chi at the upwind point are
+    the bilinear blends of the four surrounding cells of the upwind plane
+    (weights 0.7/0.3 in x, 0.4/0.6 in y), periodic in x and y."""
+    rng = np.random.default_rng(6)
+    n, nz = 5, 3
+    ox, oy, oz = 0.3, 0.6, -1.0                 # downward: upwind plane k-1
+    nrm = math.sqrt(ox * ox + oy * oy + oz * oz)
+    dirs = np.array([[ox / nrm, oy / nrm, oz / nrm]])
+    box = W.Problem(dims=3, nx=n, ny=n, nz=nz, z=np.array([1.0, 1.0, 1.0]), dirs=dirs,
+                    w_dir=np.ones(1), w_nu=np.ones(1), chi=rng.uniform(0.2, 2.0, (n * n * nz, 1)),
+                    gamma=np.zeros((n * n * nz, 1)), I_top=np.zeros(1), I_bot=np.zeros(1))
+    S = rng.standard_normal(box.n)
+    I = O.lambda_3d(box, S).reshape(nz, n, n)
+    Sg = S.reshape(nz, n, n)
+    chi = box.chi.reshape(nz, n, n)
+    ds = 1.0 / abs(dirs[0, 2])                  # path length between planes (dz = 1)
+
+    def upwind(F, y, x):                        # F at (x - 0.3, y - 0.6)
+        return (0.4 * (0.7 * F[y, x] + 0.3 * F[y, (x - 1) % n])
+                + 0.6 * (0.7 * F[(y - 1) % n, x] + 0.3 * F[(y - 1) % n, (x - 1) % n]))
+
+    for k in range(1, nz):
+        for y in range(n):
+            for x in range(n):
+                d = 0.5 * (upwind(chi[k - 1], y, x) + chi[k, y, x]) * ds
+                e = math.exp(-d)
+                beta = (d + math.expm1(-d)) / d
+                ref = (e * upwind(I[k - 1], y, x) + (1 - e - beta) * upwind(Sg[k - 1], y, x)
+                       + beta * Sg[k, y, x])
+                assert abs(I[k, y, x] - ref) < 1e-13
 
 
 def test_3d_constant_source_closed_form():
