@@ -89,3 +89,33 @@ def test_configs_shapes():
     assert all(64 <= c.nz <= 512 and 32 <= c.n_nu <= 128 and c.n_dir == 16 for c in cols)
     c3 = W.config_c3(n=8)
     assert c3.n == 8 ** 3 * 48 * 32
+
+
+def test_trapezoid_weights_exact_for_linear_functions_on_uneven_grids():
+    x = np.array([-2.0, -1.7, -0.2, 0.1, 1.5, 4.0])
+    w = W.trapezoid_weights(x)
+    assert abs(w.sum() - 6.0) < 1e-15                       # int 1 dx
+    assert abs(np.sum(w * x) - 0.5 * (16.0 - 4.0)) < 1e-14  # int x dx
+
+
+def test_mono_legendre_coefficients_are_the_printed_ones():
+    import json, os
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")))
+    assert list(W.MONO_LEGENDRE) == gold["mono_legendre"]["d"]
+
+
+def test_azimuth_averaged_dipole():
+    """1 + P2(mu) P2(mu') / 2 is the average over the azimuth difference of the
+    dipole phase 3/4 (1 + cos^2 Theta), cos Theta = mu mu' + s s' cos(dphi):
+    checked by an equispaced azimuth rule (exact for this degree-2 trig polynomial)."""
+    mu = np.array([-0.93, -0.4, 0.05, 0.61, 0.99])
+    s = np.sqrt(1 - mu * mu)
+    dphi = 2 * np.pi * np.arange(16) / 16
+    c = mu[:, None, None] * mu[None, :, None] + s[:, None, None] * s[None, :, None] * np.cos(dphi)
+    avg = np.mean(0.75 * (1 + c * c), axis=-1)
+    assert np.abs(W.dipole_azimuth_averaged(mu) - avg).max() < 1e-14
+    # the 3D dipole over the same direction pairs, averaged the same way
+    for i in range(len(mu)):
+        for j in range(len(mu)):
+            d = np.array([[s[i], 0.0, mu[i]]] + [[s[j] * np.cos(p), s[j] * np.sin(p), mu[j]] for p in dphi])
+            assert abs(np.mean(W.dipole_3d(d)[0, 1:]) - avg[i, j]) < 1e-14
