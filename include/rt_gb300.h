@@ -93,7 +93,7 @@ typedef struct rt_desc {
   const double *t_src;   /* [n_pts*n_nu] thermal term t = eps_t/chi, or NULL (= 0)    */
   const double *I_top;   /* [n_nu] inflow for mu < 0 at the top, or NULL (= 0)        */
   const double *I_bot;   /* [n_nu] inflow for mu > 0 at the bottom, or NULL (= 0)     */
-  int32_t formal_solver; /* RT_FS_SCL or RT_FS_IE                                     */
+  int32_t formal_solver; /* RT_FS_SCL, RT_FS_IE, or RT_FS_QSC (1D columns only)       */
 } rt_desc;
 
 /* ---- solve options and report ----------------------------------------- */

@@ -13,7 +13,7 @@ from typing import Optional, Sequence
 
 import numpy as np
 
-from .workloads import FS_IE, FS_QSC, Problem
+from .workloads import FS_IE, FS_QSC, FS_SCL, Problem
 
 _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "librt_gb300.so")
 
@@ -151,7 +151,10 @@ def make_desc(p: Problem, keep: list) -> rt_desc:
     d.n_dir, d.n_nu = p.n_dir, p.n_nu
     for k, v in arrs.items():
         setattr(d, k, v.ctypes.data_as(_dp) if v is not None else _dp())
-    d.formal_solver = {FS_IE: RT_FS_IE, FS_QSC: RT_FS_QSC}.get(p.formal_solver, RT_FS_SCL)
+    fs = {FS_SCL: RT_FS_SCL, FS_IE: RT_FS_IE, FS_QSC: RT_FS_QSC}.get(p.formal_solver)
+    if fs is None:
+        raise ValueError("unknown formal solver %r" % (p.formal_solver,))
+    d.formal_solver = fs
     return d
 
 

@@ -53,3 +53,30 @@ def test_missing_library_fails_loudly(tmp_path):
 
     with pytest.raises(RuntimeError):
         rt.load(str(tmp_path / "nope.so"))
+
+
+def test_descriptor_marshalling():
+    """rt_desc carries the Problem's sizes, formal solver and array addresses
+    (float64, C order); a missing optional array is NULL; an unknown formal
+    solver is refused before any call."""
+    import dataclasses
+
+    import numpy as np
+
+    from paper_2602_21958_gb300 import rt
+    from paper_2602_21958_gb300 import workloads as W
+
+    p = W.two_level_column(np.logspace(-2, 2, 7), 4, 2, 5, "r2", 1e-3, 1.0)
+    for fs, code in ((W.FS_SCL, rt.RT_FS_SCL), (W.FS_IE, rt.RT_FS_IE), (W.FS_QSC, rt.RT_FS_QSC)):
+        keep = []
+        d = rt.make_desc(dataclasses.replace(p, formal_solver=fs), keep)
+        assert (d.dims, d.nx, d.ny, d.nz, d.n_dir, d.n_nu) == (1, 1, 1, 7, 8, 5)
+        assert d.formal_solver == code
+        arrs = keep[0]
+        for name in ("z", "dir", "w_dir", "chi", "gamma", "P", "R", "t_src", "I_bot"):
+            a = arrs[name]
+            assert a.dtype == np.float64 and a.flags.c_contiguous
+            assert np.ctypeslib.as_array(getattr(d, name), shape=(a.size,)).tolist() == a.ravel().tolist()
+        assert not bool(d.Psi)
+    with pytest.raises(ValueError):
+        rt.make_desc(dataclasses.replace(p, formal_solver="sc-l"), [])
