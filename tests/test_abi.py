@@ -80,3 +80,22 @@ def test_descriptor_marshalling():
         assert not bool(d.Psi)
     with pytest.raises(ValueError):
         rt.make_desc(dataclasses.replace(p, formal_solver="sc-l"), [])
+
+
+def test_ritz_values_of_a_full_arnoldi_are_the_eigenvalues():
+    """Host half of rt_arnoldi: after n steps on an n x n matrix the square part
+    of the Hessenberg matrix carries the whole spectrum (here from the oracle's
+    Arnoldi on a non-normal matrix with known distinct eigenvalues)."""
+    import numpy as np
+
+    import oracle as O
+    from paper_2602_21958_gb300 import rt
+
+    rng = np.random.default_rng(12)
+    lam = np.array([0.75, 0.9, 0.99, 1.0, 1.2, 0.5, 0.999, 0.82])
+    X = np.eye(8) + 0.2 * rng.standard_normal((8, 8))
+    A = X @ np.diag(lam) @ np.linalg.inv(X)
+    H = O.arnoldi(lambda v: A @ v, rng.standard_normal(8), 8)
+    assert H.shape == (9, 8) or H.shape == (8, 8)
+    got = np.sort_complex(rt.ritz_values(H))
+    assert np.abs(got - np.sort(lam)).max() < 1e-10
