@@ -576,7 +576,7 @@ def main():
             steps.append(1.0 / cb["value"])
         val = 1.0 / statistics.mean(steps[args.warmup:])
         line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "batched solves/s",
-                "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": 1e3 / val, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config,
                 "cpu_baseline": {k: cb[k] for k in ("kind", "cores", "sample")} | {"value": val,
