@@ -279,6 +279,25 @@ def test_lu_equals_gmres():
     assert np.linalg.norm(g.x - x_lu) <= 1e-12 * np.linalg.norm(x_lu)
 
 
+def test_restarted_gmres_cycles_minimise_the_residual():
+    """Each GMRES(m) cycle returns the minimiser of ||b - A x|| over
+    x_prev + K_m(A, r_prev) (the method's definition): two cycles of m = 3
+    against least squares on explicit Krylov bases."""
+    rng = np.random.default_rng(13)
+    n, m = 30, 3
+    A = np.eye(n) + 0.5 * rng.standard_normal((n, n)) / np.sqrt(n)
+    b = rng.standard_normal(n)
+    x = np.zeros(n)
+    for _ in range(2):
+        r = b - A @ x
+        K = np.stack([np.linalg.matrix_power(A, k) @ r for k in range(m)], axis=1)
+        y = np.linalg.lstsq(A @ K, r, rcond=None)[0]
+        x = x + K @ y
+    got = O.gmres(lambda v: A @ v, b, tol=1e-300, restart=m, max_iter=2 * m)
+    assert got.restarts == 2 and got.iterations == 2 * m
+    assert np.abs(got.x - x).max() <= 1e-12 * np.abs(x).max()
+
+
 def test_bicgstab_solves_a_random_nonsymmetric_system():
     # library LU as the independent reference; a wrong beta/omega or sign stalls
     rng = np.random.default_rng(7)
