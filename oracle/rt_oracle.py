@@ -34,6 +34,7 @@ SERIES_CUT = 0.1
 # ------------------------------------------------------------ formal solvers
 def w1_over_dtau(d: np.ndarray) -> np.ndarray:
     """w1/dtau with w1 = dtau - (1 - e^-dtau) = int_0^dtau s e^-(dtau-s) ds / ...
+    (the linear-source weight of the SC-L step; Sec. 3.2 admits any formal solver).
 
     For dtau < 0.1 the alternating series sum_{k>=1} (-1)^(k+1) dtau^k/(k+1)!
     (16 terms) replaces the cancelling closed form.
@@ -74,7 +75,8 @@ def step_coefficients(dtau: np.ndarray, formal_solver: str):
 
 
 def qsc_moments(d: np.ndarray):
-    """W1 = int_0^d s e^-(d-s) ds = d - (1 - e^-d) and W2 = int_0^d s^2 e^-(d-s) ds
+    """Moments of the quadratic step (the quadratic integrator of Sec. 5.3, restated):
+    W1 = int_0^d s e^-(d-s) ds = d - (1 - e^-d) and W2 = int_0^d s^2 e^-(d-s) ds
     = d^2 - 2 W1, returned as W1/d^2 and W2/d^3.  Below d = 0.1 the cancelling
     closed forms are replaced by their series, W1/d^2 = sum_{k>=0} (-1)^k
     d^k/(k+2)! and W2/d^3 = 2 sum_{k>=0} (-1)^k d^k/(k+3)! (18 terms)."""
@@ -159,7 +161,8 @@ def lambda_1d(prob: Problem, S: np.ndarray, with_inflow: bool = False) -> np.nda
 
 
 def _lambda_1d_qsc(prob: Problem, S: np.ndarray, with_inflow: bool) -> np.ndarray:
-    """Quadratic short characteristics along every ray: each step uses the
+    """Quadratic short characteristics along every ray (Sec. 5.3 integrator,
+    recurrence of eqs. ie_1, ie_2 with a downwind term): each step uses the
     upwind, current and downwind points (qsc_coefficients); the last step of a
     ray, which has no downwind point, is the linear SC-L step."""
     nz = prob.nz
@@ -193,7 +196,8 @@ def _lambda_1d_qsc(prob: Problem, S: np.ndarray, with_inflow: bool) -> np.ndarra
 
 def lambda_matrix_1d(prob: Problem) -> np.ndarray:
     """Dense Lambda_N (N x N) assembled from the step recurrence, ray by ray,
-    in the space-based ordering (Lambda_N = P^T blockdiag(Lambda_[k]) P)."""
+    in the space-based ordering (Lambda_N = P^T blockdiag(Lambda_[k]) P;
+    Sec. 3.2, eq. lambda_block)."""
     nz, nd, nn = prob.nz, prob.n_dir, prob.n_nu
     N = prob.n
     if prob.formal_solver == FS_QSC:  # columns of the matrix-free operator
@@ -245,7 +249,8 @@ def lambda_ie_closed_form(prob: Problem) -> np.ndarray:
 # ---------------------------------------------------------------- 3D transfer
 def _bilinear_periodic(F: np.ndarray, sx: float, sy: float) -> np.ndarray:
     """Value of the periodic plane field F[..., ny, nx] at (x - sx, y - sy) for
-    every cell (x, y), by bilinear interpolation (weights sum to 1)."""
+    every cell (x, y), by bilinear interpolation (weights sum to 1): the
+    interpolation operators T_RC / T_CR of Sec. 3.4."""
     fx, fy = math.floor(sx), math.floor(sy)
     ax, ay = sx - fx, sy - fy
     # point x - sx = x - fx - ax lies between x - fx - 1 (weight ax) and x - fx
@@ -301,7 +306,7 @@ def lambda_3d(prob: Problem, S: np.ndarray, with_inflow: bool = False) -> np.nda
 
 
 def lambda_op(prob: Problem, S: np.ndarray, with_inflow: bool = False) -> np.ndarray:
-    """Lambda_N S (+ I_in) for a 1D column or a 3D box."""
+    """Lambda_N S (+ I_in) for a 1D column or a 3D box (Sec. 3.2, Sec. 3.4)."""
     if prob.dims == 1:
         return lambda_1d(prob, S, with_inflow)
     return lambda_3d(prob, S, with_inflow)
@@ -362,12 +367,13 @@ def rhs(prob: Problem) -> np.ndarray:
 
 
 def assemble_A(prob: Problem) -> np.ndarray:
-    """Dense A_N = Id - Lambda_N Sigma_N (1D only, tiny sizes)."""
+    """Dense A_N = Id - Lambda_N Sigma_N (eq. A_N; 1D only, tiny sizes)."""
     return np.eye(prob.n) - lambda_matrix_1d(prob) @ sigma_matrix(prob)
 
 
 def solve_dense(prob: Problem, b: np.ndarray | None = None) -> np.ndarray:
-    """I = A_N^{-1} b by LU with partial pivoting (LAPACK getrf/getrs)."""
+    """I = A_N^{-1} b by LU with partial pivoting (LAPACK getrf/getrs): the
+    exact solution of eq. RT_sys_algebraic at tiny sizes."""
     A = assemble_A(prob)
     return np.linalg.solve(A, rhs(prob) if b is None else b)
 
@@ -471,7 +477,8 @@ def arnoldi(matvec, v0: np.ndarray, m: int) -> np.ndarray:
 
 def solve_gmres(prob: Problem, b: np.ndarray | None = None, tol: float = 1e-13,
                 restart: int = 60, max_iter: int = 5000) -> GmresResult:
-    """Matrix-free solve of A_N I = b with the oracle's own GMRES."""
+    """Matrix-free solve of A_N I = b (eq. RT_sys_algebraic) with the oracle's
+    own GMRES (Sec. 5)."""
     bb = rhs(prob) if b is None else b
     return gmres(lambda v: apply_A(prob, v), bb, tol=tol, restart=restart, max_iter=max_iter)
 
@@ -530,14 +537,15 @@ def bicgstab(matvec, b: np.ndarray, tol: float = 1e-10, max_iter: int = 5000,
 
 def solve_bicgstab(prob: Problem, b: np.ndarray | None = None, tol: float = 1e-13,
                    max_iter: int = 5000) -> GmresResult:
-    """Matrix-free solve of A_N I = b with the oracle's own BiCGStab."""
+    """Matrix-free solve of A_N I = b (eq. RT_sys_algebraic) with the oracle's
+    own BiCGStab (Sec. 5)."""
     bb = rhs(prob) if b is None else b
     return bicgstab(lambda v: apply_A(prob, v), bb, tol=tol, max_iter=max_iter)
 
 
 # ------------------------------------------------- reduced CRD system (1D only)
 def solve_crd_reduced(prob: Problem) -> np.ndarray:
-    """Isotropic CRD (P = 1, R = phi phi^T, gamma = (1 - eps)/phi, t = eps B):
+    """Isotropic CRD (Sec. 5.2: P = 1, R = phi phi^T, gamma = (1 - eps)/phi, t = eps B):
     S depends on depth only, S = (1-eps) Jbar + eps B with Jbar = sum w_dir w_nu
     phi I.  Solve (Id - diag(1-eps) Lambda_bar) S = eps B + (1-eps) Jbar_bc with
     Lambda_bar[i, j] = sum_{dir, nu} w w phi Lambda_(dir,nu)[i, j] (N_z x N_z),
@@ -565,17 +573,20 @@ def solve_crd_reduced(prob: Problem) -> np.ndarray:
 
 # ------------------------------------------------------------------ batches
 def batch_offsets(probs) -> np.ndarray:
-    """Start offsets of each column in the concatenated batch vector."""
+    """Start offsets of each column in the concatenated batch vector (columns
+    back to back, each in the ordering of Sec. 3.1)."""
     return np.concatenate([[0], np.cumsum([p.n for p in probs])])
 
 
 def apply_A_batch(probs, x: np.ndarray) -> np.ndarray:
-    """A applied column by column to a concatenated batch vector."""
+    """A_N (eq. RT_sys_algebraic) applied column by column to a concatenated
+    batch vector."""
     off = batch_offsets(probs)
     return np.concatenate([apply_A(p, x[off[c]:off[c + 1]]) for c, p in enumerate(probs)])
 
 
 def rhs_batch(probs) -> np.ndarray:
+    """b = Lambda_N t + I_in (eq. RT_sys_algebraic) of every column, concatenated."""
     return np.concatenate([rhs(p) for p in probs])
 
 
