@@ -408,7 +408,16 @@ def test_sqrt_eps_law():
 
 
 # ------------------------------------------------------------ paper's numbers
-@pytest.mark.parametrize("n_s,n_omega", [(10, 12), (10, 24), (20, 12), (20, 24), (40, 12)])
+_MONO_MISMATCH = pytest.mark.xfail(strict=True, reason="printed entry not reproduced (N_Omega = 50 column "
+                                   "and (40, 24)); no neighbouring N_Omega reproduces it either")
+
+
+@pytest.mark.parametrize("n_s,n_omega", [(10, 12), (10, 24), (20, 12), (20, 24), (40, 12), (10, 100),
+                                         (20, 100), (100, 12), (100, 24), (200, 12),
+                                         pytest.param(10, 50, marks=_MONO_MISMATCH),
+                                         pytest.param(20, 50, marks=_MONO_MISMATCH),
+                                         pytest.param(40, 50, marks=_MONO_MISMATCH),
+                                         pytest.param(40, 24, marks=_MONO_MISMATCH)])
 def test_table_mono(n_s, n_omega):
     tab = GOLDEN["table_mono"]
     ref = tab["rows"][str(n_s)][tab["n_omega"].index(n_omega)]
