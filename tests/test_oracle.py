@@ -413,10 +413,11 @@ _MONO_MISMATCH = pytest.mark.xfail(strict=True, reason="printed entry not reprod
 
 
 @pytest.mark.parametrize("n_s,n_omega", [(10, 12), (10, 24), (20, 12), (20, 24), (40, 12), (10, 100),
-                                         (20, 100), (100, 12), (100, 24), (200, 12),
+                                         (20, 100), (40, 100), (100, 12), (100, 24), (200, 12),
                                          pytest.param(10, 50, marks=_MONO_MISMATCH),
                                          pytest.param(20, 50, marks=_MONO_MISMATCH),
                                          pytest.param(40, 50, marks=_MONO_MISMATCH),
+                                         pytest.param(100, 50, marks=_MONO_MISMATCH),
                                          pytest.param(40, 24, marks=_MONO_MISMATCH)])
 def test_table_mono(n_s, n_omega):
     tab = GOLDEN["table_mono"]
