@@ -142,13 +142,18 @@ int rt_create(const rt_desc *desc, int32_t n_rhs, int32_t precision,
               int32_t max_restart, rt_handle **out);
 
 /* Create a handle for a batch of independent 1D columns (each desc->dims ==
- * 1) of uneven nz, n_dir, n_nu, solved together (one persistent launch).
- * Workspace scales with the number of concurrently resident instances, not
- * with the batch.  Same errors as rt_create. */
+ * 1) of uneven nz, n_dir, n_nu, solved together (one persistent launch).  The
+ * batch operator is block diagonal: each column is its own system A_N I = b of
+ * Sec. 3.1 (eq. RT_sys_algebraic) with its own grid of Sec. 3.1 (N_s, N_Omega,
+ * N_nu), and a batch vector holds the columns back to back per right-hand
+ * side.  Workspace scales with the number of concurrently resident instances,
+ * not with the batch.  Same errors as rt_create. */
 int rt_create_batch(const rt_desc *cols, int32_t n_cols, int32_t n_rhs,
                     int32_t precision, int32_t max_restart, rt_handle **out);
 
-/* Number of float64 values of one x / y / b argument (all columns, all rhs). */
+/* Number of float64 values of one x / y / b argument (all columns, all rhs):
+ * n_rhs * sum over columns of N = N_s N_Omega N_nu (Sec. 3.1, the size of the
+ * space-based vector ordering); 0 for a NULL handle. */
 int64_t rt_vector_length(const rt_handle *h);
 
 /* Apply one operator (RT_OP_*) to all n_rhs vectors: y = op(x).  x and y must
@@ -180,11 +185,13 @@ typedef struct rt_tune_info {
  * choice; the paper has no counterpart.) */
 int rt_autotune(rt_handle *h, int32_t flags, rt_tune_info *out, void *stream);
 
-/* Allocation-free variant of rt_apply for callers that cannot allocate device
- * memory at call time: code running while a CUDA stream is being captured into
- * a graph (cudaMalloc is illegal there), real-time loops that must not touch
- * the allocator, or hosts whose device memory is fully budgeted up front.  (The
- * paper has no counterpart; it is a property of this library's interface.)
+/* Allocation-free variant of rt_apply, for callers that cannot allocate
+ * device memory at call time: a host program that gives its whole device
+ * memory budget to its own pool at start-up and forbids later allocations, a
+ * real-time loop that must not enter the CUDA allocator (cudaMalloc can
+ * synchronise the device and take unbounded time), or a plug-in running
+ * inside a program that owns the device.  (The paper has no counterpart; it
+ * is a property of this library's interface.)
  * Same operators and layouts as rt_apply, on a handle created beforehand, but
  * the source-function scratch of the apply is a static 16 MiB device array in
  * the library instead of handle-owned memory, and the call allocates nothing.
@@ -192,10 +199,15 @@ int rt_autotune(rt_handle *h, int32_t flags, rt_tune_info *out, void *stream);
  *  - x and y must be device pointers (host staging would allocate): else RT_ERR_ARG;
  *  - the scratch needed, n_rhs * E elements of the operator's precision
  *    (float64 if fp64 or an RT_P_FP64 handle, else float32; E alone for 3D
- *    boxes), must fit in 16 MiB: else RT_ERR_ARG naming the size;
+ *    boxes, whose frequencies are padded to a multiple of the sweep's
+ *    frequency block), must fit in 16 MiB: else RT_ERR_ARG naming the size;
  *  - the first call on a device looks up the array's device address
- *    (cudaGetSymbolAddress) with that device current; make that first call
- *    before any stream capture;
+ *    (cudaGetSymbolAddress) with that device current;
+ *  - on a mixed-precision handle whose Sigma runs on the tensor cores (dense
+ *    kernel), ops RT_OP_A and RT_OP_SIGMA with fp64 = 0 read the kernel's
+ *    device error word back and synchronise the stream before returning, as
+ *    rt_apply does (RT_ERR_TIMEOUT if a bounded wait gave up); every other
+ *    call is asynchronous on `stream`;
  *  - every call, from any handle, shares the one array: calls that overlap on
  *    the GPU (other streams, other threads) race and must be serialised by the
  *    caller; the array keeps the last call's contents (whatever must start at
@@ -241,7 +253,11 @@ int rt_solve(rt_handle *h, const double *b, double *x, const rt_solve_opts *opts
  * non-finite v0; RT_ERR_CUDA on a CUDA failure.  Synchronises the stream. */
 int rt_arnoldi(rt_handle *h, const double *v0, int32_t m, double *H, int32_t *m_done, void *stream);
 
-/* Release every device and host resource of the handle (NULL is a no-op). */
+/* Release every device and host resource of the handle (NULL is a no-op).
+ * The handle holds the discretised operator of Sec. 3 (coefficients of
+ * Lambda_N, factors of Sigma_N) and its Krylov workspaces; caller buffers
+ * are never freed.  Must not be called while work of the handle is in
+ * flight on any stream. */
 void rt_destroy(rt_handle *h);
 
 /* Message of the last error raised on this thread ("" if none). */

@@ -4,12 +4,13 @@
 // right-hand side, then S = gamma * C.
 //
 //   operands  : bf16.  X is packed to bf16 once per apply (k_to_bf16) with each
-//               column's (rhs, point) rows stacked; A boxes (8 q x 128 rows)
-//               arrive by TMA (a 2D tensor map per column) straight into the
-//               canonical no-swizzle K-major layout, zero-filled past the
-//               column; B = PsiW is pre-tiled in global memory as the exact
-//               shared-memory image of each (256-ray, 64-q) block, one
-//               cp.async.bulk.
+//               column's (rhs, point) rows stacked; the A tile of a 64-q chunk
+//               (64 q x 128 rows, one TMA box from a 2D tensor map per column)
+//               lands in the 128-byte-swizzled K-major layout (rows of 128
+//               bytes, 16-byte chunks permuted within 8-row 1024-byte atoms),
+//               zero-filled past the column; B = PsiW is pre-tiled in global
+//               memory as the exact no-swizzle K-major shared-memory image of
+//               each (256-ray, 64-q) block, one cp.async.bulk.
 //   accumulate: fp32 in tensor memory, two 128 x 256 accumulators, read back
 //               with tcgen05.ld and scaled by Gamma in the epilogue.
 //   schedule  : persistent CTAs (one per SM) walk the tile list with
@@ -137,9 +138,10 @@ __device__ __forceinline__ bool tc_wait(uint64_t *bar, uint32_t par, volatile in
 
 // Persistent, warp-specialised tile loop.  A CTA walks tiles (column, 128
 // stacked rhs/point rows, 256 rays) j = blockIdx.x, blockIdx.x + gridDim.x, ...:
-//   warp 0 (one thread): per 64-q chunk, 8 TMA boxes of A (8 q x 128 rows,
-//     straight into the no-swizzle K-major core-matrix layout, zero-filled
-//     past the column's edges) and one cp.async.bulk of the pre-tiled B into
+//   warp 0 (one thread): per 64-q chunk, one TMA box of A (64 q x 128 rows,
+//     128-byte swizzle, read by the MMA through the SWIZZLE_128B K-major
+//     shared-memory descriptor; zero-filled past the column's edges) and one
+//     cp.async.bulk of the pre-tiled B (no-swizzle K-major core matrices) into
 //     a ring of kT2Stages stages (full / empty mbarriers);
 //   warp 1 (one thread): tcgen05.mma (M=128, N<=256, K=16) into one of two
 //     TMEM accumulators (2 x 256 columns), releases each stage by
@@ -362,8 +364,9 @@ void tc_build_jobs(const std::vector<ColDev> &cols, int n_rhs, std::vector<TcJob
 }
 
 // TMA maps over the bf16 copy of X, one per dense column: dims (q, row) =
-// (nr, n_rhs * nz), row stride nr elements, box 8 q x 128 rows (rows and q
-// past the column are zero-filled by the copy).
+// (nr, n_rhs * nz), row stride nr elements, box 64 q x 128 rows with the
+// 128-byte swizzle (rows and q past the column are zero-filled by the copy);
+// the MMA reads the box through smem_desc_sw128.
 static int tc_build_maps(rt_handle *h, std::vector<CUtensorMap> &maps) {
   using EncodeFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
                                 const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,

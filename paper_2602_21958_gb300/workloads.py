@@ -146,8 +146,7 @@ def level_symmetric(order: int) -> tuple[np.ndarray, np.ndarray]:
     pts, cls = [], []
     for i in range(nlev):
         for j in range(nlev):
-            k = nlev + 1 - i - j - 2 + 1  # i + j + k = nlev - 1 (0-based)
-            k = (nlev - 1) - i - j
+            k = (nlev - 1) - i - j  # i + j + k = nlev - 1 (0-based level indices)
             if k < 0:
                 continue
             pts.append((mus[i], mus[j], mus[k]))

@@ -424,8 +424,14 @@ def test_table_mono(n_s, n_omega):
     ref = tab["rows"][str(n_s)][tab["n_omega"].index(n_omega)]
     frac, lmin = O.cluster_fraction(O.assemble_A(W.paper_mono(n_s, n_omega)))
     assert abs(100 * frac - ref) <= 0.05 + 1e-9
-    # the bound is printed to two digits (0.8197 rounds to 0.82)
-    assert round(lmin, 2) >= tab["abs_lambda_min_gt"]
+    # Sec. 5.1 states |lambda|_min > 0.82.  The oracle meets it strictly up to
+    # N_s = 20 (0.82037-0.82186); from N_s = 40 on its smallest modulus sits
+    # just below (0.81920-0.81972, decreasing with N_s), a documented
+    # deviation of less than 1e-3 that is asserted as such, not rounded away.
+    if n_s <= 20:
+        assert lmin > tab["abs_lambda_min_gt"]
+    else:
+        assert 0.8190 < lmin < tab["abs_lambda_min_gt"]
 
 
 @pytest.mark.parametrize("n", [10, 50])
@@ -589,3 +595,55 @@ def test_3d_constant_source_closed_form():
             steps = np.arange(nz) if dirs[d, 2] < 0 else np.arange(nz)[::-1]
             ref = 1 - np.exp(-c * ds * steps)
             assert np.abs(I[:, :, d, f] - ref[:, None]).max() < 1e-14
+
+
+# ------------------------------------------------------------------ batches
+def _ragged_columns():
+    return [W.two_level_column(np.logspace(-2, 2, 5), 4, 1, 3, "crd", 1e-2, 1.0),
+            W.two_level_column(np.logspace(-3, 3, 9), 2, 2, 7, "r2", 1e-3, 1.5),
+            W.two_level_column(np.array([0.1, 2.0]), 2, 1, 1, "crd", 0.5, 1.0)]
+
+
+def test_batch_offsets_are_the_cumulative_column_sizes():
+    """The batch vector is the columns back to back (each in the ordering of
+    Sec. 3.1): offsets start at 0, step by n_z * n_dir * n_nu and end at the
+    total length."""
+    cols = _ragged_columns()
+    off = O.batch_offsets(cols)
+    sizes = [c.nz * c.n_dir * c.n_nu for c in cols]
+    assert off.tolist() == [0, sizes[0], sizes[0] + sizes[1], sum(sizes)]
+
+
+def test_batch_apply_is_the_block_diagonal_operator():
+    """A batch of independent columns is one block-diagonal system: the
+    batched apply equals the block-diagonal matrix of the columns' assembled
+    A_N (eq. RT_sys_algebraic) times a random vector, and permuting the
+    columns permutes the output blocks the same way."""
+    cols = _ragged_columns()
+    blocks = [O.assemble_A(c) for c in cols]
+    n = sum(b.shape[0] for b in blocks)
+    big = np.zeros((n, n))
+    o = 0
+    for b in blocks:
+        big[o:o + b.shape[0], o:o + b.shape[0]] = b
+        o += b.shape[0]
+    x = np.random.default_rng(3).standard_normal(n)
+    y = O.apply_A_batch(cols, x)
+    assert np.linalg.norm(y - big @ x) <= 1e-13 * np.linalg.norm(big @ x)
+    off = O.batch_offsets(cols)
+    perm = [2, 0, 1]
+    xp = np.concatenate([x[off[c]:off[c + 1]] for c in perm])
+    yp = O.apply_A_batch([cols[c] for c in perm], xp)
+    assert np.array_equal(yp, np.concatenate([y[off[c]:off[c + 1]] for c in perm]))
+
+
+def test_batch_rhs_solves_with_the_column_solutions():
+    """b of the batch (Lambda t + I_in per column) solved as one block-diagonal
+    system gives each column's own dense solution."""
+    cols = _ragged_columns()
+    b = O.rhs_batch(cols)
+    off = O.batch_offsets(cols)
+    assert b.shape == (off[-1],)
+    for c, p in enumerate(cols):
+        xc = np.linalg.solve(O.assemble_A(p), b[off[c]:off[c + 1]])
+        assert np.linalg.norm(xc - O.solve_dense(p)) <= 1e-13 * np.linalg.norm(xc)
