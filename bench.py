@@ -486,8 +486,10 @@ def profile_case(kind: str):
             h.rt_apply(rt.RT_OP_A, x, y)
         torch.cuda.synchronize()
         print("apply", E)
-    elif kind == "apply3d":
-        p = W.config_c3()
+    elif kind in ("apply3d", "apply3d-c4s"):
+        # C3 (32^3, S_6, 32 nu), or C4's planes and physics (64 x 64, S_8, 64 nu,
+        # 0.7 R_II-A + 0.3 R_III-A) on 8 planes: 1.7e8 dofs, 1.3 GB per vector
+        p = W.config_c3() if kind == "apply3d" else W.box_3d(64, 8, 64, "r23", 1e-3, W.SEED_BASE + 4, nz=8)
         h = rt.Handle(p, precision=rt.RT_P_MIXED, max_restart=4)
         x = torch.rand(p.n, dtype=torch.float64, device=dev)
         y = torch.empty_like(x)
@@ -550,7 +552,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--profile", choices=["solve-small", "apply", "sigma-tc", "apply3d"], default=None,
+    ap.add_argument("--profile", choices=["solve-small", "apply", "sigma-tc", "apply3d", "apply3d-c4s"], default=None,
                     help="run one bounded case for an ncu capture and exit (no JSON line)")
     args = ap.parse_args()
     if args.profile:

@@ -171,18 +171,22 @@ typedef struct rt_tune_info {
   int32_t sigma_points;  /* cap on points per Sigma tile: 4, 8, or 0 (as many as fit)    */
   int32_t from_cache;    /* 1 if read from the RT_TUNE_CACHE file                       */
   double ms_best;        /* rt_apply(RT_OP_A) time of the choice                         */
-  double ms_default;     /* time of the default shape (128, 4, 0); 0 if from cache       */
+  double ms_default;     /* time of the default shape; 0 if from cache                   */
+  int32_t box_fb;        /* 3D boxes: frequencies per plane-sweep CTA (1, 2 or 4)        */
+  int32_t box_cpt;       /* 3D boxes: cells per thread of the plane sweep (1, 2, 4, 8)   */
 } rt_tune_info;
 
-/* Pick the launch shapes of the batched apply kernels (the sweep tile width and
- * its load-ahead depth, the Sigma tile size) by timing rt_apply(RT_OP_A) on
- * this handle's own problem for the 27 combinations, and keep the fastest on
- * the handle (every later rt_apply uses it).  When the environment variable
- * RT_TUNE_CACHE names a file, a previous result for the same problem signature
- * is read from it (JSON lines) instead of re-timing, unless flags & 1; new
- * results are appended.  Allocates two temporary vectors.  3D boxes have one
- * launch shape: the call only reports it.  out may be NULL.  (Implementation
- * choice; the paper has no counterpart.) */
+/* Pick the launch shapes of the apply kernels by timing rt_apply(RT_OP_A) on
+ * this handle's own problem, and keep the fastest on the handle (every later
+ * rt_apply and every solve of a 3D box uses it).  1D batches: the sweep tile
+ * width and its load-ahead depth and the Sigma tile size (27 combinations).
+ * 3D boxes: the plane sweep's frequencies per CTA and cells per thread (the
+ * distinct feasible combinations of 1, 2, 4 and 1, 2, 4, 8).  When the
+ * environment variable RT_TUNE_CACHE names a file, a previous result for the
+ * same problem signature is read from it (JSON lines) instead of re-timing,
+ * unless flags & 1; new results are appended.  Allocates two temporary
+ * vectors.  out may be NULL.  (Implementation choice; the paper has no
+ * counterpart.) */
 int rt_autotune(rt_handle *h, int32_t flags, rt_tune_info *out, void *stream);
 
 /* Allocation-free variant of rt_apply, for callers that cannot allocate

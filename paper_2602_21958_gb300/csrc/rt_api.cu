@@ -6,6 +6,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <numeric>
+#include <utility>
 #include <string>
 #include <vector>
 
@@ -115,7 +116,7 @@ void free_handle(rt_handle *h) {
                   h->so.outer, h->so.inner, h->so.status, h->so.relres, h->so.bytes,
                   h->stage_x, h->stage_y, h->d_sig_tiles, h->d_sw_tiles, h->apply_S,
                   h->d_tc_jobs, h->d_tc_off, h->d_tc_tiles, h->d_tc_xb, h->d_tc_maps, h->d_err, h->d_geo,
-                  h->chi64, h->chi32, h->g_part, h->g_red, h->g_coef, h->g_r, h->Q64, h->Q32};
+                  h->chi64, h->chi32, h->box_w064, h->box_bt64, h->g_part, h->g_red, h->g_coef, h->g_r, h->Q64, h->Q32};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (h->solve_graph) cudaGraphExecDestroy(h->solve_graph);
@@ -560,8 +561,7 @@ int create_box(const rt_desc *d, int n_rhs, int precision, int max_restart, rt_h
   if (d->formal_solver != RT_FS_SCL && d->formal_solver != RT_FS_IE) return fail(RT_ERR_ARG, "unknown formal_solver");
   const int64_t npts = (int64_t)d->nx * d->ny * d->nz;
   const int64_t plane = (int64_t)d->nx * d->ny;
-  if (plane * 32 > 200 * 1024) return fail(RT_ERR_ARG, "box: a z-plane must fit in shared memory (nx*ny <= 6400)");
-  if (plane * 8 > 32 * 1024) return fail(RT_ERR_ARG, "box: nx*ny must be at most 4096 (32 values per thread)");
+  if (!rt::box_plane_fits(d->nx, d->ny)) return fail(RT_ERR_ARG, "box: nx*ny must be at most 4096 (a z-plane in shared memory)");
   for (int k = 0; k < d->n_dir; ++k)
     if (!(std::fabs(d->dir[3 * k + 2]) > 0.0)) return fail(RT_ERR_ARG, "box: direction with Omega_z = 0");
   const size_t np = (size_t)npts * d->n_nu;
@@ -572,6 +572,8 @@ int create_box(const rt_desc *d, int n_rhs, int precision, int max_restart, rt_h
   rt_desc dd = *d;
   int rc = build_column(&dd, ch);
   if (rc != RT_OK) return rc;
+  if (!d->Psi && !rt::box_sigma_fits(d, ch.c.rp))
+    return fail(RT_ERR_ARG, "box: the separable kernel needs rank(P) <= 6 and n_nu <= 128");
   rt_handle *h = new rt_handle();
   h->dims = 3;
   h->n_cols = 1;
@@ -618,9 +620,14 @@ int create_box(const rt_desc *d, int n_rhs, int precision, int max_restart, rt_h
   UPB(h->d_dir_cls, ch.dir_cls);
   UPB(h->d_dir_up, ch.dir_up);
   UPB(h->d_geo, geo);
-  UPB(h->chi64, chi);
-  std::vector<float> chif = to_f32(chi), gamf = to_f32(gam);
-  UPB(h->chi32, chif);
+  {
+    const cudaError_t be = (cudaError_t)rt::box_prepare(h, chi.data());
+    if (be != cudaSuccess) {
+      free_handle(h);
+      return fail(be == cudaErrorMemoryAllocation ? RT_ERR_OOM : RT_ERR_CUDA, std::string("box opacity: ") + cudaGetErrorString(be));
+    }
+  }
+  std::vector<float> gamf = to_f32(gam);
   UPB(h->gam64, gam);
   UPB(h->gam32, gamf);
   UPB(h->d_Itop, itop);
@@ -648,7 +655,10 @@ int create_box(const rt_desc *d, int n_rhs, int precision, int max_restart, rt_h
   cudaError_t ce = cudaGetDevice(&dev);
   if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&h->n_sm, cudaDevAttrMultiProcessorCount, dev);
   const int G = 2 * h->n_sm;
-  if (ce == cudaSuccess) ce = cudaMalloc(&h->apply_S, (size_t)h->E * sizeof(double));
+  // source-function scratch in the sweep layout: frequencies padded up to the
+  // sweep's block (at most to a multiple of 4), float64 at most
+  const size_t s_bytes = (size_t)npts * d->n_dir * h->box_npad * sizeof(double);
+  if (ce == cudaSuccess) ce = cudaMalloc(&h->apply_S, std::max(s_bytes, (size_t)h->E * sizeof(double)));
   if (ce == cudaSuccess) ce = cudaMalloc(&h->g_r, (size_t)h->E * sizeof(double));
   if (ce == cudaSuccess) ce = cudaMalloc(&h->g_part, (size_t)G * 16 * sizeof(double));
   if (ce == cudaSuccess) ce = cudaMalloc(&h->g_red, 64 * sizeof(double));
@@ -693,6 +703,104 @@ int ensure_stage(rt_handle *h, int64_t len) {
   RT_CUDA(cudaMalloc(&h->stage_y, len * sizeof(double)));
   h->stage_len = len;
   return RT_OK;
+}
+
+// Plane-sweep launch shape of a 3D box (frequencies per CTA, cells per
+// thread): every distinct feasible combination timed on rt_apply(RT_OP_A) in
+// the handle's precision, the fastest kept; RT_TUNE_CACHE as for batches.
+int autotune_box(rt_handle *h, int flags, rt_tune_info *out, cudaStream_t s, const char *sig, const char *path,
+                 rt_tune_info loc) {
+  const bool f64 = h->precision == RT_P_FP64;
+  auto report = [&](double best, double first, int from_cache) {
+    int fb = 0, cpt = 0;
+    rt::box_effective_shape(h, f64, fb, cpt);
+    loc.box_fb = fb;
+    loc.box_cpt = cpt;
+    loc.ms_best = best;
+    loc.ms_default = first;
+    loc.from_cache = from_cache;
+    if (out) *out = loc;
+    return RT_OK;
+  };
+  if (path && !(flags & 1)) {
+    if (FILE *f = std::fopen(path, "r")) {
+      char line[512];
+      int fb = 0, cpt = 0;
+      double ms = 0;
+      bool hit = false;
+      while (std::fgets(line, sizeof line, f)) {
+        const char *q = std::strstr(line, "\"sig\": \"");
+        if (!q || std::strncmp(q + 8, sig, std::strlen(sig)) != 0 || q[8 + std::strlen(sig)] != '"') continue;
+        const char *r = std::strstr(line, "\"box_fb\":");
+        if (r && std::sscanf(r, "\"box_fb\": %d, \"box_cpt\": %d, \"ms\": %lf", &fb, &cpt, &ms) == 3) hit = true;
+      }
+      std::fclose(f);
+      if (hit) {
+        h->tune.box_fb = fb;
+        h->tune.box_cpt = cpt;
+        h->tune.ms = ms;
+        h->tune.from_cache = 1;
+        return report(ms, 0.0, 1);
+      }
+    }
+  }
+  const int64_t len = h->E;
+  double *x = nullptr, *y = nullptr;
+  RT_CUDA(cudaMalloc(&x, len * sizeof(double)));
+  cudaError_t ce = cudaMalloc(&y, len * sizeof(double));
+  if (ce != cudaSuccess) {
+    cudaFree(x);
+    return fail(RT_ERR_OOM, "autotune buffers");
+  }
+  cudaMemsetAsync(x, 0, len * sizeof(double), s);
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  double best = 1e300, first = 0.0;
+  int best_fb = 0, best_cpt = 0;
+  std::vector<std::pair<int, int>> seen;
+  int rc = RT_OK;
+  const int fbs[3] = {4, 2, 1}, cpts[4] = {1, 2, 4, 8};
+  for (int a = 0; a < 3 && rc == RT_OK; ++a)
+    for (int b = 0; b < 4 && rc == RT_OK; ++b) {
+      h->tune.box_fb = fbs[a];
+      h->tune.box_cpt = cpts[b];
+      int fb = 0, cpt = 0;
+      rt::box_effective_shape(h, f64, fb, cpt);
+      if (std::find(seen.begin(), seen.end(), std::make_pair(fb, cpt)) != seen.end()) continue;
+      seen.emplace_back(fb, cpt);
+      if (rt::launch_apply(h, RT_OP_A, f64, x, y, s) != 0) { rc = fail(RT_ERR_CUDA, "autotune launch"); break; }
+      cudaEventRecord(e0, s);
+      for (int k = 0; k < 3; ++k) rt::launch_apply(h, RT_OP_A, f64, x, y, s);
+      cudaEventRecord(e1, s);
+      if (cudaEventSynchronize(e1) != cudaSuccess) { rc = fail(RT_ERR_CUDA, "autotune launch"); break; }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      const double t = ms / 3.0;
+      if (seen.size() == 1) first = t;
+      if (t < best) {
+        best = t;
+        best_fb = fb;
+        best_cpt = cpt;
+      }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(x);
+  cudaFree(y);
+  if (rc != RT_OK) return rc;
+  h->tune.box_fb = best_fb;
+  h->tune.box_cpt = best_cpt;
+  h->tune.ms = best;
+  h->tune.from_cache = 0;
+  if (path) {
+    if (FILE *f = std::fopen(path, "a")) {
+      std::fprintf(f, "{\"sig\": \"%s\", \"box_fb\": %d, \"box_cpt\": %d, \"ms\": %.6f}\n", sig, best_fb, best_cpt,
+                   best);
+      std::fclose(f);
+    }
+  }
+  return report(best, first, 0);
 }
 
 }  // namespace
@@ -764,7 +872,8 @@ int rt_apply_noalloc(rt_handle *h, int32_t op, int32_t fp64, const double *x, do
   if ((x && !is_device_ptr(x)) || !is_device_ptr(y))
     return fail(RT_ERR_ARG, "rt_apply_noalloc takes device pointers only");
   const bool f64 = fp64 || h->precision == RT_P_FP64;
-  const long long need = (long long)(h->dims == 3 ? h->E : h->E * h->n_rhs) * (f64 ? 8 : 4);
+  const long long need = (h->dims == 3 ? (long long)rt::box_scratch_elems(h, f64) : (long long)h->E * h->n_rhs) *
+                         (f64 ? 8 : 4);
   if (need > rt::kNoAllocScratchBytes) {
     char msg[200];
     std::snprintf(msg, sizeof msg, "rt_apply_noalloc: the apply needs %lld bytes of scratch, the static "
@@ -801,11 +910,8 @@ int rt_autotune(rt_handle *h, int32_t flags, rt_tune_info *out, void *stream) {
   loc.ray_block = h->tune.ray_block;
   loc.ahead = h->tune.ahead;
   loc.sigma_points = h->tune.sigma_pts;
-  if (h->dims == 3) {  // the plane sweep has a single launch shape per box
-    if (out) *out = loc;
-    return RT_OK;
-  }
   const char *path = std::getenv("RT_TUNE_CACHE");
+  if (h->dims == 3) return autotune_box(h, flags, out, s, sig, path, loc);
   if (path && !(flags & 1)) {
     if (FILE *f = std::fopen(path, "r")) {
       char line[512];

@@ -125,57 +125,9 @@ static int run_apply(rt_handle *h, const Tables<T> &tb, int op, const double *x,
   return (int)cudaGetLastError();
 }
 
-template <typename T, typename TX>
-static int box_apply_t(rt_handle *h, const Tables<T> &tb, int op, const TX *x, void *y, bool yf, cudaStream_t s,
-                       void *scratch) {
-  const Common cm{h->d_cols, h->d_dir_cls, h->d_dir_up, h->d_tsrc, h->d_Itop, h->d_Ibot};
-  T *S = reinterpret_cast<T *>(scratch ? scratch : h->apply_S);
-  const bool fp64 = sizeof(T) == 8;
-  const bool xf = sizeof(TX) == 4;
-  const int64_t len = h->E;
-  const int cgrid = (int)std::min<int64_t>((len + 255) / 256, 16 * 152);
-  switch (op) {
-    case 0:
-      k_sigma_tiles<T, TX><<<h->n_sig_tiles, kSigNT, 0, s>>>(cm, tb, h->d_sig_tiles, 1, h->E, x, S, 0);
-      return launch_sweep3d(h, fp64, S, nullptr, x, xf, y, yf, kOutAminus, false, s);
-    case 1:
-      if (xf) return (int)cudaErrorInvalidValue;
-      k_convert<T><<<cgrid, 256, 0, s>>>(reinterpret_cast<const double *>(x), S, len);
-      return launch_sweep3d(h, fp64, S, nullptr, nullptr, false, y, yf, kOutI, false, s);
-    case 2:
-      if (yf) return (int)cudaErrorInvalidValue;
-      k_sigma_tiles<T, TX><<<h->n_sig_tiles, kSigNT, 0, s>>>(cm, tb, h->d_sig_tiles, 1, h->E, x, S, 0);
-      k_widen<T><<<cgrid, 256, 0, s>>>(S, static_cast<double *>(y), len);
-      return (int)cudaGetLastError();
-    default:
-      if (h->d_tsrc) return launch_sweep3d(h, fp64, S, h->d_tsrc, nullptr, false, y, yf, kOutI, true, s);
-      cudaMemsetAsync(S, 0, len * sizeof(T), s);
-      return launch_sweep3d(h, fp64, S, nullptr, nullptr, false, y, yf, kOutI, true, s);
-  }
-}
-
-// Operators of a 3D box: Sigma by point tiles, then the plane sweep.  x (and
-// y) are float32 when xf (yf), else float64; the float64 operator needs both
-// in float64.
-static int apply_box_s(rt_handle *h, int op, bool fp64, const void *x, bool xf, void *y, bool yf, cudaStream_t s,
-                       void *scratch) {
-  if (fp64 || h->precision == 0) {
-    const Tables<double> tb = tables64(h);
-    if (xf) return (int)cudaErrorInvalidValue;
-    return box_apply_t<double, double>(h, tb, op, static_cast<const double *>(x), y, yf, s, scratch);
-  }
-  const Tables<float> tb = tables32(h);
-  if (xf) return box_apply_t<float, float>(h, tb, op, static_cast<const float *>(x), y, yf, s, scratch);
-  return box_apply_t<float, double>(h, tb, op, static_cast<const double *>(x), y, yf, s, scratch);
-}
-
-int apply_box(rt_handle *h, int op, bool fp64, const void *x, bool xf, void *y, bool yf, cudaStream_t s) {
-  return apply_box_s(h, op, fp64, x, xf, y, yf, s, nullptr);
-}
-
 static int launch_apply_s(rt_handle *h, int op, bool fp64, const double *x, double *y, cudaStream_t s,
                           bool first_rhs_only, void *scratch) {
-  if (h->dims == 3) return apply_box_s(h, op, fp64, x, false, y, false, s, scratch);
+  if (h->dims == 3) return box_apply(h, op, fp64, x, false, y, false, s, scratch);
   if (fp64 || h->precision == 0) {
     const Tables<double> tb = tables64(h);
     return run_apply<double>(h, tb, op, x, y, s, first_rhs_only, scratch);

@@ -1,44 +1,92 @@
-// rt_box.cu -- 3D boxes (Sec. 3.4): short-characteristics formal solution
-// between consecutive z-planes, periodic in x and y, with bilinear
-// interpolation of I, S and chi at the upwind point (the interpolation
-// operators T_RC, T_CR of Sec. 3.4, rows summing to one).
+// rt_box.cu -- 3D boxes (Sec. 3.4): the scattering contraction and the
+// short-characteristics formal solution between consecutive z-planes,
+// periodic in x and y, with bilinear interpolation of I, S and chi at the
+// upwind point (the interpolation operators T_RC, T_CR of Sec. 3.4, rows
+// summing to one).
 //
-// k_sweep3d: one CTA per (direction, block of frequencies spanning 32 bytes)
-// marches the planes; the previous plane's intensity lives in shared memory,
-// the upwind source and opacity are gathered from global memory (L1/L2), the
-// optical depth 0.5 (chi_u + chi_c) ds and the step coefficients are formed on
-// the fly (float32 path: expf / expm1f; float64 path: exp / expm1 and the
-// alternating series for w1/dtau below 0.1).
+// Data layout of the apply.  x and y keep the space-based ordering of
+// Sec. 3.1 (point, direction, frequency fastest).  The source function S
+// between the two kernels is internal scratch and is written by the Sigma
+// kernel in the layout the sweep streams: [direction][frequency block][point]
+// [FB frequencies], so one sweep CTA reads one contiguous run per plane.  The
+// opacity is stored in blocks of 4 frequencies: [f / 4][point][f % 4].
+//
+//   k_sigma_box : one warp per point, S = Gamma (factored P (x) R) X
+//                 (eq. Sigma) -- angular moments, frequency kernel, expansion
+//   k_sweep3d   : one CTA per (direction, block of FB frequencies) marches
+//                 the planes.  The previous plane's I, S and chi live in
+//                 shared memory (FB values per cell); each thread owns CPT
+//                 cells, loads their current-plane S, chi and x in batches
+//                 of CB cells, interpolates the upwind values from shared
+//                 memory, steps the recurrence and writes y; the new plane
+//                 replaces the old one between two barriers.
+// The float32 step coefficients use e = exp(-d) (fast exponential), and for
+// d < 0.5 the series of 1 - e^-d and of w1/d (no cancellation); the float64
+// ones use exp, expm1 and the series of w1/d below 0.1.
 #include <cuda_runtime.h>
+
+#include <algorithm>
+#include <vector>
 
 #include "rt_host.h"
 #include "rt_internal.cuh"
 
 namespace rt {
 
+template <typename T, int FB>
+struct alignas(sizeof(T) * FB) Pack {
+  T v[FB];
+};
+
+// casts between the vector and arithmetic types, without float64 cvt
+template <typename T, typename X> __device__ __forceinline__ T cast_to(X v) { return (T)v; }
+template <> __device__ __forceinline__ float cast_to<float, double>(double v) { return narrow_f32(v); }
+template <> __device__ __forceinline__ double cast_to<double, float>(float v) { return widen_f64(v); }
+
+// ------------------------------------------------------------ coefficients
 template <typename T>
-__device__ __forceinline__ void step_coef(T d, int ie, T &e, T &a, T &b) {
+__device__ __forceinline__ void step_coef(T d, int ie, T &e, T &a, T &b);
+
+template <>
+__device__ __forceinline__ void step_coef<float>(float d, int ie, float &e, float &a, float &b) {
   if (ie) {
-    e = (T)1 / ((T)1 + d);
-    a = 0;
+    e = __fdividef(1.f, 1.f + d);
+    a = 0.f;
     b = d * e;
     return;
   }
-  T w0;
-  if (sizeof(T) == 8) {
-    e = (T)exp((double)-d);
-    w0 = (T)-expm1((double)-d);
-  } else {
-    e = (T)expf((float)-d);
-    w0 = (T)-expm1f((float)-d);
+  e = __expf(-d);
+  // series below 0.5: 1 - e^-d = d (1 - d/2 (1 - d/3 (...))) and
+  // w1/d = (d/2)(1 - (d/3)(1 - (d/4)(...))), 10 factors each
+  float s0 = 1.f, s1 = 1.f;
+#pragma unroll
+  for (int j = 11; j >= 2; --j) s0 = 1.f - d * (1.f / (float)j) * s0;
+#pragma unroll
+  for (int j = 12; j >= 3; --j) s1 = 1.f - d * (1.f / (float)j) * s1;
+  const bool small = d < 0.5f;
+  const float w0 = small ? d * s0 : 1.f - e;
+  const float beta = small ? 0.5f * d * s1 : 1.f - __fdividef(w0, d);
+  b = beta;
+  a = w0 - beta;
+}
+
+template <>
+__device__ __forceinline__ void step_coef<double>(double d, int ie, double &e, double &a, double &b) {
+  if (ie) {
+    e = 1.0 / (1.0 + d);
+    a = 0.0;
+    b = d * e;
+    return;
   }
-  T beta;
-  if (d < (T)0.1) {
-    // w1/d = (d/2)(1 - (d/3)(1 - (d/4)(1 - ...))): 16 terms (fp64), 8 (fp32)
-    T s = 1;
-    const int top = sizeof(T) == 8 ? 17 : 9;
-    for (int j = top; j >= 3; --j) s = (T)1 - (d / (T)j) * s;
-    beta = (T)0.5 * d * s;
+  e = exp(-d);
+  const double w0 = -expm1(-d);
+  double beta;
+  if (d < 0.1) {
+    // w1/d = (d/2)(1 - (d/3)(1 - (d/4)(1 - ...))): 16 factors
+    double s = 1.0;
+#pragma unroll
+    for (int j = 17; j >= 3; --j) s = 1.0 - d * (1.0 / j) * s;
+    beta = 0.5 * d * s;
   } else {
     beta = (d - w0) / d;
   }
@@ -46,132 +94,642 @@ __device__ __forceinline__ void step_coef(T d, int ie, T &e, T &a, T &b) {
   a = w0 - beta;
 }
 
+// ------------------------------------------------------------------ Sigma
+constexpr int kBoxSigNT = 256;     // threads per Sigma CTA (8 warps, one point each)
+constexpr int kBoxRwCache = 32768;  // bytes of frequency kernel staged in shared memory (else global)
+
+// Index of (point p, direction d, frequency f) in the sweep layout
+// [d][f / FB][p][f % FB]; fb_out == 0 selects the space-based layout.
+__device__ __forceinline__ int64_t box_out_index(int64_t p, int d, int f, int nn, int nr, int64_t npts, int fb_out,
+                                                 int nfb) {
+  if (fb_out == 0) return p * nr + (int64_t)d * nn + f;
+  const int fb = f / fb_out;
+  return (((int64_t)d * nfb + fb) * npts + p) * fb_out + (f - fb * fb_out);
+}
+
+// Separable kernel: one warp per point (grid-stride).  Lane l owns the
+// frequencies l, l + 32, ..., FL of them, and keeps their KR >= rank moments
+// and frequency-kernel outputs in registers through the three stages, so a
+// shared-memory load of a factor entry feeds FL FMAs.  Shared memory: Uw | Ul
+// (nd * KR each, zero past the rank), the frequency kernel RwT when it fits
+// kBoxRwCache, and per warp the moments (KR * nn) that stage 2 broadcasts.
+template <typename T, typename TX, int KR, int FL>
+__global__ void __launch_bounds__(kBoxSigNT) k_sigma_box(ColDev c, Tables<T> tb, int64_t npts, const TX *__restrict__ X,
+                                                         T *__restrict__ S, int fb_out) {
+  extern __shared__ __align__(16) unsigned char sig_smem[];
+  const int nd = c.nd, nn = c.nn, nr = c.nr, rp = c.rp;
+  const int nfb = fb_out ? (nn + fb_out - 1) / fb_out : 0;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  T *sUw = reinterpret_cast<T *>(sig_smem);
+  T *sUl = sUw + nd * KR;
+  T *sRw = sUl + nd * KR;
+  const bool rw_cached = !c.rdiag && (int64_t)nn * nn * sizeof(T) <= kBoxRwCache;
+  const int rw_len = c.rdiag ? nn : (rw_cached ? nn * nn : 0);
+  T *wm = sRw + ((rw_len + 1) & ~1) + (int64_t)warp * KR * nn;
+  for (int i = threadIdx.x; i < nd * KR; i += blockDim.x) {
+    const int d = i / KR, k = i - d * KR;
+    sUw[i] = k < rp ? tb.Uw[c.u_off + d * rp + k] : T(0);
+    sUl[i] = k < rp ? tb.Ul[c.u_off + d * rp + k] : T(0);
+  }
+  for (int i = threadIdx.x; i < rw_len; i += blockDim.x) sRw[i] = tb.RwT[c.r_off + i];
+  __syncthreads();
+  const T *Rw = (c.rdiag || rw_cached) ? sRw : tb.RwT + c.r_off;
+  const T *gam = tb.gamma + c.g_off;
+  int fl[FL];
+  bool on[FL];
+#pragma unroll
+  for (int j = 0; j < FL; ++j) {
+    on[j] = lane + 32 * j < nn;
+    fl[j] = on[j] ? lane + 32 * j : 0;
+  }
+  for (int64_t p = (int64_t)blockIdx.x * nw + warp; p < npts; p += (int64_t)gridDim.x * nw) {
+    const TX *xp = X + p * nr;
+    // 1. moments m_k(f) = sum_d Uw[d][k] X(d, f)
+    T m[FL][KR];
+#pragma unroll
+    for (int j = 0; j < FL; ++j)
+#pragma unroll
+      for (int k = 0; k < KR; ++k) m[j][k] = 0;
+    int d = 0;
+    for (; d + 4 <= nd; d += 4) {
+      T xv[4][FL];
+#pragma unroll
+      for (int e = 0; e < 4; ++e)
+#pragma unroll
+        for (int j = 0; j < FL; ++j) xv[e][j] = on[j] ? cast_to<T>(xp[(d + e) * nn + fl[j]]) : T(0);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const T *u = sUw + (d + e) * KR;
+#pragma unroll
+        for (int k = 0; k < KR; ++k) {
+          const T uk = u[k];
+#pragma unroll
+          for (int j = 0; j < FL; ++j) m[j][k] = fma(uk, xv[e][j], m[j][k]);
+        }
+      }
+    }
+    for (; d < nd; ++d) {
+      const T *u = sUw + d * KR;
+#pragma unroll
+      for (int j = 0; j < FL; ++j) {
+        const T xv = on[j] ? cast_to<T>(xp[d * nn + fl[j]]) : T(0);
+#pragma unroll
+        for (int k = 0; k < KR; ++k) m[j][k] = fma(u[k], xv, m[j][k]);
+      }
+    }
+    // 2. frequency kernel z_k(f) = sum_q RwT[q][f] m_k(q)
+    T z[FL][KR];
+    if (c.rdiag) {
+#pragma unroll
+      for (int j = 0; j < FL; ++j)
+#pragma unroll
+        for (int k = 0; k < KR; ++k) z[j][k] = Rw[fl[j]] * m[j][k];
+    } else {
+#pragma unroll
+      for (int j = 0; j < FL; ++j)
+        if (on[j]) {
+#pragma unroll
+          for (int k = 0; k < KR; ++k) wm[k * nn + fl[j]] = m[j][k];
+        }
+      __syncwarp();
+#pragma unroll
+      for (int j = 0; j < FL; ++j)
+#pragma unroll
+        for (int k = 0; k < KR; ++k) z[j][k] = 0;
+      for (int q = 0; q < nn; ++q) {
+        T mq[KR];
+#pragma unroll
+        for (int k = 0; k < KR; ++k) mq[k] = wm[k * nn + q];
+#pragma unroll
+        for (int j = 0; j < FL; ++j) {
+          const T r = Rw[q * nn + fl[j]];
+#pragma unroll
+          for (int k = 0; k < KR; ++k) z[j][k] = fma(r, mq[k], z[j][k]);
+        }
+      }
+      __syncwarp();
+    }
+    // 3. expansion S(d, f) = gamma(f) sum_k Ul[d][k] z_k(f)
+    T gf[FL];
+#pragma unroll
+    for (int j = 0; j < FL; ++j) {
+      gf[j] = gam[p * nn + fl[j]];
+#pragma unroll
+      for (int k = 0; k < KR; ++k) z[j][k] *= gf[j];
+    }
+    for (int dd = 0; dd < nd; ++dd) {
+      const T *u = sUl + dd * KR;
+      T acc[FL];
+#pragma unroll
+      for (int j = 0; j < FL; ++j) acc[j] = 0;
+#pragma unroll
+      for (int k = 0; k < KR; ++k) {
+        const T uk = u[k];
+#pragma unroll
+        for (int j = 0; j < FL; ++j) acc[j] = fma(uk, z[j][k], acc[j]);
+      }
+#pragma unroll
+      for (int j = 0; j < FL; ++j)
+        if (on[j]) S[box_out_index(p, dd, fl[j], nn, nr, npts, fb_out, nfb)] = acc[j];
+    }
+  }
+}
+
+// Dense kernel Psi (n_r x n_r): S(p, r) = gamma sum_q PsiwT[q][r] X(p, q),
+// lanes over r, one warp per point (small problems only).
+template <typename T, typename TX>
+__global__ void __launch_bounds__(kBoxSigNT) k_sigma_box_dense(ColDev c, Tables<T> tb, int64_t npts,
+                                                               const TX *__restrict__ X, T *__restrict__ S,
+                                                               int fb_out) {
+  const int nn = c.nn, nr = c.nr;
+  const int nfb = fb_out ? (nn + fb_out - 1) / fb_out : 0;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const T *Pw = tb.PsiwT + c.psi_off;
+  const T *gam = tb.gamma + c.g_off;
+  for (int64_t p = (int64_t)blockIdx.x * nw + warp; p < npts; p += (int64_t)gridDim.x * nw) {
+    const TX *xp = X + p * nr;
+    for (int r = lane; r < nr; r += 32) {
+      T acc = 0;
+      for (int q = 0; q < nr; ++q) acc = fma(Pw[(int64_t)q * nr + r], cast_to<T>(xp[q]), acc);
+      const int d = r / nn, f = r - d * nn;
+      S[box_out_index(p, d, f, nn, nr, npts, fb_out, nfb)] = gam[p * nn + f] * acc;
+    }
+  }
+}
+
+// x (space-based layout, float64) -> the sweep layout in T (Lambda x alone)
+// (one CTA per point, threads over its rays)
+template <typename T>
+__global__ void k_box_to_sweep(const double *__restrict__ x, T *__restrict__ S, int64_t npts, int nd, int nn,
+                               int fb) {
+  const int nfb = (nn + fb - 1) / fb, nr = nd * nn;
+  for (int64_t p = blockIdx.x; p < npts; p += gridDim.x)
+    for (int r = threadIdx.x; r < nr; r += blockDim.x) {
+      const int d = r / nn, f = r - d * nn;
+      S[box_out_index(p, d, f, nn, nr, npts, fb, nfb)] = cast_to<T>(x[p * nr + r]);
+    }
+}
+
+// sweep layout T -> space-based float64 (Sigma x alone)
+template <typename T>
+__global__ void k_box_from_sweep(const T *__restrict__ S, double *__restrict__ y, int64_t npts, int nd, int nn,
+                                 int fb) {
+  const int nfb = (nn + fb - 1) / fb, nr = nd * nn;
+  for (int64_t p = blockIdx.x; p < npts; p += gridDim.x)
+    for (int r = threadIdx.x; r < nr; r += blockDim.x) {
+      const int d = r / nn, f = r - d * nn;
+      y[p * nr + r] = cast_to<double>(S[box_out_index(p, d, f, nn, nr, npts, fb, nfb)]);
+    }
+}
+
+// ------------------------------------------------------------------ sweep
 // geo per direction (6 doubles): fx, fy (integer upwind shift in cells,
 // reduced modulo nx, ny: the box is periodic), ax, ay (fractional parts),
-// ds (path length between planes), up (1: Omega_z > 0)
-template <typename T, int VPT>
-__global__ void __launch_bounds__(1024, 1) k_sweep3d(BoxDev bx, const double *__restrict__ geo,
-                                                  const T *__restrict__ chi, const T *S,
-                                                  const double *__restrict__ tsrc, const void *xin,
-                                                  int x_is_float, void *yout, int y_is_float, int out,
-                                                  int inflow, const double *__restrict__ I_top,
-                                                  const double *__restrict__ I_bot) {
-  constexpr int FB = 32 / sizeof(T);
+// ds (path length between planes), up (1: Omega_z > 0).
+// chiN: opacity [npad / 4][npts][4] (npad = nn rounded up to 4, zero past nn),
+// so a CTA's FB <= 4 frequencies of consecutive cells are contiguous.
+// SL: source in the sweep layout, or null when the source is the thermal
+// term tsrc [npts][nn] (float64) broadcast over directions.
+// x, y: space-based layout; x unused for kOutI.
+template <typename T, int FB, int CPT, int CB, typename TX, typename TY>
+__global__ void __launch_bounds__(512) k_sweep3d(BoxDev bx, const double *__restrict__ geo,
+                                                 const T *__restrict__ chiN, int npad,
+                                                 const Pack<T, FB> *__restrict__ SL,
+                                                 const double *__restrict__ tsrc, const TX *__restrict__ x,
+                                                 TY *__restrict__ y, int out, int inflow,
+                                                 const double *__restrict__ I_top,
+                                                 const double *__restrict__ I_bot,
+                                                 const T *__restrict__ cW0, const T *__restrict__ cB) {
+  using P = Pack<T, FB>;
   extern __shared__ __align__(16) unsigned char sw_smem[];
-  T *Ip = reinterpret_cast<T *>(sw_smem);  // [plane][FB]
-  const int nd = bx.nd, nn = bx.nn, nx = bx.nx, ny = bx.ny, nz = bx.nz;
+  const int nx = bx.nx, ny = bx.ny, nz = bx.nz, nn = bx.nn, nd = bx.nd;
   const int plane = nx * ny;
   const int nfb = (nn + FB - 1) / FB;
-  const int d = blockIdx.x / nfb, f0 = (blockIdx.x % nfb) * FB;
-  const int nr = nd * nn;
+  P *sI = reinterpret_cast<P *>(sw_smem);
+  P *sS = sI + plane;
+  P *sC = sS + plane;
+  const int d = blockIdx.x / nfb, fb = blockIdx.x - d * nfb, f0 = fb * FB;
+  const int64_t npts = (int64_t)plane * nz;
+  const int64_t nr = (int64_t)nd * nn;
   const double *g = geo + 6 * d;
   const int fx = (int)g[0], fy = (int)g[1];
   const T ax = (T)g[2], ay = (T)g[3];
   const T hds = (T)(0.5 * g[4]);
-  const int up = g[5] > 0.5;
+  const bool up = g[5] > 0.5;
   const T w00 = ((T)1 - ay) * ((T)1 - ax), w01 = ((T)1 - ay) * ax, w10 = ay * ((T)1 - ax), w11 = ay * ax;
-  const int step = up ? -1 : 1;
-  const int k0 = up ? nz - 1 : 0;
-  const int nval = plane * FB;
-  const double *xd = static_cast<const double *>(xin);
-  const float *xf = static_cast<const float *>(xin);
-  double *yd = static_cast<double *>(yout);
-  float *yf = static_cast<float *>(yout);
-  auto emit = [&](int64_t k, T I) {
-    if (out == kOutI) {
-      if (y_is_float) yf[k] = (float)I;
-      else yd[k] = (double)I;
-    } else if (y_is_float && x_is_float) {
-      yf[k] = xf[k] - (float)I;
-    } else {
-      const double v = (x_is_float ? (double)xf[k] : xd[k]) - (double)I;
-      if (y_is_float) yf[k] = (float)v;
-      else yd[k] = v;
-    }
-  };
-  auto src = [&](int64_t p, int f) -> T {
-    return tsrc ? (T)tsrc[p * nn + f] : S[p * nr + (int64_t)d * nn + f];
-  };
-  const bool pow2 = (nx & (nx - 1)) == 0;
-  const int lgx = __ffs(nx) - 1;
-  // first plane: inflow (or zero)
-  for (int v = threadIdx.x; v < nval; v += blockDim.x) {
-    const int c = v / FB, fl = v - c * FB, f = f0 + fl;
-    T I0 = 0;
-    if (inflow && f < nn) I0 = (T)(up ? I_bot[f] : I_top[f]);
-    Ip[v] = I0;
-    if (f < nn) emit(((int64_t)k0 * plane + c) * nr + (int64_t)d * nn + f, I0);
-  }
-  __syncthreads();
-  for (int s = 1; s < nz; ++s) {
-    const int k = k0 + s * step, ku = k - step;
-    const int64_t pu = (int64_t)ku * plane, pk = (int64_t)k * plane;
-    T In[VPT];
+  const int step = up ? -1 : 1, k0 = up ? nz - 1 : 0;
+  const P *Sd = SL ? SL + ((int64_t)d * nfb + fb) * npts : nullptr;
+  const int ie = bx.ie;
+  // this thread's cells and their four upwind neighbours (the shift is the
+  // same for every plane), packed two 16-bit cell indices per word
+  uint32_t nb0[CPT], nb1[CPT];
 #pragma unroll
-    for (int i = 0; i < VPT; ++i) {
-      In[i] = 0;
-      const int v = threadIdx.x + i * blockDim.x;
-      if (v >= nval) continue;
-      const int c = v / FB, fl = v - c * FB, f = f0 + fl;
-      if (f >= nn) continue;
-      const int y = pow2 ? (c >> lgx) : c / nx, x = c - y * nx;
-      int x0 = x - fx, y0 = y - fy;
+  for (int i = 0; i < CPT; ++i) {
+    const int c = threadIdx.x + i * blockDim.x;
+    nb0[i] = nb1[i] = 0;
+    if (c < plane) {
+      const int yy = c / nx, xx = c - yy * nx;
+      int x0 = xx - fx, y0 = yy - fy;
       if (x0 < 0) x0 += nx;
       if (y0 < 0) y0 += ny;
       const int x1 = x0 == 0 ? nx - 1 : x0 - 1;
       const int y1 = y0 == 0 ? ny - 1 : y0 - 1;
-      const int c00 = y0 * nx + x0, c01 = y0 * nx + x1, c10 = y1 * nx + x0, c11 = y1 * nx + x1;
-      const int64_t pc = pk + c;
-      const T Iu = w00 * Ip[c00 * FB + fl] + w01 * Ip[c01 * FB + fl] + w10 * Ip[c10 * FB + fl] +
-                   w11 * Ip[c11 * FB + fl];
-      const T Su = w00 * src(pu + c00, f) + w01 * src(pu + c01, f) + w10 * src(pu + c10, f) +
-                   w11 * src(pu + c11, f);
-      const T cu = w00 * chi[(pu + c00) * nn + f] + w01 * chi[(pu + c01) * nn + f] +
-                   w10 * chi[(pu + c10) * nn + f] + w11 * chi[(pu + c11) * nn + f];
-      T e, a, b;
-      step_coef<T>(hds * (cu + chi[pc * nn + f]), bx.ie, e, a, b);
-      In[i] = e * Iu + a * Su + b * src(pc, f);
-      emit(pc * nr + (int64_t)d * nn + f, In[i]);
+      nb0[i] = (uint32_t)(y0 * nx + x0) | ((uint32_t)(y0 * nx + x1) << 16);
+      nb1[i] = (uint32_t)(y1 * nx + x0) | ((uint32_t)(y1 * nx + x1) << 16);
+    }
+  }
+  auto load_src = [&](int64_t p) -> P {
+    if (Sd) return Sd[p];
+    P r;
+#pragma unroll
+    for (int j = 0; j < FB; ++j) r.v[j] = f0 + j < nn ? cast_to<T>(tsrc[p * nn + f0 + j]) : T(0);
+    return r;
+  };
+  const T *chiB = chiN + (int64_t)(f0 >> 2) * npts * 4 + (f0 & 3);
+  auto load_chi = [&](int64_t p) -> P { return *reinterpret_cast<const P *>(chiB + p * 4); };
+  // precomputed step weights (1 - e^-d, w1/d) in blocks of 2 frequencies:
+  // [d][f / 2][p][f % 2]; the plane's opacity is then not needed
+  const bool pre = cW0 != nullptr;
+  const int64_t cbase = pre ? ((int64_t)d * ((nn + 1) / 2) + (f0 >> 1)) * npts * 2 + (f0 & 1) : 0;
+  // x and y of a cell: FB consecutive values, one vector access when aligned
+  const bool vec = nn % FB == 0;
+  using PX = Pack<TX, FB>;
+  using PY = Pack<TY, FB>;
+  // first plane: inflow (or zero)
+  {
+    P I0;
+#pragma unroll
+    for (int j = 0; j < FB; ++j)
+      I0.v[j] = (inflow && f0 + j < nn) ? (T)(up ? I_bot[f0 + j] : I_top[f0 + j]) : T(0);
+    const int64_t pk = (int64_t)k0 * plane;
+#pragma unroll
+    for (int i = 0; i < CPT; ++i) {
+      const int c = threadIdx.x + i * blockDim.x;
+      if (c >= plane) continue;
+      sI[c] = I0;
+      sS[c] = load_src(pk + c);
+      sC[c] = load_chi(pk + c);
+      const int64_t k = (pk + c) * nr + (int64_t)d * nn + f0;
+#pragma unroll
+      for (int j = 0; j < FB; ++j) {
+        if (f0 + j >= nn) continue;
+        if (out == kOutI) y[k + j] = cast_to<TY>(I0.v[j]);
+        else y[k + j] = cast_to<TY>(cast_to<T>(x[k + j]) - I0.v[j]);
+      }
+    }
+  }
+  __syncthreads();
+  for (int s = 1; s < nz; ++s) {
+    const int kp = k0 + s * step;
+    const int64_t pk = (int64_t)kp * plane;
+    P In[CPT];
+#pragma unroll
+    for (int i0 = 0; i0 < CPT; i0 += CB) {
+      // loads of CB cells issued together
+      P Sc[CB], Cc[CB];
+      TX xv[CB][FB];
+#pragma unroll
+      for (int u = 0; u < CB; ++u) {
+        const int c = threadIdx.x + (i0 + u) * blockDim.x;
+        const int cc = c < plane ? c : 0;
+        Sc[u] = load_src(pk + cc);
+        if (pre) {  // Cc holds (1 - e^-d) and the gathered opacity is unused; Sc.. the source
+          Cc[u] = *reinterpret_cast<const P *>(cW0 + cbase + (pk + cc) * 2);
+        } else {
+          Cc[u] = load_chi(pk + cc);
+        }
+        if (out != kOutI) {
+          const int64_t k = (pk + cc) * nr + (int64_t)d * nn + f0;
+          if (vec) {
+            const PX v = *reinterpret_cast<const PX *>(x + k);
+#pragma unroll
+            for (int j = 0; j < FB; ++j) xv[u][j] = v.v[j];
+          } else {
+#pragma unroll
+            for (int j = 0; j < FB; ++j) xv[u][j] = f0 + j < nn ? x[k + j] : TX(0);
+          }
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < CB; ++u) {
+        const int i = i0 + u;
+        const int c = threadIdx.x + i * blockDim.x;
+        if (c >= plane) continue;
+        const int c00 = nb0[i] & 0xffff, c01 = nb0[i] >> 16, c10 = nb1[i] & 0xffff, c11 = nb1[i] >> 16;
+        const P I00 = sI[c00], I01 = sI[c01], I10 = sI[c10], I11 = sI[c11];
+        const P S00 = sS[c00], S01 = sS[c01], S10 = sS[c10], S11 = sS[c11];
+        P C00, C01, C10, C11, Bc;
+        if (pre) {
+          Bc = *reinterpret_cast<const P *>(cB + cbase + (pk + c) * 2);
+        } else {
+          C00 = sC[c00], C01 = sC[c01], C10 = sC[c10], C11 = sC[c11];
+        }
+        const int64_t k = (pk + c) * nr + (int64_t)d * nn + f0;
+        PY yv;
+#pragma unroll
+        for (int j = 0; j < FB; ++j) {
+          const T Iu = w00 * I00.v[j] + w01 * I01.v[j] + w10 * I10.v[j] + w11 * I11.v[j];
+          const T Su = w00 * S00.v[j] + w01 * S01.v[j] + w10 * S10.v[j] + w11 * S11.v[j];
+          T e, a, b;
+          if (pre) {
+            const T w0 = Cc[u].v[j];
+            e = (T)1 - w0;
+            b = Bc.v[j];
+            a = w0 - b;
+          } else {
+            const T Cu = w00 * C00.v[j] + w01 * C01.v[j] + w10 * C10.v[j] + w11 * C11.v[j];
+            step_coef<T>(hds * (Cu + Cc[u].v[j]), ie, e, a, b);
+          }
+          const T I = fma(e, Iu, fma(a, Su, b * Sc[u].v[j]));
+          In[i].v[j] = I;
+          yv.v[j] = out == kOutI ? cast_to<TY>(I) : cast_to<TY>(cast_to<T>(xv[u][j]) - I);
+        }
+        if (vec) {
+          *reinterpret_cast<PY *>(y + k) = yv;
+        } else {
+#pragma unroll
+          for (int j = 0; j < FB; ++j)
+            if (f0 + j < nn) y[k + j] = yv.v[j];
+        }
+      }
     }
     __syncthreads();
 #pragma unroll
-    for (int i = 0; i < VPT; ++i) {
-      const int v = threadIdx.x + i * blockDim.x;
-      if (v < nval) Ip[v] = In[i];
+    for (int i = 0; i < CPT; ++i) {
+      const int c = threadIdx.x + i * blockDim.x;
+      if (c >= plane) continue;
+      sI[c] = In[i];
+      sS[c] = load_src(pk + c);
+      if (!pre) sC[c] = load_chi(pk + c);
     }
     __syncthreads();
   }
 }
 
-// Launch the 3D sweep; x/y may be float or double (the float64 path passes
-// double for both).  32 values per thread; threads per CTA = plane*FB/32.
-template <typename T>
-static int sweep3d_launch(rt_handle *h, const T *chi, const T *S, const double *tsrc, const void *x,
-                          bool xf, void *y, bool yf, int out, bool inflow, cudaStream_t s) {
+// Step weights of the float64 sweep, once per handle: for every (direction,
+// point, frequency) the optical depth of the step from the upwind plane,
+// 0.5 (chi_u + chi_c) ds with chi_u bilinear at the upwind point, and from it
+// w0 = 1 - e^-d (expm1) and w1/d (series below 0.1), or the implicit-Euler
+// pair (d/(1+d), d/(1+d)).  Layout [d][f / 2][p][f % 2]; the first plane of
+// each direction (no step) holds zeros.
+__global__ void k_box_coef64(BoxDev bx, const double *__restrict__ geo, const double *__restrict__ chiN,
+                             double *__restrict__ W0, double *__restrict__ Bt) {
+  const int nx = bx.nx, ny = bx.ny, nz = bx.nz, nn = bx.nn, nd = bx.nd;
+  const int plane = nx * ny;
+  const int64_t npts = (int64_t)plane * nz;
+  const int nfb2 = (nn + 1) / 2;
+  const int64_t total = (int64_t)nd * npts * nfb2 * 2;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int j = (int)(i & 1);
+    const int64_t r = i >> 1;
+    const int64_t p = r % npts;
+    const int64_t db = r / npts;
+    const int fb2 = (int)(db % nfb2), d = (int)(db / nfb2);
+    const int f = 2 * fb2 + j;
+    double w0 = 0.0, bt = 0.0;
+    const double *g = geo + 6 * d;
+    const bool up = g[5] > 0.5;
+    const int kp = (int)(p / plane), c = (int)(p - (int64_t)kp * plane);
+    const int k0 = up ? nz - 1 : 0, step = up ? -1 : 1;
+    if (f < nn && kp != k0) {
+      const int fx = (int)g[0], fy = (int)g[1];
+      const double ax = g[2], ay = g[3];
+      const int yy = c / nx, xx = c - yy * nx;
+      int x0 = xx - fx, y0 = yy - fy;
+      if (x0 < 0) x0 += nx;
+      if (y0 < 0) y0 += ny;
+      const int x1 = x0 == 0 ? nx - 1 : x0 - 1, y1 = y0 == 0 ? ny - 1 : y0 - 1;
+      const int64_t pu = (int64_t)(kp - step) * plane;
+      auto chi = [&](int64_t q) { return chiN[((int64_t)(f >> 2) * npts + q) * 4 + (f & 3)]; };
+      const double cu = (1 - ay) * (1 - ax) * chi(pu + y0 * nx + x0) + (1 - ay) * ax * chi(pu + y0 * nx + x1) +
+                        ay * (1 - ax) * chi(pu + y1 * nx + x0) + ay * ax * chi(pu + y1 * nx + x1);
+      const double dt = 0.5 * g[4] * (cu + chi(p));
+      double e, a, b;
+      step_coef<double>(dt, bx.ie, e, a, b);
+      w0 = bx.ie ? b : -expm1(-dt);
+      bt = b;
+    }
+    W0[i] = w0;
+    Bt[i] = bt;
+  }
+}
+
+// ------------------------------------------------------------ host side
+// Launch shape of the sweep for one precision: FB frequencies per CTA and
+// CPT cells per thread (at most 512 threads).  The shapes are those whose
+// registers stay within 128 per thread without spills (float32: FB = 4 up to
+// CPT = 4, FB <= 2 up to 8; float64: FB = 2 up to 2, FB = 1 up to 8).  FB is
+// the largest whose three plane arrays fit the shared memory and whose plane
+// fits 512 threads, not wider than the frequencies need; rt_autotune may cap
+// FB and raise CPT.
+static int box_cpt_max(bool fp64, int fb) { return fp64 ? (fb == 2 ? 2 : 8) : (fb == 4 ? 4 : 8); }
+
+static void box_shape(const rt_handle *h, bool fp64, int &fb, int &cpt) {
+  const int plane = h->box.nx * h->box.ny;
+  const int esz = fp64 ? 8 : 4;
+  const int fbmax = fp64 ? 2 : 4;
+  fb = h->tune.box_fb > 0 ? std::min(fbmax, h->tune.box_fb) : fbmax;
+  while (fb > 1 && (fb / 2 >= h->box.nn || 3ll * plane * fb * esz > kBoxSmemMax || plane > 512 * box_cpt_max(fp64, fb)))
+    fb /= 2;
+  cpt = 1;
+  while ((plane + cpt - 1) / cpt > 512) cpt *= 2;
+  if (h->tune.box_cpt > cpt) cpt = std::min(h->tune.box_cpt, box_cpt_max(fp64, fb));
+}
+
+void box_effective_shape(const rt_handle *h, bool fp64, int &fb, int &cpt) { box_shape(h, fp64, fb, cpt); }
+
+static int box_fb(const rt_handle *h, bool fp64) {
+  int fb, cpt;
+  box_shape(h, fp64, fb, cpt);
+  return fb;
+}
+
+bool box_plane_fits(int nx, int ny) {
+  const int64_t plane = (int64_t)nx * ny;
+  return plane <= 8 * 512 && plane < 65536 && 3 * plane * 8 <= kBoxSmemMax;
+}
+
+int64_t box_scratch_elems(const rt_handle *h, bool fp64) {
+  const int fb = box_fb(h, fp64);
+  const int64_t npts = (int64_t)h->box.nx * h->box.ny * h->box.nz;
+  const int64_t nfb = (h->box.nn + fb - 1) / fb;
+  return npts * h->box.nd * nfb * fb;
+}
+
+template <typename T, int FB, int CPT, typename TX, typename TY>
+static int sweep3d_run(rt_handle *h, const T *chiN, const void *S, const double *tsrc, const TX *x, TY *y, int out,
+                       bool inflow, cudaStream_t s) {
   const BoxDev &bx = h->box;
-  constexpr int FB = 32 / sizeof(T);
-  constexpr int VPT = 32;
   const int plane = bx.nx * bx.ny;
-  const int nval = plane * FB;
   const int nfb = (bx.nn + FB - 1) / FB;
-  const int grid = bx.nd * nfb;
-  const size_t smem = (size_t)nval * sizeof(T);
-  int nt = (nval + VPT - 1) / VPT;
-  nt = (nt + 31) / 32 * 32;
-  if (nt > 1024 || plane >= 65536) return (int)cudaErrorInvalidConfiguration;
-  cudaFuncSetAttribute(k_sweep3d<T, VPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_sweep3d<T, VPT><<<grid, nt, smem, s>>>(bx, h->d_geo, chi, S, tsrc, x, xf ? 1 : 0, y, yf ? 1 : 0, out,
-                                           inflow ? 1 : 0, h->d_Itop, h->d_Ibot);
+  const int nt = std::min(512, ((plane + CPT - 1) / CPT + 31) / 32 * 32);
+  if ((int64_t)nt * CPT < plane) return (int)cudaErrorInvalidConfiguration;
+  const size_t smem = (size_t)3 * plane * FB * sizeof(T);
+  constexpr int CB = (8 / FB) < CPT ? (8 / FB) : CPT;  // cells whose loads are issued together
+  auto kern = k_sweep3d<T, FB, CPT, CB, TX, TY>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return (int)e;
+  const T *cw = nullptr, *cb = nullptr;
+  if (sizeof(T) == 8 && h->box_w064) {
+    cw = reinterpret_cast<const T *>(h->box_w064);
+    cb = reinterpret_cast<const T *>(h->box_bt64);
+  }
+  kern<<<bx.nd * nfb, nt, smem, s>>>(bx, h->d_geo, chiN, h->box_npad, static_cast<const Pack<T, FB> *>(S), tsrc, x,
+                                     y, out, inflow ? 1 : 0, h->d_Itop, h->d_Ibot, cw, cb);
   return (int)cudaGetLastError();
 }
 
-int launch_sweep3d(rt_handle *h, bool fp64, const void *S, const double *tsrc, const void *x, bool xf,
-                   void *y, bool yf, int out, bool inflow, cudaStream_t s) {
-  if (fp64)
-    return sweep3d_launch<double>(h, h->chi64, static_cast<const double *>(S), tsrc, x, xf, y, yf, out,
-                                  inflow, s);
-  return sweep3d_launch<float>(h, h->chi32, static_cast<const float *>(S), tsrc, x, xf, y, yf, out, inflow,
-                               s);
+template <typename T, int FB, typename TX, typename TY>
+static int sweep3d_cpt(rt_handle *h, int cpt, const T *chiN, const void *S, const double *tsrc, const TX *x, TY *y,
+                       int out, bool inflow, cudaStream_t s) {
+  constexpr bool f64 = sizeof(T) == 8;
+  constexpr int cmax = f64 ? (FB == 2 ? 2 : 8) : (FB == 4 ? 4 : 8);
+  if (cpt <= 1) return sweep3d_run<T, FB, 1>(h, chiN, S, tsrc, x, y, out, inflow, s);
+  if (cpt == 2 || cmax == 2) return sweep3d_run<T, FB, 2>(h, chiN, S, tsrc, x, y, out, inflow, s);
+  if constexpr (cmax >= 4) {
+    if (cpt == 4 || cmax == 4) return sweep3d_run<T, FB, 4>(h, chiN, S, tsrc, x, y, out, inflow, s);
+  }
+  if constexpr (cmax >= 8) return sweep3d_run<T, FB, 8>(h, chiN, S, tsrc, x, y, out, inflow, s);
+  return (int)cudaErrorInvalidConfiguration;
+}
+
+template <typename T, typename TX, typename TY>
+static int sweep3d(rt_handle *h, const void *S, const double *tsrc, const TX *x, TY *y, int out, bool inflow,
+                   cudaStream_t s) {
+  constexpr bool f64 = sizeof(T) == 8;
+  const T *chiN = reinterpret_cast<const T *>(f64 ? (const void *)h->chi64 : (const void *)h->chi32);
+  int fb, cpt;
+  box_shape(h, f64, fb, cpt);
+  if constexpr (!f64) {
+    if (fb == 4) return sweep3d_cpt<T, 4>(h, cpt, chiN, S, tsrc, x, y, out, inflow, s);
+  }
+  if (fb == 2) return sweep3d_cpt<T, 2>(h, cpt, chiN, S, tsrc, x, y, out, inflow, s);
+  return sweep3d_cpt<T, 1>(h, cpt, chiN, S, tsrc, x, y, out, inflow, s);
+}
+
+template <typename T, typename TX>
+static int sigma_box(rt_handle *h, const Tables<T> &tb, const TX *x, T *S, int fb_out, cudaStream_t s) {
+  const ColDev &c = h->h_cols[0];
+  const int64_t npts = (int64_t)h->box.nx * h->box.ny * h->box.nz;
+  const int nw = kBoxSigNT / 32;
+  const int grid = (int)std::min<int64_t>((npts + nw - 1) / nw, (int64_t)h->n_sm * 16);
+  if (c.psi_off >= 0) {
+    k_sigma_box_dense<T, TX><<<grid, kBoxSigNT, 0, s>>>(c, tb, npts, x, S, fb_out);
+    return (int)cudaGetLastError();
+  }
+  const bool rw_cached = !c.rdiag && (int64_t)c.nn * c.nn * sizeof(T) <= kBoxRwCache;
+  const int rw_len = c.rdiag ? c.nn : (rw_cached ? c.nn * c.nn : 0);
+  auto launch = [&](auto kern, int kr) -> int {
+    const size_t smem = sizeof(T) * ((size_t)2 * c.nd * kr + ((rw_len + 1) & ~1) + (size_t)nw * kr * c.nn);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return (int)e;
+    kern<<<grid, kBoxSigNT, smem, s>>>(c, tb, npts, x, S, fb_out);
+    return (int)cudaGetLastError();
+  };
+  const int fl = (c.nn + 31) / 32;
+  if (c.rp <= 2) {
+    if (fl <= 1) return launch(k_sigma_box<T, TX, 2, 1>, 2);
+    if (fl <= 2) return launch(k_sigma_box<T, TX, 2, 2>, 2);
+    return launch(k_sigma_box<T, TX, 2, 4>, 2);
+  }
+  if (fl <= 1) return launch(k_sigma_box<T, TX, 6, 1>, 6);
+  if (fl <= 2) return launch(k_sigma_box<T, TX, 6, 2>, 6);
+  return launch(k_sigma_box<T, TX, 6, 4>, 6);
+}
+
+// the box Sigma holds the rank and frequencies in registers: rank <= 6 and
+// n_nu <= 128 (four frequencies per lane)
+bool box_sigma_fits(const rt_desc *d, int rp) {
+  const size_t esz = 8;
+  const int nn = d->n_nu;
+  const bool rw_cached = (int64_t)nn * nn * esz <= kBoxRwCache;
+  const size_t smem = esz * ((size_t)2 * d->n_dir * 6 + (rw_cached ? nn * nn + 1 : 1) + (size_t)(kBoxSigNT / 32) * 6 * nn);
+  return rp <= 6 && nn <= 128 && smem <= 200 * 1024;
+}
+
+template <typename T, typename TX, typename TY>
+static int box_apply_t(rt_handle *h, const Tables<T> &tb, int op, const TX *x, TY *y, cudaStream_t s, void *S) {
+  const int fb = box_fb(h, sizeof(T) == 8);
+  const int64_t npts = (int64_t)h->box.nx * h->box.ny * h->box.nz;
+  const int64_t len = h->E;
+  const int cgrid = (int)std::min<int64_t>((len + 255) / 256, 16 * 152);
+  T *St = static_cast<T *>(S);
+  int e = 0;
+  switch (op) {
+    case 0:  // y = x - Lambda Sigma x
+      if ((e = sigma_box<T, TX>(h, tb, x, St, fb, s))) return e;
+      return sweep3d<T, TX, TY>(h, St, nullptr, x, y, kOutAminus, false, s);
+    case 1:  // y = Lambda x
+      if constexpr (sizeof(TX) != 8) return (int)cudaErrorInvalidValue;
+      else {
+        k_box_to_sweep<T><<<(int)std::min<int64_t>(npts, 65535), 256, 0, s>>>(x, St, npts, h->box.nd, h->box.nn, fb);
+        return sweep3d<T, TX, TY>(h, St, nullptr, nullptr, y, kOutI, false, s);
+      }
+    case 2:  // y = Sigma x (space-based layout, float64 out)
+      if constexpr (sizeof(TY) != 8) return (int)cudaErrorInvalidValue;
+      else {
+        if ((e = sigma_box<T, TX>(h, tb, x, St, fb, s))) return e;
+        k_box_from_sweep<T><<<(int)std::min<int64_t>(npts, 65535), 256, 0, s>>>(St, y, npts, h->box.nd, h->box.nn, fb);
+        return (int)cudaGetLastError();
+      }
+    default:  // y = Lambda t + I_in
+      if (h->d_tsrc) return sweep3d<T, TX, TY>(h, nullptr, h->d_tsrc, nullptr, y, kOutI, true, s);
+      cudaMemsetAsync(St, 0, box_scratch_elems(h, sizeof(T) == 8) * sizeof(T), s);
+      return sweep3d<T, TX, TY>(h, St, nullptr, nullptr, y, kOutI, true, s);
+  }
+}
+
+// Operators of a 3D box; x (and y) are float32 when xf (yf), else float64;
+// the float64 operator needs both in float64.  scratch: the source function
+// (box_scratch_elems of the operator's precision), or null for the handle's.
+int box_apply(rt_handle *h, int op, bool fp64, const void *x, bool xf, void *y, bool yf, cudaStream_t s,
+              void *scratch) {
+  void *S = scratch ? scratch : h->apply_S;
+  if (fp64 || h->precision == 0) {
+    if (xf || yf) return (int)cudaErrorInvalidValue;
+    return box_apply_t<double, double, double>(h, tables64(h), op, static_cast<const double *>(x),
+                                               static_cast<double *>(y), s, S);
+  }
+  const Tables<float> tb = tables32(h);
+  if (xf && yf)
+    return box_apply_t<float, float, float>(h, tb, op, static_cast<const float *>(x), static_cast<float *>(y), s, S);
+  if (!xf && !yf)
+    return box_apply_t<float, double, double>(h, tb, op, static_cast<const double *>(x), static_cast<double *>(y),
+                                              s, S);
+  return (int)cudaErrorInvalidValue;
+}
+
+// Opacity in the sweep's padded per-point layout, both precisions.
+int box_prepare(rt_handle *h, const double *chi) {
+  const int nn = h->box.nn;
+  const int npad = (nn + 3) / 4 * 4;
+  const int64_t npts = (int64_t)h->box.nx * h->box.ny * h->box.nz;
+  h->box_npad = npad;
+  std::vector<double> c64((size_t)npts * npad, 0.0);
+  std::vector<float> c32((size_t)npts * npad, 0.f);
+  for (int64_t p = 0; p < npts; ++p)
+    for (int f = 0; f < nn; ++f) {
+      const size_t k = ((size_t)(f >> 2) * npts + p) * 4 + (f & 3);  // [f / 4][p][f % 4]
+      c64[k] = chi[(size_t)p * nn + f];
+      c32[k] = (float)chi[(size_t)p * nn + f];
+    }
+  cudaError_t e = cudaMalloc(&h->chi64, c64.size() * 8);
+  if (e == cudaSuccess) e = cudaMemcpy(h->chi64, c64.data(), c64.size() * 8, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMalloc(&h->chi32, c32.size() * 4);
+  if (e == cudaSuccess) e = cudaMemcpy(h->chi32, c32.data(), c32.size() * 4, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return (int)e;
+  // float64 step weights, when they take at most a quarter of the free memory
+  const int64_t ncoef = (int64_t)h->box.nd * npts * ((nn + 1) / 2) * 2;
+  size_t free_b = 0, total_b = 0;
+  if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess && (double)ncoef * 16.0 <= 0.25 * (double)free_b) {
+    e = cudaMalloc(&h->box_w064, (size_t)ncoef * 8);
+    if (e == cudaSuccess) e = cudaMalloc(&h->box_bt64, (size_t)ncoef * 8);
+    if (e != cudaSuccess) return (int)e;
+    const int grid = (int)std::min<int64_t>((ncoef + 255) / 256, 152 * 32);
+    k_box_coef64<<<grid, 256>>>(h->box, h->d_geo, h->chi64, h->box_w064, h->box_bt64);
+    e = cudaGetLastError();
+  }
+  return (int)e;
 }
 
 }  // namespace rt

@@ -5,6 +5,7 @@
 #include <string>
 #include <vector>
 
+#include "../../include/rt_gb300.h"
 #include "rt_internal.cuh"
 
 namespace rt {
@@ -33,7 +34,11 @@ struct Tune {
   int sigma_pts = 0;     // cap on points per Sigma tile: 4, 8, or 0 (as many as fit)
   double ms = 0.0;       // apply time measured for this choice
   int from_cache = 0;
+  int box_fb = 0;        // 3D sweep: cap on frequencies per CTA (0: largest that fits)
+  int box_cpt = 0;       // 3D sweep: cells per thread (0: 8, adjusted to the plane)
 };
+
+constexpr int kBoxSmemMax = 220 * 1024;  // shared-memory budget of one 3D sweep CTA
 
 // 3D box geometry (device-side copy of the scalars)
 struct BoxDev {
@@ -94,8 +99,10 @@ struct rt_handle {
   rt::Tune tune{};
   rt::BoxDev box{};
   double *d_geo = nullptr;
-  double *chi64 = nullptr;
+  double *chi64 = nullptr;   // 3D: opacity [n_pts][box_npad], zero past n_nu
   float *chi32 = nullptr;
+  int box_npad = 0;          // 3D: frequencies rounded up to a multiple of 4
+  double *box_w064 = nullptr, *box_bt64 = nullptr;  // 3D: float64 step weights, or null
   double *g_part = nullptr, *g_red = nullptr, *g_coef = nullptr, *g_r = nullptr;
   int64_t stage_len = 0;
   bool has_dense = false;
@@ -136,9 +143,17 @@ int launch_sigma_dense_tc(rt_handle *h, bool x_is_float, const void *x, void *S,
 int tc_all_columns(const rt_handle *h);
 struct TcJob;
 int tc_prepare(rt_handle *h, const std::vector<double> &psiwT);
-int launch_sweep3d(rt_handle *h, bool fp64, const void *S, const double *tsrc, const void *x, bool xf,
-                   void *y, bool yf, int out, bool inflow, cudaStream_t s);
-int apply_box(rt_handle *h, int op, bool fp64, const void *x, bool xf, void *y, bool yf, cudaStream_t s);
+// 3D boxes (rt_box.cu)
+int box_apply(rt_handle *h, int op, bool fp64, const void *x, bool xf, void *y, bool yf, cudaStream_t s,
+              void *scratch);
+inline int apply_box(rt_handle *h, int op, bool fp64, const void *x, bool xf, void *y, bool yf, cudaStream_t s) {
+  return box_apply(h, op, fp64, x, xf, y, yf, s, nullptr);
+}
+int box_prepare(rt_handle *h, const double *chi);
+int64_t box_scratch_elems(const rt_handle *h, bool fp64);
+bool box_plane_fits(int nx, int ny);
+bool box_sigma_fits(const rt_desc *d, int rp);
+void box_effective_shape(const rt_handle *h, bool fp64, int &fb, int &cpt);
 int launch_bicgstab(rt_handle *h, const double *b, double *x, double tol, int max_outer, int max_iter,
                     int use_x0, cudaStream_t s);
 bool bicgstab_fits(const rt_handle *h);

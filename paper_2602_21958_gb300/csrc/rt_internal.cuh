@@ -88,6 +88,32 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double *red, double *
   __syncthreads();
 }
 
+// ------------------------------------------------- float64 <-> float32 casts
+// On GB300 the conversion instructions between float64 and float32 run on the
+// float64 pipe (about 0.6 T/s per GPU, measured), slower than streaming the
+// values from HBM.  These casts work on the IEEE-754 bit fields with integer
+// operations instead; values outside the float32 normal range (and zeros,
+// subnormals, inf, nan) take the conversion instruction.
+// narrow_f32: round to nearest even, as the cvt.rn.f32.f64 it replaces.
+__device__ __forceinline__ float narrow_f32(double v) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  const uint32_t hi = (uint32_t)(b >> 32), lo = (uint32_t)b;
+  const uint32_t e = (hi >> 20) & 0x7ffu;
+  if (e - 897u > 253u) return (float)v;  // biased exponent outside [897, 1150]
+  uint32_t r = ((e - 896u) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
+  const uint32_t rem = lo & 0x1fffffffu;
+  r += (rem > 0x10000000u || (rem == 0x10000000u && (r & 1u))) ? 1u : 0u;
+  return __uint_as_float(r | (hi & 0x80000000u));
+}
+// widen_f64: exact, as cvt.f64.f32.
+__device__ __forceinline__ double widen_f64(float v) {
+  const uint32_t u = __float_as_uint(v);
+  const uint32_t e = (u >> 23) & 0xffu;
+  if (e - 1u > 253u) return (double)v;  // zero, subnormal, inf, nan
+  const uint32_t hi = (u & 0x80000000u) | ((e + 896u) << 20) | ((u & 0x7fffffu) >> 3);
+  return __hiloint2double((int)hi, (int)(u << 29));
+}
+
 template <typename T> __device__ __forceinline__ T to(double v) { return (T)v; }
 template <typename T> __device__ __forceinline__ T to(float v) { return (T)v; }
 template <typename T> __device__ __forceinline__ T to(__half v) { return (T)__half2float(v); }

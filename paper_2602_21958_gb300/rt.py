@@ -54,7 +54,8 @@ EXPORTS = ("rt_create", "rt_create_batch", "rt_vector_length", "rt_apply", "rt_a
 
 class rt_tune_info(C.Structure):
     _fields_ = [("ray_block", C.c_int32), ("ahead", C.c_int32), ("sigma_points", C.c_int32),
-                ("from_cache", C.c_int32), ("ms_best", C.c_double), ("ms_default", C.c_double)]
+                ("from_cache", C.c_int32), ("ms_best", C.c_double), ("ms_default", C.c_double),
+                ("box_fb", C.c_int32), ("box_cpt", C.c_int32)]
 
 _lib = None
 
@@ -205,7 +206,8 @@ class Handle:
         t = rt_tune_info()
         _check(load().rt_autotune(self._h, 1 if force else 0, C.byref(t), _stream_ptr(stream)))
         return {"ray_block": t.ray_block, "ahead": t.ahead, "sigma_points": t.sigma_points,
-                "from_cache": bool(t.from_cache), "ms_best": t.ms_best, "ms_default": t.ms_default}
+                "from_cache": bool(t.from_cache), "ms_best": t.ms_best, "ms_default": t.ms_default,
+                "box_fb": t.box_fb, "box_cpt": t.box_cpt}
 
     def rt_solve(self, b, x, tol: float = 1e-11, tol_inner: float = 0.1, restart: Optional[int] = None,
                  max_outer: int = 50, use_x0: bool = False, stream=None, per_instance: bool = False,

@@ -466,19 +466,21 @@ def c5_random_rhs(ci: int, rhs: int, n: int, seed: Optional[int] = None) -> np.n
 
 
 def box_3d(n: int, order: int, n_nu: int, kernel: str, eps: float, seed: int,
-           corr: float = 4.0, name: str = "") -> Problem:
-    """Periodic-in-x,y box of n^3 unit cells, level-symmetric S_order directions,
-    dipole phase, lognormal opacity kappa(p) phi(nu), open top (I=0) and bottom
-    (I=B=1), gamma = (1-eps)/phi, t = eps B."""
+           corr: float = 4.0, name: str = "", nz: Optional[int] = None) -> Problem:
+    """Periodic-in-x,y box of n x n x nz unit cells (nz = n by default),
+    level-symmetric S_order directions, dipole phase, lognormal opacity
+    kappa(p) phi(nu), open top (I=0) and bottom (I=B=1), gamma = (1-eps)/phi,
+    t = eps B."""
+    nz = n if nz is None else nz
     rng = np.random.Generator(np.random.PCG64(seed))
-    kappa = lognormal_opacity((n, n, n), corr, rng).ravel()
+    kappa = lognormal_opacity((nz, n, n), corr, rng).ravel()
     dirs, wd = level_symmetric(order)
     x, wn, phi, R = line_data(n_nu, kernel)
-    npts = n ** 3
+    npts = n * n * nz
     chi = kappa[:, None] * phi[None, :]
     gamma = np.tile((1.0 - eps) / phi, (npts, 1))
     t_src = np.full((npts, n_nu), eps * 1.0)
-    return Problem(dims=3, nx=n, ny=n, nz=n, z=np.array([1.0, 1.0, 1.0]), dirs=dirs,
+    return Problem(dims=3, nx=n, ny=n, nz=nz, z=np.array([1.0, 1.0, 1.0]), dirs=dirs,
                    w_dir=wd, w_nu=wn, chi=chi, gamma=gamma, P=dipole_3d(dirs), R=R,
                    t_src=t_src, I_top=np.zeros(n_nu), I_bot=np.ones(n_nu),
                    formal_solver=FS_SCL, name=name)
