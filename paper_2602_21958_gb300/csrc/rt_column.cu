@@ -387,8 +387,8 @@ __global__ void __launch_bounds__(kNT, 1) k_solve(SolveParams p) {
         bpe += 0.0;
       } else {
         sigma_column<double, double>(c, p.t64, x, S64, sm, 4 * kSigBuf);
-        double a[1] = {sweep_column<double, double, double, 2>(c, p.t64, p.cm, S64, nullptr, x, bv, S64,
-                                                            kOutResid, false)};
+        double a[1] = {sweep_column<double, double, double, 2, kOutResid>(c, p.t64, p.cm, S64, nullptr, x, bv,
+                                                                           S64, false)};
         block_sum<1>(a, red, outb);
         rn = sqrt(a[0]);
         rsrc = S64;
@@ -409,7 +409,7 @@ __global__ void __launch_bounds__(kNT, 1) k_solve(SolveParams p) {
         TL *vj = Vslot + (int64_t)j * ldv;
         TL *w = Vslot + (int64_t)(j + 1) * ldv;
         sigma_column<TL, TL>(c, tl, vj, SL, reinterpret_cast<TL *>(sm), 4 * kSigBuf * (int)(8 / sizeof(TL)));
-        sweep_column<TL, TL, TL, sizeof(TL) == 8 ? 2 : 4>(c, tl, p.cm, SL, nullptr, vj, nullptr, w, kOutAminus, false);
+        sweep_column<TL, TL, TL, sizeof(TL) == 8 ? 2 : 4, kOutAminus>(c, tl, p.cm, SL, nullptr, vj, nullptr, w, false);
         __syncthreads();
         bpe += 5.0 * sz;  // v, S, S, v, w
         const double ww = cta_dots<TL>(Vslot, ldv, j, w, n, h, red, outb);
@@ -999,8 +999,8 @@ __global__ void __launch_bounds__(kNT, 1) k_solve_nested(SolveParams p) {
         rsrc = bv;
       } else {
         sigma_column<double, double>(c, p.t64, x, S64, sm, 4 * kSigBuf);
-        double a[1] = {sweep_column<double, double, double, 2>(c, p.t64, p.cm, S64, nullptr, x, bv, S64,
-                                                            kOutResid, false)};
+        double a[1] = {sweep_column<double, double, double, 2, kOutResid>(c, p.t64, p.cm, S64, nullptr, x, bv,
+                                                                           S64, false)};
         block_sum<1>(a, red, outb);
         rn = sqrt(a[0]);
         rsrc = S64;
@@ -1045,7 +1045,7 @@ __global__ void __launch_bounds__(kNT, 1) k_solve_nested(SolveParams p) {
             sigma_column<float, __half>(c, p.t32, uj, S32, reinterpret_cast<float *>(sm), 8 * kSigBuf, rw_c);
           // Arnoldi on K = Lambda Sigma (A = Id - K, same Krylov space): the
           // sweep emits K u_j and needs no read of u_j
-          sweep_column<float, __half, float, 4>(c, p.t32, p.cm, S32, nullptr, uj, nullptr, W32, kOutI, false);
+          sweep_column<float, __half, float, 4, kOutI>(c, p.t32, p.cm, S32, nullptr, uj, nullptr, W32, false);
           __syncthreads();
           bpe += 14.0;
           const double hn = arnoldi16(U, ldv, j, W32, n, h, h2, hf32, red, outb, bpe);
@@ -1085,7 +1085,7 @@ __global__ void __launch_bounds__(kNT, 1) k_solve_nested(SolveParams p) {
         // is e_i + h)
         double *w = Vo + (int64_t)(i + 1) * ldv;
         sigma_column<double, float>(c, p.t64, zi, S64, sm, 4 * kSigBuf);
-        sweep_column<double, float, double, 2>(c, p.t64, p.cm, S64, nullptr, zi, vi, w, kOutAminusB, false);
+        sweep_column<double, float, double, 2, kOutAminusB>(c, p.t64, p.cm, S64, nullptr, zi, vi, w, false);
         __syncthreads();
         bpe += 4.0 + 8.0 + 8.0 + 4.0 + 8.0 + 8.0;
         const double hn = arnoldi_orth<double>(Vo, ldv, i, n, h, h2, hf64, red, outb, bpe, 0.05);
@@ -1264,13 +1264,12 @@ __global__ void __launch_bounds__(kNT, 1) k_solve_bicgstab(SolveParams p) {
     double *x = p.x + rhs * p.E + c.x_off;
     auto apply = [&](const double *X, double *Y) {  // Y = A X, float64
       sigma_column<double, double>(c, p.t64, X, S64, sm, 4 * kSigBuf);
-      sweep_column<double, double, double, 2>(c, p.t64, p.cm, S64, nullptr, X, nullptr, Y, kOutAminus, false);
+      sweep_column<double, double, double, 2, kOutAminus>(c, p.t64, p.cm, S64, nullptr, X, nullptr, Y, false);
       __syncthreads();
     };
     auto true_resid = [&]() -> double {  // r = b - A x, returns ||r||
       sigma_column<double, double>(c, p.t64, x, S64, sm, 4 * kSigBuf);
-      double a[1] = {sweep_column<double, double, double, 2>(c, p.t64, p.cm, S64, nullptr, x, bv, r, kOutResid,
-                                                             false)};
+      double a[1] = {sweep_column<double, double, double, 2, kOutResid>(c, p.t64, p.cm, S64, nullptr, x, bv, r, false)};
       block_sum<1>(a, red, outb);
       return sqrt(a[0]);
     };

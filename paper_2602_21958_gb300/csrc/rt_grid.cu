@@ -19,6 +19,17 @@ constexpr int kGDots = 8;    // basis vectors per pass of the projection kernel
 
 int grid_ctas(const rt_handle *h) { return 2 * (h->n_sm > 0 ? h->n_sm : 152); }
 
+// The vector kernels below stream whole basis vectors (up to 10 GB each for
+// a 64^3 box): every thread takes kGE elements at a grid stride and issues
+// the loads of all of them (and of a group of basis rows) before the
+// arithmetic, so enough bytes are in flight to keep HBM busy; indices past n
+// are clamped (re-reads of the last element, contributions dropped).
+// Products are summed in TL over a thread's elements of kGWiden iterations
+// before one float64 add (float64 adds run at 1/73 of the float32 rate).
+constexpr int kGE = 4;      // elements per thread per iteration
+constexpr int kGWiden = 4;  // iterations summed in TL before a float64 add
+constexpr int kGRows = 4;   // basis rows per group in the update kernels
+
 // partial[blockIdx][u] = sum over this CTA's elements of V_{i0+u} . w  (u < cnt),
 // partial[blockIdx][kGDots] = w . w (when with_norm)
 template <typename TL>
@@ -27,16 +38,48 @@ __global__ void __launch_bounds__(kGT) k_gdots(const TL *V, int64_t ldv, int i0,
   __shared__ double red[(kGT / 32) * (kGDots + 1)];
   __shared__ double outb[kGDots + 1];
   double acc[kGDots + 1];
+  TL part[kGDots + 1];
 #pragma unroll
-  for (int u = 0; u <= kGDots; ++u) acc[u] = 0.0;
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
-       k += (int64_t)gridDim.x * blockDim.x) {
-    const TL wk = w[k];
+  for (int u = 0; u <= kGDots; ++u) {
+    acc[u] = 0.0;
+    part[u] = 0;
+  }
+  const TL *vp[kGDots];
+#pragma unroll
+  for (int u = 0; u < kGDots; ++u) vp[u] = V + (int64_t)(i0 + min(u, cnt - 1)) * ldv;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  int it = 0;
+  for (int64_t k0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k0 < n; k0 += kGE * stride) {
+    TL wv[kGE], vv[kGDots][kGE];
+#pragma unroll
+    for (int e = 0; e < kGE; ++e) {
+      const int64_t k = min(k0 + e * stride, n - 1);
+      wv[e] = w[k];
+#pragma unroll
+      for (int u = 0; u < kGDots; ++u) vv[u][e] = vp[u][k];
+    }
+#pragma unroll
+    for (int e = 0; e < kGE; ++e)
+      if (k0 + e * stride >= n) wv[e] = 0;
 #pragma unroll
     for (int u = 0; u < kGDots; ++u)
-      if (u < cnt) acc[u] += (double)(V[(int64_t)(i0 + u) * ldv + k] * wk);
-    if (with_norm) acc[kGDots] += (double)(wk * wk);
+#pragma unroll
+      for (int e = 0; e < kGE; ++e) part[u] = fma(vv[u][e], wv[e], part[u]);
+    if (with_norm) {
+#pragma unroll
+      for (int e = 0; e < kGE; ++e) part[kGDots] = fma(wv[e], wv[e], part[kGDots]);
+    }
+    if (++it == kGWiden) {
+      it = 0;
+#pragma unroll
+      for (int u = 0; u <= kGDots; ++u) {
+        acc[u] += (double)part[u];
+        part[u] = 0;
+      }
+    }
   }
+#pragma unroll
+  for (int u = 0; u <= kGDots; ++u) acc[u] += (double)part[u];
   block_sum<kGDots + 1>(acc, red, outb);
   if (threadIdx.x <= kGDots) partial[(int64_t)blockIdx.x * (kGDots + 1) + threadIdx.x] = acc[threadIdx.x];
 }
@@ -49,6 +92,28 @@ __global__ void k_greduce(const double *partial, int nblk, int nv, double *out) 
   }
 }
 
+// acc[e] += sum_{i < cnt} cf[i] V_i[k0 + e stride] (rows in groups of
+// kGRows, all loads of a group issued before its FMAs)
+template <typename TL>
+__device__ __forceinline__ void g_axpy(const TL *V, int64_t ldv, int cnt, const TL *cf, int64_t k0, int64_t stride,
+                                       int64_t n, TL (&acc)[kGE]) {
+  for (int r0 = 0; r0 < cnt; r0 += kGRows) {
+    TL v[kGRows][kGE], c[kGRows];
+#pragma unroll
+    for (int u = 0; u < kGRows; ++u) {
+      const int i = min(r0 + u, cnt - 1);
+      c[u] = r0 + u < cnt ? cf[r0 + u] : TL(0);
+      const TL *vi = V + (int64_t)i * ldv;
+#pragma unroll
+      for (int e = 0; e < kGE; ++e) v[u][e] = vi[min(k0 + e * stride, n - 1)];
+    }
+#pragma unroll
+    for (int u = 0; u < kGRows; ++u)
+#pragma unroll
+      for (int e = 0; e < kGE; ++e) acc[e] = fma(c[u], v[u][e], acc[e]);
+  }
+}
+
 // w = (w - sum_{i<cnt} coef[i] V_i) * scale; optional squared norm partials
 template <typename TL>
 __global__ void __launch_bounds__(kGT) k_gupdate(const TL *V, int64_t ldv, int cnt, const double *coef,
@@ -56,18 +121,34 @@ __global__ void __launch_bounds__(kGT) k_gupdate(const TL *V, int64_t ldv, int c
   __shared__ TL cf[1024];
   __shared__ double red[kGT / 32];
   __shared__ double outb[1];
-  for (int i = threadIdx.x; i < cnt; i += blockDim.x) cf[i] = (TL)coef[i];
+  for (int i = threadIdx.x; i < cnt; i += blockDim.x) cf[i] = (TL)(-coef[i]);
   __syncthreads();
   const TL sc = (TL)scale;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   double a[1] = {0.0};
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
-       k += (int64_t)gridDim.x * blockDim.x) {
-    TL wk = w[k];
-    for (int i = 0; i < cnt; ++i) wk = fma(-cf[i], V[(int64_t)i * ldv + k], wk);
-    wk *= sc;
-    w[k] = wk;
-    a[0] += (double)(wk * wk);
+  TL part = 0;
+  int it = 0;
+  for (int64_t k0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k0 < n; k0 += kGE * stride) {
+    TL wv[kGE];
+#pragma unroll
+    for (int e = 0; e < kGE; ++e) wv[e] = w[min(k0 + e * stride, n - 1)];
+    if (cnt > 0) g_axpy<TL>(V, ldv, cnt, cf, k0, stride, n, wv);
+#pragma unroll
+    for (int e = 0; e < kGE; ++e) {
+      const int64_t k = k0 + e * stride;
+      const TL v = wv[e] * sc;
+      if (k < n) {
+        w[k] = v;
+        part = fma(v, v, part);
+      }
+    }
+    if (++it == kGWiden) {
+      it = 0;
+      a[0] += (double)part;
+      part = 0;
+    }
   }
+  a[0] += (double)part;
   if (partial) {
     block_sum<1>(a, red, outb);
     if (threadIdx.x == 0) partial[blockIdx.x] = a[0];
@@ -81,11 +162,17 @@ __global__ void __launch_bounds__(kGT) k_gxupdate(const TL *V, int64_t ldv, int 
   __shared__ TL cf[1024];
   for (int i = threadIdx.x; i < cnt; i += blockDim.x) cf[i] = (TL)y[i];
   __syncthreads();
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
-       k += (int64_t)gridDim.x * blockDim.x) {
-    TL d = 0;
-    for (int i = 0; i < cnt; ++i) d = fma(cf[i], V[(int64_t)i * ldv + k], d);
-    x[k] += (double)d;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t k0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k0 < n; k0 += kGE * stride) {
+    TL d[kGE];
+#pragma unroll
+    for (int e = 0; e < kGE; ++e) d[e] = 0;
+    g_axpy<TL>(V, ldv, cnt, cf, k0, stride, n, d);
+#pragma unroll
+    for (int e = 0; e < kGE; ++e) {
+      const int64_t k = k0 + e * stride;
+      if (k < n) x[k] += (double)d[e];
+    }
   }
 }
 
@@ -235,7 +322,13 @@ static int grid_solve(rt_handle *h, const double *b, double *x, double tol, doub
       for (double v : hv) hh += v * v;
       double hn;
       h2.assign(j + 1, 0.0);
-      if (ww - hh > 0.5 * ww) {
+      // second projection (DGKS) when ||w - V h||^2 <= eta2 ||w||^2: 1/2 for
+      // float64 GMRES; 1e-4 for the float32 cycles of the mixed solve, whose
+      // residual is recomputed in float64 at every restart (w = A v keeps most
+      // of v on these operators, so the 1/2 test fires at nearly every step and
+      // doubles the Arnoldi traffic)
+      const double eta2 = mixed ? 1e-4 : 0.5;
+      if (ww - hh > eta2 * ww) {
         hn = std::sqrt(ww - hh);
         if ((e = update<TL>(g, V, ldv, hv, w, n, hn > 0 ? 1.0 / hn : 0.0, nullptr))) return e;
         bytes += sz * (j + 3) * n;

@@ -385,11 +385,15 @@ enum SweepOut : int {
 // recurrence by kAhead depth points.  Returns this thread's partial sum of y^2
 // for kOutResid (0 otherwise).  y may alias S: each thread reads S and writes y
 // only at the points of its own rays, the source value is read before the
-// output at the same point is written.
-template <typename T, typename TX, typename TY, int kAhead = 4, bool kQuad = false>
+// output at the same point is written.  OUT >= 0 fixes the output mode at
+// compile time (then `out` is ignored): the x and b values a mode does not
+// use hold no registers, and b is loaded ahead with the other values.
+template <typename T, typename TX, typename TY, int kAhead = 4, bool kQuad = false, int OUT = -1>
 __device__ double sweep_ray(const ColDev &c, const Tables<T> &tb, const Common &cm, const T *S,
                             const double *__restrict__ tsrc, const TX *__restrict__ x,
-                            const double *__restrict__ bv, TY *y, int out, bool inflow, int r) {
+                            const double *__restrict__ bv, TY *y, int out_rt, bool inflow, int r) {
+  const int out = OUT >= 0 ? OUT : out_rt;
+  constexpr bool pre_b = OUT == kOutResid || OUT == kOutAminusB;  // b prefetched (compile-time modes)
   const int nz = c.nz, nn = c.nn, nr = c.nr, ncls = c.ncls;
   const int d = r / nn, f = r - d * nn;
   const int up = cm.dir_up[c.d_off + d];
@@ -407,15 +411,15 @@ __device__ double sweep_ray(const ColDev &c, const Tables<T> &tb, const Common &
   auto src = [&](int i) -> T {
     return tsrc ? (T)tsrc[(int64_t)i * nn + f] : S[(int64_t)i * nr + r];
   };
-  // y at point i from the intensity I and the prefetched x value xi
-  auto emit = [&](int i, T I, TX xi) {
+  // y at point i from the intensity I and the prefetched x (and b) values
+  auto emit = [&](int i, T I, TX xi, double bi) {
     const int64_t k = (int64_t)i * nr + r;
     if (out == kOutResid) {
-      const double v = bv[k] - as_f64(xi) + (double)I;
+      const double v = (pre_b ? bi : bv[k]) - as_f64(xi) + (double)I;
       y[k] = (TY)v;
       ss += v * v;
     } else if (out == kOutAminusB) {
-      y[k] = (TY)(as_f64(xi) - (double)I - bv[k]);
+      y[k] = (TY)(as_f64(xi) - (double)I - (pre_b ? bi : bv[k]));
     } else if (out == kOutI) {
       y[k] = (TY)I;
     } else if (sizeof(TY) == 4 && sizeof(TX) <= 4) {
@@ -427,7 +431,7 @@ __device__ double sweep_ray(const ColDev &c, const Tables<T> &tb, const Common &
   // loads of the points i+step .. i+cnt*step (cnt <= kAhead); indices past
   // the column are clamped to its last point (the values are not used)
   auto load = [&](int i, int cnt, T (&e)[kAhead], T (&a)[kAhead], T (&b)[kAhead], T (&cq)[kAhead],
-                  T (&sc)[kAhead], TX (&xv)[kAhead]) {
+                  T (&sc)[kAhead], TX (&xv)[kAhead], double (&bb)[kAhead]) {
 #pragma unroll
     for (int u = 0; u < kAhead; ++u) {
       int ic = i + (u + 1) * step;
@@ -440,23 +444,26 @@ __device__ double sweep_ray(const ColDev &c, const Tables<T> &tb, const Common &
       cq[u] = quad ? Cq[ci] : T(0);
       sc[u] = src(ic);
       xv[u] = want_x ? x[(int64_t)ic * nr + r] : TX(0);
+      bb[u] = pre_b ? bv[(int64_t)ic * nr + r] : 0.0;
     }
   };
   T Su = src(i0);
-  emit(i0, Iu, want_x ? x[(int64_t)i0 * nr + r] : TX(0));
+  emit(i0, Iu, want_x ? x[(int64_t)i0 * nr + r] : TX(0), pre_b ? bv[(int64_t)i0 * nr + r] : 0.0);
   // chunks of kAhead points; the next chunk's loads are issued before the
   // current chunk's recurrence (2 kAhead points of loads in flight)
   T e0[kAhead], a0[kAhead], b0[kAhead], c0[kAhead], s0[kAhead];
   TX x0[kAhead];
+  double bb0[kAhead];
   int i = i0;
   int cnt = min(kAhead, nz - 1);
-  if (cnt > 0) load(i, cnt, e0, a0, b0, c0, s0, x0);
+  if (cnt > 0) load(i, cnt, e0, a0, b0, c0, s0, x0, bb0);
   for (int done = 1; done < nz; done += kAhead) {
     const int inext = i + cnt * step;
     const int cnext = min(kAhead, nz - done - cnt);
     T e1[kAhead], a1[kAhead], b1[kAhead], c1[kAhead], s1[kAhead];
     TX x1[kAhead];
-    if (cnext > 0) load(inext, cnext, e1, a1, b1, c1, s1, x1);
+    double bb1[kAhead];
+    if (cnext > 0) load(inext, cnext, e1, a1, b1, c1, s1, x1, bb1);
 #pragma unroll
     for (int u = 0; u < kAhead; ++u) {
       if (u < cnt) {
@@ -465,7 +472,7 @@ __device__ double sweep_ray(const ColDev &c, const Tables<T> &tb, const Common &
           const T Sd = u + 1 < cnt ? s0[u + 1 < kAhead ? u + 1 : 0] : (cnext > 0 ? s1[0] : T(0));
           Ic = fma(c0[u], Sd, Ic);
         }
-        emit(i + (u + 1) * step, Ic, x0[u]);
+        emit(i + (u + 1) * step, Ic, x0[u], bb0[u]);
         Iu = Ic;
         Su = s0[u];
       }
@@ -478,6 +485,7 @@ __device__ double sweep_ray(const ColDev &c, const Tables<T> &tb, const Common &
       c0[u] = c1[u];
       s0[u] = s1[u];
       x0[u] = x1[u];
+      bb0[u] = bb1[u];
     }
     i = inext;
     cnt = cnext;
@@ -494,20 +502,26 @@ __device__ double sweep_ray(const ColDev &c, const Tables<T> &tb, const Common &
 // for kOutResid (0 otherwise).  y may alias S: each thread reads S and writes y
 // only at the points of its own rays, the source value is read before the
 // output at the same point is written.
-template <typename T, typename TX, typename TY, int kAhead = 4>
-__device__ __noinline__ double sweep_column(const ColDev &c, const Tables<T> &tb, const Common &cm,
-                               const T *S, const double *__restrict__ tsrc,
-                               const TX *__restrict__ x, const double *__restrict__ bv,
-                               TY *y, int out, bool inflow) {
+// The output mode OUT (kOutAminus, kOutI, kOutResid, kOutAminusB) is a
+// compile-time parameter; the quadratic and linear steps are separate
+// non-inlined functions, each with its own register allocation.
+template <typename T, typename TX, typename TY, int kAhead, int OUT, bool kQuad>
+__device__ __noinline__ double sweep_rays(const ColDev &c, const Tables<T> &tb, const Common &cm, const T *S,
+                                          const double *__restrict__ tsrc, const TX *__restrict__ x,
+                                          const double *__restrict__ bv, TY *y, bool inflow) {
   double ss = 0.0;
-  if (c.fs == 2) {
-    for (int r = threadIdx.x; r < c.nr; r += blockDim.x)
-      ss += sweep_ray<T, TX, TY, kAhead, true>(c, tb, cm, S, tsrc, x, bv, y, out, inflow, r);
-  } else {
-    for (int r = threadIdx.x; r < c.nr; r += blockDim.x)
-      ss += sweep_ray<T, TX, TY, kAhead, false>(c, tb, cm, S, tsrc, x, bv, y, out, inflow, r);
-  }
+  for (int r = threadIdx.x; r < c.nr; r += blockDim.x)
+    ss += sweep_ray<T, TX, TY, kAhead, kQuad, OUT>(c, tb, cm, S, tsrc, x, bv, y, OUT, inflow, r);
   return ss;
+}
+
+template <typename T, typename TX, typename TY, int kAhead, int OUT>
+__device__ __forceinline__ double sweep_column(const ColDev &c, const Tables<T> &tb, const Common &cm,
+                                               const T *S, const double *__restrict__ tsrc,
+                                               const TX *__restrict__ x, const double *__restrict__ bv, TY *y,
+                                               bool inflow) {
+  if (c.fs == 2) return sweep_rays<T, TX, TY, kAhead, OUT, true>(c, tb, cm, S, tsrc, x, bv, y, inflow);
+  return sweep_rays<T, TX, TY, kAhead, OUT, false>(c, tb, cm, S, tsrc, x, bv, y, inflow);
 }
 
 }  // namespace rt
