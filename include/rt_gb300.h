@@ -218,6 +218,22 @@ int rt_autotune(rt_handle *h, int32_t flags, rt_tune_info *out, void *stream);
  *    zero is cleared by the call itself). */
 int rt_apply_noalloc(rt_handle *h, int32_t op, int32_t fp64, const double *x, double *y, void *stream);
 
+/* Compressed scattering for the low-precision operator (Sec. 4, Remark
+ * comput: Sigma_N is approximated at a rank r_eps with linear cost).  For
+ * each column of a mixed-precision 1D handle the frequency kernel is
+ * truncated in its weighted eigenbasis, W^(1/2) R W^(1/2) = U L U^T with
+ * W = diag(w_nu): the eigenvalues with |l| >= tol * max|l| are kept, so the
+ * frequency step of Sigma costs 2 n_nu r instead of n_nu^2 per point and
+ * angular rank; its error in the W^(1/2)-weighted norm is the largest dropped
+ * |l|.  Affects only the float32 operator: rt_apply with fp64 = 0 and the inner
+ * cycles of rt_solve; the float64 operator, and so the solution rt_solve
+ * returns, stay exact.  Columns whose rank would exceed 32, dense-Psi and
+ * coherent (diagonal) kernels keep the exact kernel.  tol = 0 restores the
+ * exact kernel everywhere.  max_rank (may be NULL): largest rank kept.
+ * Errors: RT_ERR_ARG for a 3D box or a float64 handle, tol outside [0, 1).
+ * Synchronous (host eigen-decompositions, one upload). */
+int rt_set_sigma_rank(rt_handle *h, double tol, int32_t *max_rank);
+
 /* Solve A_N x = b for all instances (eq. RT_sys_algebraic; the Krylov solvers
  * of Sec. 5, GMRES and BiCGStab, unpreconditioned).  b == NULL uses the
  * internal right-hand side Lambda t + I_in for every rhs.

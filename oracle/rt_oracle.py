@@ -336,6 +336,34 @@ def sigma_op(prob: Problem, X: np.ndarray, with_source: bool = False) -> np.ndar
     return S.reshape(-1)
 
 
+def truncated_frequency_kernel(prob: Problem, tol: float) -> tuple[np.ndarray, int]:
+    """Low-rank frequency kernel for the compressed Sigma (Sec. 4, Remark
+    comput: the scattering operator is approximated at rank r_eps with linear
+    cost).  The frequency part of Sigma applies R W (W = diag(w_nu)).  It is
+    truncated in the W-weighted eigenbasis: M = W^(1/2) R W^(1/2) = U L U^T
+    (symmetric R), keeping the eigenvalues with |l| >= tol max |l|, so that
+    R_r W = W^(-1/2) U_r L_r U_r^T W^(1/2) is the best rank-r approximation of
+    R W in the norm weighted by W^(1/2).  tol = 0 keeps every eigenvalue.
+    Returns R_r and r."""
+    sw = np.sqrt(prob.w_nu)
+    M = sw[:, None] * prob.R * sw[None, :]
+    lam, U = np.linalg.eigh(0.5 * (M + M.T))
+    keep = np.abs(lam) >= tol * np.abs(lam).max() if tol > 0 else np.ones(lam.size, dtype=bool)
+    Ur, lr = U[:, keep], lam[keep]
+    Rr = (Ur * lr[None, :]) @ Ur.T / (sw[:, None] * sw[None, :])
+    return Rr, int(keep.sum())
+
+
+def sigma_op_lowrank(prob: Problem, X: np.ndarray, tol: float) -> np.ndarray:
+    """Sigma_N X (eq. Sigma) with the frequency kernel replaced by its
+    truncation (truncated_frequency_kernel); separable kernels only."""
+    if prob.Psi is not None:
+        raise ValueError("the low-rank Sigma needs a separable kernel P (x) R")
+    Rr, _ = truncated_frequency_kernel(prob, tol)
+    from dataclasses import replace
+    return sigma_op(replace(prob, R=Rr), X)
+
+
 def sigma_matrix(prob: Problem) -> np.ndarray:
     """Dense Sigma_N = Gamma_N Psi_N (Id (x) W_r) (eq. Sigma), block diagonal."""
     nd, nn, nr = prob.n_dir, prob.n_nu, prob.n_r

@@ -5,7 +5,9 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <atomic>
 #include <numeric>
+#include <thread>
 #include <utility>
 #include <string>
 #include <vector>
@@ -116,7 +118,7 @@ void free_handle(rt_handle *h) {
                   h->so.outer, h->so.inner, h->so.status, h->so.relres, h->so.bytes,
                   h->stage_x, h->stage_y, h->d_sig_tiles, h->d_sw_tiles, h->apply_S,
                   h->d_tc_jobs, h->d_tc_off, h->d_tc_tiles, h->d_tc_xb, h->d_tc_maps, h->d_err, h->d_geo,
-                  h->chi64, h->chi32, h->box_w064, h->box_bt64, h->g_part, h->g_red, h->g_coef, h->g_r, h->Q64, h->Q32};
+                  h->chi64, h->chi32, h->box_w064, h->box_bt64, h->g_part, h->g_red, h->g_coef, h->g_r, h->Q64, h->Q32, h->lr32};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (h->solve_graph) cudaGraphExecDestroy(h->solve_graph);
@@ -364,7 +366,7 @@ int create_columns(const rt_desc *descs, int n_cols, int n_rhs, int precision, i
   h->max_restart = max_restart;
   std::vector<rt::ColDev> cols(n_cols);
   std::vector<int32_t> dir_cls, dir_up, cls_off, fs;
-  std::vector<double> z, mu_cls, chi, gam, tsrc, itop, ibot, Uw, Ul, Rw, Psi;
+  std::vector<double> z, mu_cls, chi, gam, tsrc, itop, ibot, Uw, Ul, Rw, Psi, wnu;
   std::vector<int64_t> zoff;
   bool any_t = false;
   for (int i = 0; i < n_cols; ++i) any_t = any_t || descs[i].t_src;
@@ -408,6 +410,7 @@ int create_columns(const rt_desc *descs, int n_cols, int n_rhs, int precision, i
       itop.push_back(d->I_top ? d->I_top[f] : 0.0);
       ibot.push_back(d->I_bot ? d->I_bot[f] : 0.0);
     }
+    wnu.insert(wnu.end(), d->w_nu, d->w_nu + d->n_nu);
     dir_cls.insert(dir_cls.end(), ch.dir_cls.begin(), ch.dir_cls.end());
     dir_up.insert(dir_up.end(), ch.dir_up.begin(), ch.dir_up.end());
     Uw.insert(Uw.end(), ch.Uw.begin(), ch.Uw.end());
@@ -425,6 +428,8 @@ int create_columns(const rt_desc *descs, int n_cols, int n_rhs, int precision, i
   }
   h->E = x_off;
   h->h_cols = cols;
+  h->h_rw = Rw;
+  h->h_wnu = wnu;
   int rc = RT_OK;
 #define UP(dst, src)                          \
   if ((rc = dev_upload(&(dst), src)) != RT_OK) { \
@@ -892,6 +897,83 @@ int rt_apply_noalloc(rt_handle *h, int32_t op, int32_t fp64, const double *x, do
       return fail(RT_ERR_TIMEOUT, "tensor-core Sigma: a bounded wait gave up");
     }
   }
+  return RT_OK;
+}
+
+int rt_set_sigma_rank(rt_handle *h, double tol, int32_t *max_rank) {
+  if (!h) return fail(RT_ERR_ARG, "null handle");
+  if (h->dims != 1 || h->precision != RT_P_MIXED)
+    return fail(RT_ERR_ARG, "rt_set_sigma_rank: the truncated kernel acts on the float32 operator of mixed 1D handles");
+  if (!(tol >= 0.0) || !(tol < 1.0)) return fail(RT_ERR_ARG, "rt_set_sigma_rank: need 0 <= tol < 1");
+  const int n_cols = h->n_cols;
+  std::vector<std::vector<float>> fac(n_cols);
+  std::vector<int> rank(n_cols, 0);
+  if (tol > 0.0) {
+    // per column: M = W^1/2 R W^1/2 (symmetric), eigen-decomposed; keep
+    // |l| >= tol max |l|; A[q][s] = U[q][s] w_q^1/2, B[f][s] = U[f][s] l_s w_f^-1/2
+    auto work = [&](int ci) {
+      const rt::ColDev &c = h->h_cols[ci];
+      if (c.psi_off >= 0 || c.rdiag) return;
+      const int nn = c.nn;
+      const double *RwT = h->h_rw.data() + c.r_off;   // RwT[q][f] = R(f, q) w_q
+      const double *w = h->h_wnu.data() + c.in_off;
+      std::vector<double> M((size_t)nn * nn), lam, Q;
+      for (int f = 0; f < nn; ++f)
+        for (int q = 0; q < nn; ++q)
+          M[(size_t)f * nn + q] = std::sqrt(w[f] / w[q]) * RwT[(size_t)q * nn + f];
+      for (int f = 0; f < nn; ++f)  // symmetrise the rounding
+        for (int q = f + 1; q < nn; ++q) {
+          const double v = 0.5 * (M[(size_t)f * nn + q] + M[(size_t)q * nn + f]);
+          M[(size_t)f * nn + q] = M[(size_t)q * nn + f] = v;
+        }
+      jacobi_eig(nn, M, lam, Q);
+      double lmax = 0.0;
+      for (double v : lam) lmax = std::max(lmax, std::fabs(v));
+      std::vector<int> keep;
+      for (int k = 0; k < nn; ++k)
+        if (std::fabs(lam[k]) >= tol * lmax && lam[k] != 0.0) keep.push_back(k);
+      const int r = (int)keep.size();
+      if (r == 0 || r > rt::kLrMax) return;  // exact kernel for this column
+      std::vector<float> &F = fac[ci];
+      F.assign((size_t)2 * nn * r, 0.f);
+      for (int q = 0; q < nn; ++q)
+        for (int k = 0; k < r; ++k) {
+          const double u = Q[(size_t)q * nn + keep[k]];
+          F[(size_t)q * r + k] = (float)(u * std::sqrt(w[q]));
+          F[(size_t)nn * r + (size_t)q * r + k] = (float)(u * lam[keep[k]] / std::sqrt(w[q]));
+        }
+      rank[ci] = r;
+    };
+    const int nt = std::max(1, std::min<int>((int)std::thread::hardware_concurrency(), 32));
+    std::vector<std::thread> pool;
+    std::atomic<int> next{0};
+    for (int t = 0; t < nt; ++t)
+      pool.emplace_back([&]() {
+        for (int ci = next++; ci < n_cols; ci = next++) work(ci);
+      });
+    for (auto &th : pool) th.join();
+  }
+  std::vector<float> all;
+  int rmax = 0;
+  for (int ci = 0; ci < n_cols; ++ci) {
+    h->h_cols[ci].lr_rank = rank[ci];
+    h->h_cols[ci].lr_off = (int64_t)all.size();
+    all.insert(all.end(), fac[ci].begin(), fac[ci].end());
+    rmax = std::max(rmax, rank[ci]);
+  }
+  if (h->lr32) cudaFree(h->lr32);
+  h->lr32 = nullptr;
+  if (!all.empty()) {
+    int rc = dev_upload(&h->lr32, all);
+    if (rc != RT_OK) return rc;
+  }
+  RT_CUDA(cudaMemcpy(h->d_cols, h->h_cols.data(), h->h_cols.size() * sizeof(rt::ColDev), cudaMemcpyHostToDevice));
+  h->lr_tol = tol;
+  if (h->solve_graph) {  // the captured solve holds the old table pointers
+    cudaGraphExecDestroy(h->solve_graph);
+    h->solve_graph = nullptr;
+  }
+  if (max_rank) *max_rank = rmax;
   return RT_OK;
 }
 

@@ -586,7 +586,7 @@ template <int KR>
 __device__ __noinline__ void sigma_points_h16(const ColDev &c, const Tables<float> &tb,
                                               const __half *__restrict__ X, float *__restrict__ S,
                                               unsigned char *wbuf, const float *Rw, const float *Uw,
-                                              const float *Ul) {
+                                              const float *Ul, const float *lrA) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int nd = c.nd, nn = c.nn, nr = c.nr, rp = c.rp;
   const float *gam = tb.gamma + c.g_off;
@@ -624,6 +624,12 @@ __device__ __noinline__ void sigma_points_h16(const ColDev &c, const Tables<floa
         if (k < rp) wm[k * nn + f] = m[k];
     }
     __syncwarp();
+    const float *zw = wz;
+    if (lrA) {
+      // truncated frequency kernel: t = A^T m into wz, z = B t back into wm
+      lowrank_frequency_warp<float>(lrA, lrA + nn * c.lr_rank, c.lr_rank, nn, rp, wm, wz, wm);
+      zw = wm;
+    } else
     // 2. frequency kernel z_k(f) = sum_q RwT[q][f] m_k(q), two frequencies per lane
     for (int fb = 0; fb < nn; fb += 64) {
       const int fa = fb + lane, fc = fa + 32;
@@ -665,7 +671,7 @@ __device__ __noinline__ void sigma_points_h16(const ColDev &c, const Tables<floa
     for (int f = lane; f < nn; f += 32) {
       float zf[KR];
 #pragma unroll
-      for (int k = 0; k < KR; ++k) zf[k] = k < rp ? wz[k * nn + f] : 0.f;
+      for (int k = 0; k < KR; ++k) zf[k] = k < rp ? zw[k * nn + f] : 0.f;
       const float gf = gs[f];
       for (int d = 0; d < nd; ++d) {
         const float *u = Ul + d * rp;
@@ -684,12 +690,13 @@ __device__ __noinline__ void sigma_points_h16(const ColDev &c, const Tables<floa
 
 // Every point of one column (one CTA); wbase: nw * kSig16WarpBytes of shared
 // memory; Rw, Uw, Ul: the column's float32 factors (shared or global).
+// lrA: the column's truncated frequency kernel A | B (shared memory), or null
 __device__ __noinline__ void sigma_column_h16(const ColDev &c, const Tables<float> &tb, const __half *X,
                                               float *S, unsigned char *wbase, const float *Rw, const float *Uw,
-                                              const float *Ul) {
+                                              const float *Ul, const float *lrA) {
   unsigned char *wbuf = wbase + (threadIdx.x >> 5) * kSig16WarpBytes;
-  if (c.rp <= 2) sigma_points_h16<2>(c, tb, X, S, wbuf, Rw, Uw, Ul);
-  else sigma_points_h16<8>(c, tb, X, S, wbuf, Rw, Uw, Ul);
+  if (c.rp <= 2) sigma_points_h16<2>(c, tb, X, S, wbuf, Rw, Uw, Ul, lrA);
+  else sigma_points_h16<8>(c, tb, X, S, wbuf, Rw, Uw, Ul, lrA);
   __syncthreads();
 }
 
@@ -960,9 +967,15 @@ __global__ void __launch_bounds__(kNT, 1) k_solve_nested(SolveParams p) {
     double *x = p.x + rhs * p.E + c.x_off;
     const double bn = sqrt(cta_norm2(bv, n, red, outb));
     const bool h16 = sig16_ok(c) && (blockDim.x >> 5) * kSig16WarpBytes <= (int)sizeof(sm);
-    // stage the float32 frequency kernel of this column (dense, up to 128 x 128)
-    const float *rw_c = nullptr;
-    if (!c.rdiag && c.psi_off < 0 && c.nn * c.nn <= kRwCache) {
+    // stage the float32 frequency kernel of this column (dense, up to 128 x
+    // 128), or its truncated factors A | B when the handle has them
+    const float *rw_c = nullptr, *lr_c = nullptr;
+    if (p.t32.LR && c.lr_rank > 0 && !c.rdiag && c.psi_off < 0) {
+      const int len = 2 * c.nn * c.lr_rank;
+      for (int k = threadIdx.x; k < len; k += blockDim.x) rw_s[k] = p.t32.LR[c.lr_off + k];
+      __syncthreads();
+      lr_c = rw_s;
+    } else if (!c.rdiag && c.psi_off < 0 && c.nn * c.nn <= kRwCache) {
       for (int k = threadIdx.x; k < c.nn * c.nn; k += blockDim.x) rw_s[k] = p.t32.RwT[c.r_off + k];
       __syncthreads();
       rw_c = rw_s;
@@ -1040,7 +1053,7 @@ __global__ void __launch_bounds__(kNT, 1) k_solve_nested(SolveParams p) {
           const __half *uj = U + (int64_t)j * ldv;
           if (h16)
             sigma_column_h16(c, p.t32, uj, S32, reinterpret_cast<unsigned char *>(sm),
-                             rw_c ? rw_c : p.t32.RwT + c.r_off, uw_c, ul_c);
+                             rw_c ? rw_c : p.t32.RwT + c.r_off, uw_c, ul_c, lr_c);
           else
             sigma_column<float, __half>(c, p.t32, uj, S32, reinterpret_cast<float *>(sm), 8 * kSigBuf, rw_c);
           // Arnoldi on K = Lambda Sigma (A = Id - K, same Krylov space): the

@@ -102,6 +102,11 @@ struct rt_handle {
   double *chi64 = nullptr;   // 3D: opacity [n_pts][box_npad], zero past n_nu
   float *chi32 = nullptr;
   int box_npad = 0;          // 3D: frequencies rounded up to a multiple of 4
+  // truncated frequency kernels of the float32 operator (rt_set_sigma_rank):
+  // factors A | B per column, null when every column is exact
+  float *lr32 = nullptr;
+  double lr_tol = 0.0;
+  std::vector<double> h_rw, h_wnu;   // host copies: R w (as RwT) and w_nu per column
   double *box_w064 = nullptr, *box_bt64 = nullptr;  // 3D: float64 step weights, or null
   double *g_part = nullptr, *g_red = nullptr, *g_coef = nullptr, *g_r = nullptr;
   int64_t stage_len = 0;
@@ -125,6 +130,7 @@ inline Tables<double> tables64(const rt_handle *h) {
 }
 inline Tables<float> tables32(const rt_handle *h) {
   Tables<float> t{h->E32, h->A32, h->B32, h->Uw32, h->Ul32, h->Rw32, h->Psi32, h->gam32};
+  t.LR = h->lr32;
   if (h->Q32) {
     t.C = h->Q32;
     t.A2 = h->Q32 + h->n_coef;

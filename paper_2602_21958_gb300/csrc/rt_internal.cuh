@@ -29,7 +29,11 @@ struct ColDev {
   int32_t rp;       // rank of the angular factor
   int32_t rdiag;    // 1: frequency kernel is diagonal (coherent scattering)
   int32_t fs;       // formal solver: 0 SC-L, 1 implicit Euler, 2 quadratic SC
+  int32_t lr_rank;  // float32 operator: rank of the truncated frequency kernel (0: exact)
+  int64_t lr_off;   // offset of its factors A | B ([nn][lr_rank] each) in Tables::LR
 };
+
+constexpr int kLrMax = 32;  // largest rank of a truncated frequency kernel
 
 // Arrays in one arithmetic precision T (double: fp64 path; float: mixed path).
 template <typename T>
@@ -44,7 +48,37 @@ struct Tables {
   // with (A, B, C) for rays going down (mu < 0) and (A2, B2, C2) going up,
   // indexed like E by the layer between u and c (C = 0 on a ray's last step)
   const T *C = nullptr, *A2 = nullptr, *B2 = nullptr, *C2 = nullptr;
+  // truncated frequency kernel (float32 operator, columns with lr_rank > 0):
+  // R W ~ B A^T with A[q][s] = U[q][s] w_q^(1/2), B[f][s] = U[f][s] l_s w_f^(-1/2)
+  const T *LR = nullptr;
 };
+
+// Frequency kernel of one point in low-rank form: z_k(f) = sum_s B[f][s]
+// t_k(s), t_k(s) = sum_q A[q][s] m_k(q), for the rp ranks k of the angular
+// factor.  m: [rp][nn] moments (read), t: [rp][r] scratch, z: [rp][nn] out
+// (z may be m: m is not read after the first half).  Lanes of one warp.
+template <typename T>
+__device__ __forceinline__ void lowrank_frequency_warp(const T *A, const T *B, int r, int nn, int rp, const T *m,
+                                                       T *t, T *z) {
+  const int lane = threadIdx.x & 31;
+  for (int i = lane; i < rp * r; i += 32) {
+    const int k = i / r, sidx = i - k * r;
+    const T *mk = m + k * nn;
+    T acc = 0;
+    for (int q = 0; q < nn; ++q) acc = fma(A[q * r + sidx], mk[q], acc);
+    t[i] = acc;
+  }
+  __syncwarp();
+  for (int i = lane; i < rp * nn; i += 32) {
+    const int k = i / nn, f = i - k * nn;
+    const T *tk = t + k * r;
+    const T *bf = B + f * r;
+    T acc = 0;
+    for (int sidx = 0; sidx < r; ++sidx) acc = fma(bf[sidx], tk[sidx], acc);
+    z[i] = acc;
+  }
+  __syncwarp();
+}
 
 struct Common {
   const ColDev *cols;
@@ -195,23 +229,46 @@ __device__ void sigma_block_kr(const ColDev &c, const Tables<T> &tb, const TX *_
   }
   __syncthreads();
   // 2. frequency kernel, one thread per (point, rank, nu)
-  for (int i = threadIdx.x; i < np * per_pt; i += blockDim.x) {
-    const int f = i % nn;
-    const T *mrow = sm0 + (i - f);
-    T acc;
-    if (c.rdiag) {
-      acc = Rw[f] * mrow[f];
-    } else {
-      acc = 0;
-      for (int q = 0; q < nn; ++q) acc = fma(Rw[q * nn + f], mrow[q], acc);
+  T *zbuf = sm1;
+  if (tb.LR && c.lr_rank > 0 && !c.rdiag) {
+    // low rank: t = A^T m into sm1, then z = B t into sm0 (moments consumed)
+    const int lr = c.lr_rank;
+    const T *A = tb.LR + c.lr_off, *Bf = A + (int64_t)nn * lr;
+    for (int i = threadIdx.x; i < np * rp * lr; i += blockDim.x) {
+      const int row = i / lr, sidx = i - row * lr;
+      const T *mrow = sm0 + row * nn;
+      T acc = 0;
+      for (int q = 0; q < nn; ++q) acc = fma(A[q * lr + sidx], mrow[q], acc);
+      sm1[i] = acc;
     }
-    sm1[i] = acc;
+    __syncthreads();
+    for (int i = threadIdx.x; i < np * per_pt; i += blockDim.x) {
+      const int row = i / nn, f = i - row * nn;
+      const T *trow = sm1 + row * lr;
+      T acc = 0;
+      for (int sidx = 0; sidx < lr; ++sidx) acc = fma(Bf[f * lr + sidx], trow[sidx], acc);
+      sm0[i] = acc;
+    }
+    zbuf = sm0;
+  } else {
+    for (int i = threadIdx.x; i < np * per_pt; i += blockDim.x) {
+      const int f = i % nn;
+      const T *mrow = sm0 + (i - f);
+      T acc;
+      if (c.rdiag) {
+        acc = Rw[f] * mrow[f];
+      } else {
+        acc = 0;
+        for (int q = 0; q < nn; ++q) acc = fma(Rw[q * nn + f], mrow[q], acc);
+      }
+      sm1[i] = acc;
+    }
   }
   __syncthreads();
   // 3. expansion over directions, scaled by Gamma
   for (int i = threadIdx.x; i < np * nr; i += blockDim.x) {
     const int b = i / nr, r = i - b * nr, d = r / nn, f = r - d * nn;
-    const T *zb = sm1 + b * per_pt + f;
+    const T *zb = zbuf + b * per_pt + f;
     const T *u = Ul + d * rp;
     T acc = 0;
     for (int k = 0; k < rp; ++k) acc = fma(u[k], zb[k * nn], acc);
@@ -284,6 +341,13 @@ __device__ void sigma_points_warp(const ColDev &c, const Tables<T> &tb, const TX
       }
     }
     __syncwarp();
+    const T *zw = wz;
+    if (tb.LR && c.lr_rank > 0 && !c.rdiag) {
+      // low rank: t into wz, z back into wm (moments consumed)
+      const T *A = tb.LR + c.lr_off;
+      lowrank_frequency_warp<T>(A, A + (int64_t)nn * c.lr_rank, c.lr_rank, nn, rp, wm, wz, wm);
+      zw = wm;
+    } else
     // 2. frequency kernel z_k(f) = sum_q RwT[q][f] m_k(q): each lane owns two
     //    frequencies (f, f+32) and KR ranks, so a RwT load feeds KR FMAs and a
     //    moment load feeds two
@@ -332,7 +396,7 @@ __device__ void sigma_points_warp(const ColDev &c, const Tables<T> &tb, const TX
       const int d = r / nn, f = r - d * nn;
       const T *u = Ul + d * rp;
       T acc = 0;
-      for (int k = 0; k < rp; ++k) acc = fma(u[k], wz[k * nn + f], acc);
+      for (int k = 0; k < rp; ++k) acc = fma(u[k], zw[k * nn + f], acc);
       sp[r] = g[f] * acc;
     }
     __syncwarp();

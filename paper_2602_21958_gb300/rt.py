@@ -49,7 +49,8 @@ class rt_info(C.Structure):
 
 
 EXPORTS = ("rt_create", "rt_create_batch", "rt_vector_length", "rt_apply", "rt_apply_noalloc",
-           "rt_autotune", "rt_solve", "rt_arnoldi", "rt_destroy", "rt_last_error", "rt_version")
+           "rt_autotune", "rt_set_sigma_rank", "rt_solve", "rt_arnoldi", "rt_destroy", "rt_last_error",
+           "rt_version")
 
 
 class rt_tune_info(C.Structure):
@@ -79,6 +80,8 @@ def load(path: Optional[str] = None) -> C.CDLL:
     lib.rt_apply_noalloc.argtypes = [vp, C.c_int32, C.c_int32, vp, vp, vp]
     lib.rt_autotune.argtypes = [vp, C.c_int32, C.POINTER(rt_tune_info), vp]
     lib.rt_autotune.restype = C.c_int
+    lib.rt_set_sigma_rank.argtypes = [vp, C.c_double, C.POINTER(C.c_int32)]
+    lib.rt_set_sigma_rank.restype = C.c_int
     lib.rt_solve.argtypes = [vp, vp, vp, C.POINTER(rt_solve_opts), C.POINTER(rt_info), vp]
     lib.rt_arnoldi.argtypes = [vp, vp, C.c_int32, vp, C.POINTER(C.c_int32), vp]
     lib.rt_destroy.argtypes = [vp]
@@ -208,6 +211,13 @@ class Handle:
         return {"ray_block": t.ray_block, "ahead": t.ahead, "sigma_points": t.sigma_points,
                 "from_cache": bool(t.from_cache), "ms_best": t.ms_best, "ms_default": t.ms_default,
                 "box_fb": t.box_fb, "box_cpt": t.box_cpt}
+
+    def rt_set_sigma_rank(self, tol: float) -> int:
+        """Truncate the float32 operator's frequency kernels at ``tol``
+        (0: exact); returns the largest rank kept."""
+        r = C.c_int32(0)
+        _check(load().rt_set_sigma_rank(self._h, float(tol), C.byref(r)))
+        return r.value
 
     def rt_solve(self, b, x, tol: float = 1e-11, tol_inner: float = 0.1, restart: Optional[int] = None,
                  max_outer: int = 50, use_x0: bool = False, stream=None, per_instance: bool = False,

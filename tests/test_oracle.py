@@ -647,3 +647,49 @@ def test_batch_rhs_solves_with_the_column_solutions():
     for c, p in enumerate(cols):
         xc = np.linalg.solve(O.assemble_A(p), b[off[c]:off[c + 1]])
         assert np.linalg.norm(xc - O.solve_dense(p)) <= 1e-13 * np.linalg.norm(xc)
+
+
+# ------------------------------------------------- low-rank Sigma (Sec. 4)
+def _lowrank_column():
+    return W.two_level_column(np.logspace(-3, 3, 11), 4, 2, 24, "r2", 1e-3, 1.0)
+
+
+def test_truncated_frequency_kernel_at_zero_tolerance_is_the_kernel():
+    p = _lowrank_column()
+    Rr, r = O.truncated_frequency_kernel(p, 0.0)
+    assert r == p.n_nu
+    assert np.abs(Rr - p.R).max() <= 1e-13 * np.abs(p.R).max()
+    # Gamma = (1 - eps)/phi amplifies the reconstruction's rounding in the
+    # line wings (phi ~ 1e-7 there), hence the looser bar on Sigma itself
+    x = W.random_vectors(p.n, 1, 5)[0]
+    assert np.linalg.norm(O.sigma_op_lowrank(p, x, 0.0) - O.sigma_op(p, x)) <= 1e-10 * np.linalg.norm(O.sigma_op(p, x))
+
+
+def test_truncation_error_is_the_largest_dropped_eigenvalue():
+    """In the norm weighted by W^(1/2), the error of the truncated R W is the
+    largest dropped |eigenvalue| of W^(1/2) R W^(1/2) (Eckart-Young for a
+    symmetric matrix), and the rank falls monotonically with the tolerance."""
+    p = _lowrank_column()
+    sw = np.sqrt(p.w_nu)
+    lam = np.linalg.eigvalsh(sw[:, None] * p.R * sw[None, :])
+    ranks = []
+    for tol in (1e-6, 1e-3, 1e-1):
+        Rr, r = O.truncated_frequency_kernel(p, tol)
+        ranks.append(r)
+        E = sw[:, None] * (p.R - Rr) * sw[None, :]      # W^(1/2) (R - R_r) W^(1/2)
+        dropped = np.abs(lam)[np.abs(lam) < tol * np.abs(lam).max()]
+        assert r == p.n_nu - dropped.size
+        assert abs(np.linalg.norm(E, 2) - (dropped.max() if dropped.size else 0.0)) <= 1e-12 * np.abs(lam).max()
+    assert ranks[0] >= ranks[1] >= ranks[2] and ranks[2] < p.n_nu
+
+
+def test_crd_kernel_is_rank_one():
+    """Complete redistribution R = phi phi^T has rank 1: any tolerance below 1
+    keeps one eigenvalue and the Sigma is exact."""
+    p = W.two_level_column(np.logspace(-2, 2, 6), 4, 2, 9, "crd", 1e-2, 1.0)
+    Rr, r = O.truncated_frequency_kernel(p, 1e-3)
+    assert r == 1
+    x = W.random_vectors(p.n, 1, 6)[0]
+    ref = O.sigma_op(p, x)
+    # exact up to the reconstruction's rounding, amplified by Gamma = (1 - eps)/phi
+    assert np.linalg.norm(O.sigma_op_lowrank(p, x, 1e-3) - ref) <= 1e-10 * np.linalg.norm(ref)
