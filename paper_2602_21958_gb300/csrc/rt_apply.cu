@@ -54,13 +54,13 @@ __global__ void __launch_bounds__(RB) k_sweep_tiles(Common cm, Tables<T> tb, con
 template <typename T>
 __global__ void k_convert(const double *a, T *b, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    b[i] = (T)a[i];
+    b[i] = cvt<T>(a[i]);
 }
 
 template <typename T>
 __global__ void k_widen(const T *a, double *b, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    b[i] = (double)a[i];
+    b[i] = cvt<double>(a[i]);
 }
 
 // sweep launch with the handle's tuned (ray block, loads ahead)

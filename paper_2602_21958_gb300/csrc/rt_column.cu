@@ -1041,7 +1041,7 @@ __global__ void __launch_bounds__(kNT, 1) k_solve_nested(SolveParams p) {
           for (int64_t q = threadIdx.x; q < ldv / 4; q += blockDim.x) {
             float f[4];
 #pragma unroll
-            for (int t = 0; t < 4; ++t) f[t] = 4 * q + t < n ? (float)(vi[4 * q + t] * inv) : 0.f;
+            for (int t = 0; t < 4; ++t) f[t] = 4 * q + t < n ? narrow_f32(vi[4 * q + t] * inv) : 0.f;
             st_h4(U + 4 * q, f);
           }
           __syncthreads();
@@ -1115,7 +1115,7 @@ __global__ void __launch_bounds__(kNT, 1) k_solve_nested(SolveParams p) {
       tri_solve(Ho, kout + 1, go, idone, ybuf);
       for (int64_t k = threadIdx.x; k < n; k += blockDim.x) {
         double acc = x[k];
-        for (int i = 0; i < idone; ++i) acc = fma(ybuf[i], (double)Z[(int64_t)i * ldv + k], acc);
+        for (int i = 0; i < idone; ++i) acc = fma(ybuf[i], widen_f64(Z[(int64_t)i * ldv + k]), acc);
         x[k] = acc;
       }
       __syncthreads();

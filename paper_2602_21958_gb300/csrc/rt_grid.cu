@@ -171,7 +171,7 @@ __global__ void __launch_bounds__(kGT) k_gxupdate(const TL *V, int64_t ldv, int 
 #pragma unroll
     for (int e = 0; e < kGE; ++e) {
       const int64_t k = k0 + e * stride;
-      if (k < n) x[k] += (double)d[e];
+      if (k < n) x[k] += cvt<double>(d[e]);
     }
   }
 }
@@ -194,7 +194,7 @@ __global__ void __launch_bounds__(kGT) k_gresid(const double *b, double *y, int6
 template <typename TL>
 __global__ void k_gscale(const double *src, TL *dst, int64_t n, double s) {
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
-    dst[k] = (TL)(src[k] * s);
+    dst[k] = cvt<TL>(src[k] * s);
 }
 
 __global__ void k_gnorm(const double *v, int64_t n, double *partial) {

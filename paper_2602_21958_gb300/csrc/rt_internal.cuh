@@ -148,15 +148,20 @@ __device__ __forceinline__ double widen_f64(float v) {
   return __hiloint2double((int)hi, (int)(u << 29));
 }
 
-template <typename T> __device__ __forceinline__ T to(double v) { return (T)v; }
-template <typename T> __device__ __forceinline__ T to(float v) { return (T)v; }
-template <typename T> __device__ __forceinline__ T to(__half v) { return (T)__half2float(v); }
+// cvt<TO>(v): a cast that never issues a float64 <-> float32 conversion instruction
+template <typename TO, typename FROM> __device__ __forceinline__ TO cvt(FROM v) { return (TO)v; }
+template <> __device__ __forceinline__ float cvt<float, double>(double v) { return narrow_f32(v); }
+template <> __device__ __forceinline__ double cvt<double, float>(float v) { return widen_f64(v); }
+
+template <typename T> __device__ __forceinline__ T to(double v) { return cvt<T>(v); }
+template <typename T> __device__ __forceinline__ T to(float v) { return cvt<T>(v); }
+template <typename T> __device__ __forceinline__ T to(__half v) { return cvt<T>(__half2float(v)); }
 __device__ __forceinline__ float as_f32(float v) { return v; }
-__device__ __forceinline__ float as_f32(double v) { return (float)v; }
+__device__ __forceinline__ float as_f32(double v) { return narrow_f32(v); }
 __device__ __forceinline__ float as_f32(__half v) { return __half2float(v); }
 __device__ __forceinline__ double as_f64(double v) { return v; }
-__device__ __forceinline__ double as_f64(float v) { return (double)v; }
-__device__ __forceinline__ double as_f64(__half v) { return (double)__half2float(v); }
+__device__ __forceinline__ double as_f64(float v) { return widen_f64(v); }
+__device__ __forceinline__ double as_f64(__half v) { return widen_f64(__half2float(v)); }
 
 // ------------------------------------------------------------------ Sigma
 // S_p = Gamma_p Psi W X_p for every point of one column (eq. Sigma), the
@@ -471,25 +476,27 @@ __device__ double sweep_ray(const ColDev &c, const Tables<T> &tb, const Common &
   const int i0 = up ? nz - 1 : 0;
   const bool want_x = out != kOutI;
   T Iu = 0;
-  if (inflow) Iu = (T)(up ? cm.I_bot[c.in_off + f] : cm.I_top[c.in_off + f]);
+  if (inflow) Iu = cvt<T>(up ? cm.I_bot[c.in_off + f] : cm.I_top[c.in_off + f]);
   auto src = [&](int i) -> T {
-    return tsrc ? (T)tsrc[(int64_t)i * nn + f] : S[(int64_t)i * nr + r];
+    return tsrc ? cvt<T>(tsrc[(int64_t)i * nn + f]) : S[(int64_t)i * nr + r];
   };
   // y at point i from the intensity I and the prefetched x (and b) values
+  // (the float32 operator, T = float, subtracts in float32: x is rounded to
+  // float32 first, and no float64 instruction is issued)
   auto emit = [&](int i, T I, TX xi, double bi) {
     const int64_t k = (int64_t)i * nr + r;
     if (out == kOutResid) {
-      const double v = (pre_b ? bi : bv[k]) - as_f64(xi) + (double)I;
-      y[k] = (TY)v;
+      const double v = (pre_b ? bi : bv[k]) - as_f64(xi) + as_f64(I);
+      y[k] = cvt<TY>(v);
       ss += v * v;
     } else if (out == kOutAminusB) {
-      y[k] = (TY)(as_f64(xi) - (double)I - (pre_b ? bi : bv[k]));
+      y[k] = cvt<TY>(as_f64(xi) - as_f64(I) - (pre_b ? bi : bv[k]));
     } else if (out == kOutI) {
-      y[k] = (TY)I;
-    } else if (sizeof(TY) == 4 && sizeof(TX) <= 4) {
-      y[k] = (TY)(as_f32(xi) - (float)I);  // float pipeline: no float64 op
+      y[k] = cvt<TY>(I);
+    } else if (sizeof(T) == 4) {
+      y[k] = cvt<TY>(as_f32(xi) - (float)I);
     } else {
-      y[k] = (TY)(as_f64(xi) - (double)I);
+      y[k] = cvt<TY>(as_f64(xi) - as_f64(I));
     }
   };
   // loads of the points i+step .. i+cnt*step (cnt <= kAhead); indices past

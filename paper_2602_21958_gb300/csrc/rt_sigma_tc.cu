@@ -99,6 +99,11 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
   return *reinterpret_cast<uint32_t *>(&h);
 }
 
+// float64 -> float32 on the integer pipe (the conversion instruction runs at
+// the float64 rate on GB300); float32 passes through
+__device__ __forceinline__ float to_f32(double v) { return narrow_f32(v); }
+__device__ __forceinline__ float to_f32(float v) { return v; }
+
 // ----------------------------------------------------------------- kernel
 // X -> bf16, the A operand of the GEMM.  Column c's rows of all right-hand
 // sides are stacked: row m = rhs * nz + p at n_rhs * x_off + m * nr, so one 2D
@@ -114,7 +119,7 @@ __global__ void k_to_bf16(const ColDev *__restrict__ cols, const TX *__restrict_
   const TX *src = X + rhs * E + c.x_off;
   uint32_t *dst = Xb + ((int64_t)n_rhs * c.x_off + (int64_t)rhs * c.nz * c.nr) / 2;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n2; i += (int64_t)gridDim.x * blockDim.x)
-    dst[i] = pack_bf16((float)src[2 * i], (float)src[2 * i + 1]);
+    dst[i] = pack_bf16(to_f32(src[2 * i]), to_f32(src[2 * i + 1]));
 }
 
 // Bounded mbarrier wait that also gives up once another role raised *abort.
@@ -289,14 +294,18 @@ __global__ void __launch_bounds__(kT2Threads, 1)
             const float4 v = *reinterpret_cast<const float4 *>(tile + rr * kT2Ld + ci);
             const float *gp = gamma + c.g_off + (int64_t)p * nn;
             const int r0 = J.n0 + cs + ci;
-            const float a0 = gp[r0 % nn] * v.x, a1 = gp[(r0 + 1) % nn] * v.y;
-            const float a2 = gp[(r0 + 2) % nn] * v.z, a3 = gp[(r0 + 3) % nn] * v.w;
+            // frequency of ray r0 (ray = direction * nn + frequency), then the
+            // next three with wrap-around instead of a division each
+            int f0 = r0 - (r0 / nn) * nn;
+            const int f1 = f0 + 1 == nn ? 0 : f0 + 1, f2 = f1 + 1 == nn ? 0 : f1 + 1, f3 = f2 + 1 == nn ? 0 : f2 + 1;
+            const float a0 = gp[f0] * v.x, a1 = gp[f1] * v.y;
+            const float a2 = gp[f2] * v.z, a3 = gp[f3] * v.w;
             TS *dst = S + rhs * E + c.x_off + (int64_t)p * nr + r0;
             if (sizeof(TS) == 4) {
               *reinterpret_cast<float4 *>(dst) = make_float4(a0, a1, a2, a3);
             } else {
-              reinterpret_cast<double2 *>(dst)[0] = make_double2(a0, a1);
-              reinterpret_cast<double2 *>(dst)[1] = make_double2(a2, a3);
+              reinterpret_cast<double2 *>(dst)[0] = make_double2(widen_f64(a0), widen_f64(a1));
+              reinterpret_cast<double2 *>(dst)[1] = make_double2(widen_f64(a2), widen_f64(a3));
             }
           }
         }
