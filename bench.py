@@ -219,16 +219,18 @@ def run_ours(args, rank: int, world: int):
     E = sum(c.n for c in cols)
     n_inst = len(cols) * N_RHS
     hm = rt.Handle(cols, n_rhs=N_RHS, precision=rt.RT_P_MIXED, max_restart=RESTART_MIXED)
-    tune = hm.rt_autotune()  # apply launch shapes (RT_TUNE_CACHE if set), before any timed region
+    # apply launch shapes and the persistent solve's CTA shape and inner cycle
+    # length (RT_TUNE_CACHE if set), before any timed region
+    tune = hm.rt_autotune(solve=True)
     b = torch.empty(N_RHS * E, dtype=torch.float64, device=dev)
     hm.rt_apply(rt.RT_OP_RHS, None, b, fp64=True)       # every rhs slot = physical b
     b[E:] = torch.from_numpy(build_rhs(cols, E, rank).reshape(-1)).to(dev)
     x = torch.zeros_like(b)
     stream = torch.cuda.current_stream()
 
-    def solve(h, xx):
+    def solve(h, xx):  # inner_restart 0: the tuned inner cycle length
         return h.rt_solve(b, xx, tol=TOL, tol_inner=TOL_INNER, restart=RESTART_MIXED, max_outer=MAX_OUTER,
-                          inner_restart=INNER)
+                          inner_restart=0)
 
     for _ in range(args.warmup):
         info = solve(hm, x)

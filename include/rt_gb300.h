@@ -106,7 +106,8 @@ typedef struct rt_solve_opts {
                             what its workspace slot holds                             */
   int32_t max_outer;     /* restart cycles allowed                                      */
   int32_t use_x0;        /* 1: x holds the initial guess on entry; 0: start from x = 0  */
-  int32_t inner_restart; /* RT_P_MIXED: inner float32 GMRES cycle length (0 -> 20)      */
+  int32_t inner_restart; /* RT_P_MIXED: inner float32 GMRES cycle length (0 -> the
+                            length rt_autotune picked, else 20)                       */
   int32_t method;        /* RT_KRYLOV_GMRES (0) or RT_KRYLOV_BICGSTAB (1)               */
   int32_t max_iter;      /* BiCGStab: iteration cap per instance (0 -> 10000); with
                             BiCGStab, max_outer bounds the restarts from the true
@@ -174,6 +175,9 @@ typedef struct rt_tune_info {
   double ms_default;     /* time of the default shape; 0 if from cache                   */
   int32_t box_fb;        /* 3D boxes: frequencies per plane-sweep CTA (1, 2 or 4)        */
   int32_t box_cpt;       /* 3D boxes: cells per thread of the plane sweep (1, 2, 4, 8)   */
+  int32_t solve_per_sm;  /* flags & 2: CTAs per SM of the mixed batched solve (1 or 2)   */
+  int32_t solve_inner;   /* flags & 2: its inner cycle length (12, 20 or 30)             */
+  double solve_ms;       /* flags & 2: solve time of the choice                          */
 } rt_tune_info;
 
 /* Pick the launch shapes of the apply kernels by timing rt_apply(RT_OP_A) on
@@ -181,12 +185,16 @@ typedef struct rt_tune_info {
  * rt_apply and every solve of a 3D box uses it).  1D batches: the sweep tile
  * width and its load-ahead depth and the Sigma tile size (27 combinations).
  * 3D boxes: the plane sweep's frequencies per CTA and cells per thread (the
- * distinct feasible combinations of 1, 2, 4 and 1, 2, 4, 8).  When the
+ * distinct feasible combinations of 1, 2, 4 and 1, 2, 4, 8).  With flags & 2,
+ * on a mixed-precision 1D batch of more than one instance, also the persistent
+ * solve: one 512-thread or two 256-thread CTAs per SM (the Krylov workspace is
+ * re-allocated to match) and the inner cycle length used when
+ * rt_solve_opts.inner_restart is 0, timed on full solves of the batch with the
+ * internal right-hand side (several seconds for a large batch).  When the
  * environment variable RT_TUNE_CACHE names a file, a previous result for the
  * same problem signature is read from it (JSON lines) instead of re-timing,
- * unless flags & 1; new results are appended.  Allocates two temporary
- * vectors.  out may be NULL.  (Implementation choice; the paper has no
- * counterpart.) */
+ * unless flags & 1; new results are appended.  Allocates temporary vectors.
+ * out may be NULL.  (Implementation choice; the paper has no counterpart.) */
 int rt_autotune(rt_handle *h, int32_t flags, rt_tune_info *out, void *stream);
 
 /* Allocation-free variant of rt_apply, for callers that cannot allocate

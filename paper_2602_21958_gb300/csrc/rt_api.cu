@@ -264,11 +264,18 @@ int build_column(const rt_desc *d, ColumnHost &ch) {
 // Workspace: one slot per resident CTA of the solve kernel.  A slot's basis
 // bytes are shared by whatever instance runs there, so the restart length of an
 // instance is (slot bytes / instance bytes) - 1, capped by the request.
-int alloc_workspace(rt_handle *h, int max_restart) {
+// per_sm: concurrently resident CTAs of the mixed batched solve per SM (1 or
+// 2); a second call replaces the previous workspace.
+int alloc_workspace(rt_handle *h, int max_restart, int per_sm = 1) {
   const int m = std::max(1, std::min(max_restart, rt::max_krylov()));
   int dev = 0;
   RT_CUDA(cudaGetDevice(&dev));
   RT_CUDA(cudaDeviceGetAttribute(&h->n_sm, cudaDevAttrMultiProcessorCount, dev));
+  if (h->ws.V) cudaFree(h->ws.V);
+  if (h->ws.S) cudaFree(h->ws.S);
+  if (h->ws.H) cudaFree(h->ws.H);
+  h->ws.V = nullptr;
+  h->ws.S = h->ws.H = nullptr;
   const int n_inst = h->n_cols * h->n_rhs;
   const int64_t ld = (h->nmax + 31) / 32 * 32;
   const int64_t elt = h->precision == RT_P_FP64 ? 8 : 4;
@@ -286,13 +293,15 @@ int alloc_workspace(rt_handle *h, int max_restart) {
   const int64_t want_cap = bytes_per_elt(m) * ld;
   const double fixed = (double)(ld * 8 + hld * 8);
   const double budget = 0.6 * (double)free_b;
-  // one 512-thread CTA per SM: a heavy instance gets a whole SM's bandwidth
-  int slots = std::min(n_inst, h->n_sm);
+  // one 512-thread CTA per SM (a heavy instance gets a whole SM's bandwidth),
+  // or two 256-thread CTAs
+  int slots = std::min(n_inst, h->n_sm * per_sm);
   while (slots > 1 && budget / slots < fixed + (double)min_cap) --slots;
   if (budget < fixed + (double)min_cap) return fail(RT_ERR_OOM, "not enough device memory for one Krylov workspace");
   int64_t cap = (int64_t)std::min<double>((double)want_cap, budget / slots - fixed);
   cap = cap / 256 * 256;
   h->ws.slots = slots;
+  h->ws.per_sm = per_sm;
   h->ws.m = m;
   h->ws.ld = ld;
   h->ws.cap_bytes = cap;
@@ -300,11 +309,17 @@ int alloc_workspace(rt_handle *h, int max_restart) {
   RT_CUDA(cudaMalloc(&h->ws.V, (size_t)slots * cap));
   RT_CUDA(cudaMalloc(&h->ws.S, (size_t)slots * ld * sizeof(double)));
   RT_CUDA(cudaMalloc(&h->ws.H, (size_t)slots * hld * sizeof(double)));
-  RT_CUDA(cudaMalloc(&h->so.outer, n_inst * sizeof(int32_t)));
-  RT_CUDA(cudaMalloc(&h->so.inner, n_inst * sizeof(int32_t)));
-  RT_CUDA(cudaMalloc(&h->so.status, n_inst * sizeof(int32_t)));
-  RT_CUDA(cudaMalloc(&h->so.relres, n_inst * sizeof(double)));
-  RT_CUDA(cudaMalloc(&h->so.bytes, n_inst * sizeof(double)));
+  if (!h->so.outer) {
+    RT_CUDA(cudaMalloc(&h->so.outer, n_inst * sizeof(int32_t)));
+    RT_CUDA(cudaMalloc(&h->so.inner, n_inst * sizeof(int32_t)));
+    RT_CUDA(cudaMalloc(&h->so.status, n_inst * sizeof(int32_t)));
+    RT_CUDA(cudaMalloc(&h->so.relres, n_inst * sizeof(double)));
+    RT_CUDA(cudaMalloc(&h->so.bytes, n_inst * sizeof(double)));
+  }
+  if (h->solve_graph) {  // captured with the old workspace
+    cudaGraphExecDestroy(h->solve_graph);
+    h->solve_graph = nullptr;
+  }
   return RT_OK;
 }
 
@@ -808,6 +823,98 @@ int autotune_box(rt_handle *h, int flags, rt_tune_info *out, cudaStream_t s, con
   return report(best, first, 0);
 }
 
+// Persistent mixed solve of a 1D batch: CTAs per SM (1 x 512 or 2 x 256
+// threads; the workspace is re-allocated to match) and the inner float32
+// cycle length, timed on full solves of the handle's own batch with the
+// internal right-hand side (tolerance 1e-10, tol_inner 0.1): first the two CTA
+// shapes at cycle length 20, then cycle lengths 12 and 30 with the faster
+// shape.  RT_TUNE_CACHE as for the apply shapes.
+int autotune_solve(rt_handle *h, int flags, cudaStream_t s, const char *sig, const char *path,
+                   rt_tune_info &loc) {
+  if (path && !(flags & 1)) {
+    if (FILE *f = std::fopen(path, "r")) {
+      char line[512];
+      int ps = 0, mi = 0;
+      double ms = 0;
+      bool hit = false;
+      while (std::fgets(line, sizeof line, f)) {
+        const char *q = std::strstr(line, "\"sig\": \"");
+        if (!q || std::strncmp(q + 8, sig, std::strlen(sig)) != 0 || q[8 + std::strlen(sig)] != '"') continue;
+        const char *r = std::strstr(line, "\"solve_per_sm\":");
+        if (r && std::sscanf(r, "\"solve_per_sm\": %d, \"solve_inner\": %d, \"solve_ms\": %lf", &ps, &mi, &ms) == 3)
+          hit = true;
+      }
+      std::fclose(f);
+      if (hit) {
+        if (ps != h->ws.per_sm) {
+          const int rc = alloc_workspace(h, h->max_restart, ps);
+          if (rc != RT_OK) return rc;
+        }
+        h->tune.solve_m_in = mi;
+        loc.solve_per_sm = ps;
+        loc.solve_inner = mi;
+        loc.solve_ms = ms;
+        return RT_OK;
+      }
+    }
+  }
+  const int64_t len = h->E * h->n_rhs;
+  double *x = nullptr;
+  RT_CUDA(cudaMalloc(&x, len * sizeof(double)));
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const int m = std::min(32, h->ws.m);
+  int rc = RT_OK;
+  auto time_solve = [&](int m_in, double &ms) -> int {
+    cudaEventRecord(e0, s);
+    int e = rt::launch_solve(h, nullptr, x, 1e-10, 0.1, m, 60, 0, s, std::min(m_in, h->ws.m));
+    cudaEventRecord(e1, s);
+    if (e || cudaEventSynchronize(e1) != cudaSuccess) return fail(RT_ERR_CUDA, "autotune solve launch");
+    float f = 0.f;
+    cudaEventElapsedTime(&f, e0, e1);
+    ms = f;
+    return RT_OK;
+  };
+  double best = 1e300;
+  int best_ps = h->ws.per_sm, best_mi = 20;
+  for (int ps = 1; ps <= 2 && rc == RT_OK; ++ps) {
+    if (ps != h->ws.per_sm && (rc = alloc_workspace(h, h->max_restart, ps)) != RT_OK) break;
+    double ms = 0;
+    if ((rc = time_solve(20, ms)) != RT_OK) break;
+    if (ms < best) {
+      best = ms;
+      best_ps = ps;
+    }
+  }
+  if (rc == RT_OK && best_ps != h->ws.per_sm) rc = alloc_workspace(h, h->max_restart, best_ps);
+  for (int mi : {12, 30}) {
+    if (rc != RT_OK || mi > h->ws.m) break;
+    double ms = 0;
+    if ((rc = time_solve(mi, ms)) != RT_OK) break;
+    if (ms < best) {
+      best = ms;
+      best_mi = mi;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(x);
+  if (rc != RT_OK) return rc;
+  h->tune.solve_m_in = best_mi;
+  loc.solve_per_sm = best_ps;
+  loc.solve_inner = best_mi;
+  loc.solve_ms = best;
+  if (path) {
+    if (FILE *f = std::fopen(path, "a")) {
+      std::fprintf(f, "{\"sig\": \"%s\", \"solve_per_sm\": %d, \"solve_inner\": %d, \"solve_ms\": %.3f}\n", sig,
+                   best_ps, best_mi, best);
+      std::fclose(f);
+    }
+  }
+  return RT_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1014,12 +1121,14 @@ int rt_autotune(rt_handle *h, int32_t flags, rt_tune_info *out, void *stream) {
       }
       std::fclose(f);
       if (h->tune.from_cache) {
-        const int rc = build_apply_tiles(h, h->tune.ray_block, h->tune.sigma_pts);
+        int rc = build_apply_tiles(h, h->tune.ray_block, h->tune.sigma_pts);
         loc.ray_block = h->tune.ray_block;
         loc.ahead = h->tune.ahead;
         loc.sigma_points = h->tune.sigma_pts;
         loc.ms_best = h->tune.ms;
         loc.from_cache = 1;
+        if (rc == RT_OK && (flags & 2) && h->precision == RT_P_MIXED && h->n_cols * h->n_rhs > 1)
+          rc = autotune_solve(h, flags, s, sig, path, loc);
         if (out) *out = loc;
         return rc;
       }
@@ -1084,6 +1193,8 @@ int rt_autotune(rt_handle *h, int32_t flags, rt_tune_info *out, void *stream) {
   loc.ms_best = best;
   loc.ms_default = first;
   loc.from_cache = 0;
+  if ((flags & 2) && h->precision == RT_P_MIXED && h->n_cols * h->n_rhs > 1)
+    if ((rc = autotune_solve(h, flags, s, sig, path, loc)) != RT_OK) return rc;
   if (out) *out = loc;
   return RT_OK;
 }
@@ -1160,7 +1271,7 @@ int rt_solve(rt_handle *h, const double *b, double *x, const rt_solve_opts *o, r
                                                   o->use_x0, s, outer, inner, relres, status, bytes)
                        : rt::launch_grid_solve(h, bin ? bin : h->b_int, xio, o->tol, o->tol_inner, o->restart,
                                                o->max_outer, o->use_x0, s, outer, inner, relres, status, bytes,
-                                               o->inner_restart > 0 ? o->inner_restart : 20);
+                                               o->inner_restart > 0 ? o->inner_restart : 20);  // single instance
     RT_CUDA(cudaEventRecord(e1, s));
     if (e != 0) {
       cudaEventDestroy(e0);
@@ -1204,7 +1315,7 @@ int rt_solve(rt_handle *h, const double *b, double *x, const rt_solve_opts *o, r
   RT_CUDA(cudaEventCreate(&e1));
   // the launch (queue reset + persistent kernel) is captured once into a CUDA
   // graph and replayed while (b, x, options) stay the same
-  const int m_in = o->inner_restart > 0 ? o->inner_restart : 20;
+  const int m_in = o->inner_restart > 0 ? o->inner_restart : (h->tune.solve_m_in > 0 ? h->tune.solve_m_in : 20);
   unsigned long long key[10];
   key[0] = (unsigned long long)(uintptr_t)bin;
   key[1] = (unsigned long long)(uintptr_t)xio;

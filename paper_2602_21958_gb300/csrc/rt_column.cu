@@ -922,11 +922,17 @@ __device__ __forceinline__ void tri_solve(const double *Hc, int ld, const double
 // float32 GMRES(m_in) on the float32 operator (relative tolerance tol_inner):
 //   z_i ~ A^-1 v_i (float32), w = A z_i (float64 operator), orthogonalise w,
 //   x += Z y at the end of a cycle; cycles restart from the true residual.
-// One CTA per (column, rhs) instance, as k_solve.
-__global__ void __launch_bounds__(kNT, 1) k_solve_nested(SolveParams p) {
-  __shared__ __align__(16) double sm[7 * kSigBuf];  // Sigma work buffers (inner: 16 x kSig16WarpBytes)
+// One CTA per (column, rhs) instance, as k_solve.  NT threads per CTA: 512
+// (one CTA per SM) or 256 (two per SM, so one instance's latency-bound phases
+// overlap another's streaming); shared memory scales with the warps, the
+// frequency kernel is staged when it fits RWC floats (else read from L2).
+template <int NT>
+__global__ void __launch_bounds__(NT, 512 / NT) k_solve_nested(SolveParams p) {
+  constexpr int kSmD = (NT / 32) * kSig16WarpBytes / 8;  // doubles of Sigma work buffers
+  constexpr int kRWC = NT == 512 ? kRwCache : kRwCache / 2;
+  __shared__ __align__(16) double sm[kSmD];  // Sigma work buffers (inner: a kSig16WarpBytes part per warp)
   constexpr int kRed = (kDots > kD16 ? kDots : kD16) + 1;  // widest block_sum
-  __shared__ double red[(kNT / 32) * kRed];
+  __shared__ double red[(NT / 32) * kRed];
   __shared__ double outb[kRed];
   __shared__ double hbuf[2 * (kMaxM + 8)];
   __shared__ double ybuf[kMaxM + 8];
@@ -934,7 +940,7 @@ __global__ void __launch_bounds__(kNT, 1) k_solve_nested(SolveParams p) {
   __shared__ double hf64[kMaxM + 8];
   __shared__ int s_q;
   __shared__ double s_val[4];
-  __shared__ float rw_s[kRwCache];  // float32 frequency kernel of the current column
+  __shared__ float rw_s[kRWC];  // float32 frequency kernel of the current column
   __shared__ float uwl_s[2 * kUwlCache];  // float32 angular factors Uw | Ul of the current column
   uint8_t *slot = reinterpret_cast<uint8_t *>(p.V) + (int64_t)blockIdx.x * p.cap;
   double *S64 = p.S + (int64_t)blockIdx.x * p.ld;
@@ -975,7 +981,7 @@ __global__ void __launch_bounds__(kNT, 1) k_solve_nested(SolveParams p) {
       for (int k = threadIdx.x; k < len; k += blockDim.x) rw_s[k] = p.t32.LR[c.lr_off + k];
       __syncthreads();
       lr_c = rw_s;
-    } else if (!c.rdiag && c.psi_off < 0 && c.nn * c.nn <= kRwCache) {
+    } else if (!c.rdiag && c.psi_off < 0 && c.nn * c.nn <= kRWC) {
       for (int k = threadIdx.x; k < c.nn * c.nn; k += blockDim.x) rw_s[k] = p.t32.RwT[c.r_off + k];
       __syncthreads();
       rw_c = rw_s;
@@ -1011,7 +1017,7 @@ __global__ void __launch_bounds__(kNT, 1) k_solve_nested(SolveParams p) {
         rn = bn;
         rsrc = bv;
       } else {
-        sigma_column<double, double>(c, p.t64, x, S64, sm, 4 * kSigBuf);
+        sigma_column<double, double>(c, p.t64, x, S64, sm, kSmD < 4 * kSigBuf ? kSmD : 4 * kSigBuf);
         double a[1] = {sweep_column<double, double, double, 2, kOutResid>(c, p.t64, p.cm, S64, nullptr, x, bv,
                                                                            S64, false)};
         block_sum<1>(a, red, outb);
@@ -1055,7 +1061,8 @@ __global__ void __launch_bounds__(kNT, 1) k_solve_nested(SolveParams p) {
             sigma_column_h16(c, p.t32, uj, S32, reinterpret_cast<unsigned char *>(sm),
                              rw_c ? rw_c : p.t32.RwT + c.r_off, uw_c, ul_c, lr_c);
           else
-            sigma_column<float, __half>(c, p.t32, uj, S32, reinterpret_cast<float *>(sm), 8 * kSigBuf, rw_c);
+            sigma_column<float, __half>(c, p.t32, uj, S32, reinterpret_cast<float *>(sm),
+                                        2 * kSmD < 8 * kSigBuf ? 2 * kSmD : 8 * kSigBuf, rw_c);
           // Arnoldi on K = Lambda Sigma (A = Id - K, same Krylov space): the
           // sweep emits K u_j and needs no read of u_j
           sweep_column<float, __half, float, 4, kOutI>(c, p.t32, p.cm, S32, nullptr, uj, nullptr, W32, false);
@@ -1097,7 +1104,7 @@ __global__ void __launch_bounds__(kNT, 1) k_solve_nested(SolveParams p) {
         // (projected/original norm >= 0.3 measured), and A's Hessenberg column
         // is e_i + h)
         double *w = Vo + (int64_t)(i + 1) * ldv;
-        sigma_column<double, float>(c, p.t64, zi, S64, sm, 4 * kSigBuf);
+        sigma_column<double, float>(c, p.t64, zi, S64, sm, kSmD < 4 * kSigBuf ? kSmD : 4 * kSigBuf);
         sweep_column<double, float, double, 2, kOutAminusB>(c, p.t64, p.cm, S64, nullptr, zi, vi, w, false);
         __syncthreads();
         bpe += 4.0 + 8.0 + 8.0 + 4.0 + 8.0 + 8.0;
@@ -1465,7 +1472,8 @@ int launch_solve(rt_handle *h, const double *b, double *x, double tol, double to
   cudaError_t e = cudaMemsetAsync(h->d_queue + 1, 0, sizeof(int), s);
   if (e != cudaSuccess) return (int)e;
   if (h->precision == 0) k_solve<double><<<h->ws.slots, kNT, 0, s>>>(p);
-  else k_solve_nested<<<h->ws.slots, kNT, 0, s>>>(p);
+  else if (h->ws.per_sm == 2) k_solve_nested<256><<<h->ws.slots, 256, 0, s>>>(p);
+  else k_solve_nested<512><<<h->ws.slots, 512, 0, s>>>(p);
   return (int)cudaGetLastError();
 }
 

@@ -18,6 +18,7 @@ struct SolveOut {
 
 struct Workspace {
   int slots = 0;           // concurrently resident instances (persistent CTAs)
+  int per_sm = 1;          // mixed batched solve: CTAs per SM (1: 512 threads, 2: 256)
   int m = 0;               // largest Krylov basis length a solve may ask for
   int64_t ld = 0;          // float64 scratch length per slot (>= largest column)
   int64_t cap_bytes = 0;   // Krylov basis bytes per slot (shared by whatever instance runs there)
@@ -36,6 +37,7 @@ struct Tune {
   int from_cache = 0;
   int box_fb = 0;        // 3D sweep: cap on frequencies per CTA (0: largest that fits)
   int box_cpt = 0;       // 3D sweep: cells per thread (0: 8, adjusted to the plane)
+  int solve_m_in = 0;    // mixed batched solve: inner cycle length (0: 20)
 };
 
 constexpr int kBoxSmemMax = 220 * 1024;  // shared-memory budget of one 3D sweep CTA

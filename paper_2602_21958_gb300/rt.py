@@ -56,7 +56,8 @@ EXPORTS = ("rt_create", "rt_create_batch", "rt_vector_length", "rt_apply", "rt_a
 class rt_tune_info(C.Structure):
     _fields_ = [("ray_block", C.c_int32), ("ahead", C.c_int32), ("sigma_points", C.c_int32),
                 ("from_cache", C.c_int32), ("ms_best", C.c_double), ("ms_default", C.c_double),
-                ("box_fb", C.c_int32), ("box_cpt", C.c_int32)]
+                ("box_fb", C.c_int32), ("box_cpt", C.c_int32), ("solve_per_sm", C.c_int32),
+                ("solve_inner", C.c_int32), ("solve_ms", C.c_double)]
 
 _lib = None
 
@@ -204,13 +205,17 @@ class Handle:
         library's static device array (see include/rt_gb300.h)."""
         _check(load().rt_apply_noalloc(self._h, op, int(bool(fp64)), _ptr(x), _ptr(y), _stream_ptr(stream)))
 
-    def rt_autotune(self, force: bool = False, stream=None) -> dict:
-        """Time the apply kernels' launch shapes on this problem and keep the fastest."""
+    def rt_autotune(self, force: bool = False, stream=None, solve: bool = False) -> dict:
+        """Time the apply kernels' launch shapes on this problem and keep the
+        fastest; with ``solve`` also the persistent mixed solve's CTA shape and
+        inner cycle length (batches)."""
         t = rt_tune_info()
-        _check(load().rt_autotune(self._h, 1 if force else 0, C.byref(t), _stream_ptr(stream)))
+        flags = (1 if force else 0) | (2 if solve else 0)
+        _check(load().rt_autotune(self._h, flags, C.byref(t), _stream_ptr(stream)))
         return {"ray_block": t.ray_block, "ahead": t.ahead, "sigma_points": t.sigma_points,
                 "from_cache": bool(t.from_cache), "ms_best": t.ms_best, "ms_default": t.ms_default,
-                "box_fb": t.box_fb, "box_cpt": t.box_cpt}
+                "box_fb": t.box_fb, "box_cpt": t.box_cpt, "solve_per_sm": t.solve_per_sm,
+                "solve_inner": t.solve_inner, "solve_ms": t.solve_ms}
 
     def rt_set_sigma_rank(self, tol: float) -> int:
         """Truncate the float32 operator's frequency kernels at ``tol``

@@ -320,3 +320,28 @@ def test_autotune_picks_a_shape_and_caches_it(rt, tmp_path, monkeypatch):
     t2 = h2.rt_autotune()
     assert t2["from_cache"] and (t2["ray_block"], t2["ahead"], t2["sigma_points"]) == \
         (t["ray_block"], t["ahead"], t["sigma_points"])
+
+
+def test_autotune_persistent_solve_keeps_results_and_caches(rt, tmp_path, monkeypatch):
+    """rt_autotune with the solve flag times the mixed batched solve's CTA
+    shape (1 x 512 or 2 x 256 threads per SM) and inner cycle length; the
+    solve afterwards (inner_restart = 0: the tuned length) still reaches the
+    LU solution, and a second handle reads the choice from RT_TUNE_CACHE."""
+    cache = tmp_path / "tune.jsonl"
+    monkeypatch.setenv("RT_TUNE_CACHE", str(cache))
+    probs = [small_problems()[k] for k in ("crd", "r2_ragged", "qsc", "minimal")]
+    h = rt.Handle(probs, n_rhs=2, precision=rt.RT_P_MIXED, max_restart=32)
+    t = h.rt_autotune(force=True, solve=True)
+    assert t["solve_per_sm"] in (1, 2) and t["solve_inner"] in (12, 20, 30) and t["solve_ms"] > 0
+    E = sum(p.n for p in probs)
+    x = torch.zeros(2 * E, dtype=torch.float64, device="cuda:0")
+    info = h.rt_solve(None, x, tol=1e-12, tol_inner=1e-2, max_outer=40, inner_restart=0)
+    torch.cuda.synchronize()
+    assert info["status"] == 0, info
+    ref = np.concatenate([O.solve_dense(p) for p in probs])
+    for r in range(2):
+        a, _ = rel(x.cpu().numpy()[r * E:(r + 1) * E], ref)
+        assert a < 1e-10
+    h2 = rt.Handle(probs, n_rhs=2, precision=rt.RT_P_MIXED, max_restart=32)
+    t2 = h2.rt_autotune(solve=True)
+    assert t2["from_cache"] and (t2["solve_per_sm"], t2["solve_inner"]) == (t["solve_per_sm"], t["solve_inner"])
