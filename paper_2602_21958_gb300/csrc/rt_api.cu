@@ -118,7 +118,7 @@ void free_handle(rt_handle *h) {
                   h->so.outer, h->so.inner, h->so.status, h->so.relres, h->so.bytes,
                   h->stage_x, h->stage_y, h->d_sig_tiles, h->d_sw_tiles, h->apply_S,
                   h->d_tc_jobs, h->d_tc_off, h->d_tc_tiles, h->d_tc_xb, h->d_tc_maps, h->d_err, h->d_geo,
-                  h->chi64, h->chi32, h->box_w064, h->box_bt64, h->g_part, h->g_red, h->g_coef, h->g_r, h->Q64, h->Q32, h->lr32};
+                  h->chi64, h->chi32, h->box_w064, h->box_bt64, h->box_kap32, h->box_phi32, h->g_part, h->g_red, h->g_coef, h->g_r, h->Q64, h->Q32, h->lr32};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (h->solve_graph) cudaGraphExecDestroy(h->solve_graph);

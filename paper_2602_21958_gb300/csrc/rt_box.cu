@@ -291,7 +291,14 @@ __global__ void k_box_from_sweep(const T *__restrict__ S, double *__restrict__ y
 // SL: source in the sweep layout, or null when the source is the thermal
 // term tsrc [npts][nn] (float64) broadcast over directions.
 // x, y: space-based layout; x unused for kOutI.
-template <typename T, int FB, int CPT, int CB, typename TX, typename TY>
+// MODE: how the step weights are formed.  kSwChi: from the opacity chiN
+// (interpolated at the upwind point); kSwPre: precomputed (1 - e^-d, w1/d)
+// in cW0, cB (float64 boxes); kSwKap: the opacity is kappa(p) phi(nu)
+// (detected at creation), so shared memory holds one kappa per cell (kap)
+// instead of FB opacities and d = ds/2 phi (kappa_u + kappa_c).
+enum { kSwChi = 0, kSwPre = 1, kSwKap = 2 };
+
+template <typename T, int FB, int CPT, int CB, typename TX, typename TY, int MODE>
 __global__ void __launch_bounds__(512) k_sweep3d(BoxDev bx, const double *__restrict__ geo,
                                                  const T *__restrict__ chiN, int npad,
                                                  const Pack<T, FB> *__restrict__ SL,
@@ -299,15 +306,21 @@ __global__ void __launch_bounds__(512) k_sweep3d(BoxDev bx, const double *__rest
                                                  TY *__restrict__ y, int out, int inflow,
                                                  const double *__restrict__ I_top,
                                                  const double *__restrict__ I_bot,
-                                                 const T *__restrict__ cW0, const T *__restrict__ cB) {
+                                                 const T *__restrict__ cW0, const T *__restrict__ cB,
+                                                 const T *__restrict__ kap, const T *__restrict__ phi) {
   using P = Pack<T, FB>;
   extern __shared__ __align__(16) unsigned char sw_smem[];
   const int nx = bx.nx, ny = bx.ny, nz = bx.nz, nn = bx.nn, nd = bx.nd;
   const int plane = nx * ny;
   const int nfb = (nn + FB - 1) / FB;
+  // kSwKap double-buffers I (the new plane's intensity is written as it is
+  // computed, so it needs no registers): sI and sIn swap every plane
+  constexpr bool dbl = MODE == kSwKap;
   P *sI = reinterpret_cast<P *>(sw_smem);
-  P *sS = sI + plane;
-  P *sC = sS + plane;
+  P *sIn = dbl ? sI + plane : sI;
+  P *const sS = sI + (dbl ? 2 : 1) * plane;
+  P *sC = sS + plane;                          // kSwChi: opacity of the previous plane
+  T *sK = reinterpret_cast<T *>(sS + plane);   // kSwKap: kappa of the previous plane
   const int d = blockIdx.x / nfb, fb = blockIdx.x - d * nfb, f0 = fb * FB;
   const int64_t npts = (int64_t)plane * nz;
   const int64_t nr = (int64_t)nd * nn;
@@ -349,8 +362,11 @@ __global__ void __launch_bounds__(512) k_sweep3d(BoxDev bx, const double *__rest
   auto load_chi = [&](int64_t p) -> P { return *reinterpret_cast<const P *>(chiB + p * 4); };
   // precomputed step weights (1 - e^-d, w1/d) in blocks of 2 frequencies:
   // [d][f / 2][p][f % 2]; the plane's opacity is then not needed
-  const bool pre = cW0 != nullptr;
+  constexpr bool pre = MODE == kSwPre;
   const int64_t cbase = pre ? ((int64_t)d * ((nn + 1) / 2) + (f0 >> 1)) * npts * 2 + (f0 & 1) : 0;
+  T hphi[FB];  // kSwKap: ds/2 phi(nu) of the CTA's frequencies
+#pragma unroll
+  for (int j = 0; j < FB; ++j) hphi[j] = MODE == kSwKap ? hds * phi[f0 + j] : T(0);
   // x and y of a cell: FB consecutive values, one vector access when aligned
   const bool vec = nn % FB == 0;
   using PX = Pack<TX, FB>;
@@ -368,7 +384,8 @@ __global__ void __launch_bounds__(512) k_sweep3d(BoxDev bx, const double *__rest
       if (c >= plane) continue;
       sI[c] = I0;
       sS[c] = load_src(pk + c);
-      sC[c] = load_chi(pk + c);
+      if (MODE == kSwChi) sC[c] = load_chi(pk + c);
+      if (MODE == kSwKap) sK[c] = kap[pk + c];
       const int64_t k = (pk + c) * nr + (int64_t)d * nn + f0;
 #pragma unroll
       for (int j = 0; j < FB; ++j) {
@@ -382,19 +399,22 @@ __global__ void __launch_bounds__(512) k_sweep3d(BoxDev bx, const double *__rest
   for (int s = 1; s < nz; ++s) {
     const int kp = k0 + s * step;
     const int64_t pk = (int64_t)kp * plane;
-    P In[CPT];
+    P In[dbl ? 1 : CPT];
 #pragma unroll
     for (int i0 = 0; i0 < CPT; i0 += CB) {
       // loads of CB cells issued together
       P Sc[CB], Cc[CB];
+      T Kc[CB];
       TX xv[CB][FB];
 #pragma unroll
       for (int u = 0; u < CB; ++u) {
         const int c = threadIdx.x + (i0 + u) * blockDim.x;
         const int cc = c < plane ? c : 0;
         Sc[u] = load_src(pk + cc);
-        if (pre) {  // Cc holds (1 - e^-d) and the gathered opacity is unused; Sc.. the source
+        if (MODE == kSwPre) {  // Cc holds 1 - e^-d
           Cc[u] = *reinterpret_cast<const P *>(cW0 + cbase + (pk + cc) * 2);
+        } else if (MODE == kSwKap) {
+          Kc[u] = kap[pk + cc];
         } else {
           Cc[u] = load_chi(pk + cc);
         }
@@ -419,8 +439,11 @@ __global__ void __launch_bounds__(512) k_sweep3d(BoxDev bx, const double *__rest
         const P I00 = sI[c00], I01 = sI[c01], I10 = sI[c10], I11 = sI[c11];
         const P S00 = sS[c00], S01 = sS[c01], S10 = sS[c10], S11 = sS[c11];
         P C00, C01, C10, C11, Bc;
-        if (pre) {
+        T Ku = 0;
+        if (MODE == kSwPre) {
           Bc = *reinterpret_cast<const P *>(cB + cbase + (pk + c) * 2);
+        } else if (MODE == kSwKap) {
+          Ku = w00 * sK[c00] + w01 * sK[c01] + w10 * sK[c10] + w11 * sK[c11] + Kc[u];
         } else {
           C00 = sC[c00], C01 = sC[c01], C10 = sC[c10], C11 = sC[c11];
         }
@@ -431,17 +454,19 @@ __global__ void __launch_bounds__(512) k_sweep3d(BoxDev bx, const double *__rest
           const T Iu = w00 * I00.v[j] + w01 * I01.v[j] + w10 * I10.v[j] + w11 * I11.v[j];
           const T Su = w00 * S00.v[j] + w01 * S01.v[j] + w10 * S10.v[j] + w11 * S11.v[j];
           T e, a, b;
-          if (pre) {
+          if (MODE == kSwPre) {
             const T w0 = Cc[u].v[j];
             e = (T)1 - w0;
             b = Bc.v[j];
             a = w0 - b;
+          } else if (MODE == kSwKap) {
+            step_coef<T>(hphi[j] * Ku, ie, e, a, b);
           } else {
             const T Cu = w00 * C00.v[j] + w01 * C01.v[j] + w10 * C10.v[j] + w11 * C11.v[j];
             step_coef<T>(hds * (Cu + Cc[u].v[j]), ie, e, a, b);
           }
           const T I = fma(e, Iu, fma(a, Su, b * Sc[u].v[j]));
-          In[i].v[j] = I;
+          In[dbl ? 0 : i].v[j] = I;
           yv.v[j] = out == kOutI ? cast_to<TY>(I) : cast_to<TY>(cast_to<T>(xv[u][j]) - I);
         }
         if (vec) {
@@ -451,6 +476,7 @@ __global__ void __launch_bounds__(512) k_sweep3d(BoxDev bx, const double *__rest
           for (int j = 0; j < FB; ++j)
             if (f0 + j < nn) y[k + j] = yv.v[j];
         }
+        if (dbl) sIn[c] = In[0];
       }
     }
     __syncthreads();
@@ -458,11 +484,17 @@ __global__ void __launch_bounds__(512) k_sweep3d(BoxDev bx, const double *__rest
     for (int i = 0; i < CPT; ++i) {
       const int c = threadIdx.x + i * blockDim.x;
       if (c >= plane) continue;
-      sI[c] = In[i];
+      if (!dbl) sI[c] = In[i];
       sS[c] = load_src(pk + c);
-      if (!pre) sC[c] = load_chi(pk + c);
+      if (MODE == kSwChi) sC[c] = load_chi(pk + c);
+      if (MODE == kSwKap) sK[c] = kap[pk + c];
     }
     __syncthreads();
+    if (dbl) {
+      P *t = sI;
+      sI = sIn;
+      sIn = t;
+    }
   }
 }
 
@@ -515,25 +547,44 @@ __global__ void k_box_coef64(BoxDev bx, const double *__restrict__ geo, const do
 }
 
 // ------------------------------------------------------------ host side
+// Step-weight mode of the sweep for one precision (see k_sweep3d).
+static int box_mode(const rt_handle *h, bool fp64) {
+  if (fp64) return h->box_w064 ? kSwPre : kSwChi;
+  return h->box_kap32 ? kSwKap : kSwChi;
+}
+
+// Shared memory of one sweep CTA: I and S of the plane (FB values per cell)
+// and the previous plane's opacity (FB values, or one kappa, or nothing).
+static size_t box_smem(const rt_handle *h, bool fp64, int fb) {
+  const size_t plane = (size_t)h->box.nx * h->box.ny, esz = fp64 ? 8 : 4;
+  const int mode = box_mode(h, fp64);
+  return plane * esz * (2 * fb + (mode == kSwChi ? fb : mode == kSwKap ? fb + 1 : 0));
+}
+
 // Launch shape of the sweep for one precision: FB frequencies per CTA and
 // CPT cells per thread (at most 512 threads).  The shapes are those whose
 // registers stay within 128 per thread without spills (float32: FB = 4 up to
-// CPT = 4, FB <= 2 up to 8; float64: FB = 2 up to 2, FB = 1 up to 8).  FB is
-// the largest whose three plane arrays fit the shared memory and whose plane
-// fits 512 threads, not wider than the frequencies need; rt_autotune may cap
-// FB and raise CPT.
-static int box_cpt_max(bool fp64, int fb) { return fp64 ? (fb == 2 ? 2 : 8) : (fb == 4 ? 4 : 8); }
+// CPT = 4 with the opacity, 8 with kappa, FB <= 2 up to 8; float64: FB = 2 up
+// to 2 with the opacity, 8 with precomputed weights, FB = 1 up to 8).  FB is
+// the largest whose plane arrays fit the shared memory and whose plane fits
+// 512 threads, not wider than the frequencies need; rt_autotune may cap FB
+// and raise CPT.
+static int box_cpt_max(bool fp64, int fb, int mode) {
+  if (fp64) return fb == 2 && mode != kSwPre ? 2 : 8;
+  return fb == 4 && mode != kSwKap ? 4 : 8;
+}
 
 static void box_shape(const rt_handle *h, bool fp64, int &fb, int &cpt) {
   const int plane = h->box.nx * h->box.ny;
-  const int esz = fp64 ? 8 : 4;
+  const int mode = box_mode(h, fp64);
   const int fbmax = fp64 ? 2 : 4;
   fb = h->tune.box_fb > 0 ? std::min(fbmax, h->tune.box_fb) : fbmax;
-  while (fb > 1 && (fb / 2 >= h->box.nn || 3ll * plane * fb * esz > kBoxSmemMax || plane > 512 * box_cpt_max(fp64, fb)))
+  while (fb > 1 && (fb / 2 >= h->box.nn || box_smem(h, fp64, fb) > (size_t)kBoxSmemMax ||
+                    plane > 512 * box_cpt_max(fp64, fb, mode)))
     fb /= 2;
   cpt = 1;
   while ((plane + cpt - 1) / cpt > 512) cpt *= 2;
-  if (h->tune.box_cpt > cpt) cpt = std::min(h->tune.box_cpt, box_cpt_max(fp64, fb));
+  if (h->tune.box_cpt > cpt) cpt = std::min(h->tune.box_cpt, box_cpt_max(fp64, fb, mode));
 }
 
 void box_effective_shape(const rt_handle *h, bool fp64, int &fb, int &cpt) { box_shape(h, fp64, fb, cpt); }
@@ -556,7 +607,7 @@ int64_t box_scratch_elems(const rt_handle *h, bool fp64) {
   return npts * h->box.nd * nfb * fb;
 }
 
-template <typename T, int FB, int CPT, typename TX, typename TY>
+template <typename T, int FB, int CPT, int MODE, typename TX, typename TY>
 static int sweep3d_run(rt_handle *h, const T *chiN, const void *S, const double *tsrc, const TX *x, TY *y, int out,
                        bool inflow, cudaStream_t s) {
   const BoxDev &bx = h->box;
@@ -564,33 +615,47 @@ static int sweep3d_run(rt_handle *h, const T *chiN, const void *S, const double 
   const int nfb = (bx.nn + FB - 1) / FB;
   const int nt = std::min(512, ((plane + CPT - 1) / CPT + 31) / 32 * 32);
   if ((int64_t)nt * CPT < plane) return (int)cudaErrorInvalidConfiguration;
-  const size_t smem = (size_t)3 * plane * FB * sizeof(T);
+  const size_t smem = box_smem(h, sizeof(T) == 8, FB);
   constexpr int CB = (8 / FB) < CPT ? (8 / FB) : CPT;  // cells whose loads are issued together
-  auto kern = k_sweep3d<T, FB, CPT, CB, TX, TY>;
+  auto kern = k_sweep3d<T, FB, CPT, CB, TX, TY, MODE>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return (int)e;
-  const T *cw = nullptr, *cb = nullptr;
-  if (sizeof(T) == 8 && h->box_w064) {
+  const T *cw = nullptr, *cb = nullptr, *kap = nullptr, *phi = nullptr;
+  if (MODE == kSwPre) {
     cw = reinterpret_cast<const T *>(h->box_w064);
     cb = reinterpret_cast<const T *>(h->box_bt64);
   }
+  if (MODE == kSwKap) {
+    kap = reinterpret_cast<const T *>(h->box_kap32);
+    phi = reinterpret_cast<const T *>(h->box_phi32);
+  }
   kern<<<bx.nd * nfb, nt, smem, s>>>(bx, h->d_geo, chiN, h->box_npad, static_cast<const Pack<T, FB> *>(S), tsrc, x,
-                                     y, out, inflow ? 1 : 0, h->d_Itop, h->d_Ibot, cw, cb);
+                                     y, out, inflow ? 1 : 0, h->d_Itop, h->d_Ibot, cw, cb, kap, phi);
   return (int)cudaGetLastError();
 }
 
-template <typename T, int FB, typename TX, typename TY>
+template <typename T, int FB, int MODE, typename TX, typename TY>
 static int sweep3d_cpt(rt_handle *h, int cpt, const T *chiN, const void *S, const double *tsrc, const TX *x, TY *y,
                        int out, bool inflow, cudaStream_t s) {
   constexpr bool f64 = sizeof(T) == 8;
-  constexpr int cmax = f64 ? (FB == 2 ? 2 : 8) : (FB == 4 ? 4 : 8);
-  if (cpt <= 1) return sweep3d_run<T, FB, 1>(h, chiN, S, tsrc, x, y, out, inflow, s);
-  if (cpt == 2 || cmax == 2) return sweep3d_run<T, FB, 2>(h, chiN, S, tsrc, x, y, out, inflow, s);
+  constexpr int cmax = f64 ? (FB == 2 && MODE != kSwPre ? 2 : 8) : (FB == 4 && MODE != kSwKap ? 4 : 8);
+  if (cpt <= 1) return sweep3d_run<T, FB, 1, MODE>(h, chiN, S, tsrc, x, y, out, inflow, s);
+  if (cpt == 2 || cmax == 2) return sweep3d_run<T, FB, 2, MODE>(h, chiN, S, tsrc, x, y, out, inflow, s);
   if constexpr (cmax >= 4) {
-    if (cpt == 4 || cmax == 4) return sweep3d_run<T, FB, 4>(h, chiN, S, tsrc, x, y, out, inflow, s);
+    if (cpt == 4 || cmax == 4) return sweep3d_run<T, FB, 4, MODE>(h, chiN, S, tsrc, x, y, out, inflow, s);
   }
-  if constexpr (cmax >= 8) return sweep3d_run<T, FB, 8>(h, chiN, S, tsrc, x, y, out, inflow, s);
+  if constexpr (cmax >= 8) return sweep3d_run<T, FB, 8, MODE>(h, chiN, S, tsrc, x, y, out, inflow, s);
   return (int)cudaErrorInvalidConfiguration;
+}
+
+template <typename T, int MODE, typename TX, typename TY>
+static int sweep3d_fb(rt_handle *h, int fb, int cpt, const T *chiN, const void *S, const double *tsrc, const TX *x,
+                      TY *y, int out, bool inflow, cudaStream_t s) {
+  if constexpr (sizeof(T) == 4) {
+    if (fb == 4) return sweep3d_cpt<T, 4, MODE>(h, cpt, chiN, S, tsrc, x, y, out, inflow, s);
+  }
+  if (fb == 2) return sweep3d_cpt<T, 2, MODE>(h, cpt, chiN, S, tsrc, x, y, out, inflow, s);
+  return sweep3d_cpt<T, 1, MODE>(h, cpt, chiN, S, tsrc, x, y, out, inflow, s);
 }
 
 template <typename T, typename TX, typename TY>
@@ -600,11 +665,13 @@ static int sweep3d(rt_handle *h, const void *S, const double *tsrc, const TX *x,
   const T *chiN = reinterpret_cast<const T *>(f64 ? (const void *)h->chi64 : (const void *)h->chi32);
   int fb, cpt;
   box_shape(h, f64, fb, cpt);
-  if constexpr (!f64) {
-    if (fb == 4) return sweep3d_cpt<T, 4>(h, cpt, chiN, S, tsrc, x, y, out, inflow, s);
+  const int mode = box_mode(h, f64);
+  if constexpr (f64) {
+    if (mode == kSwPre) return sweep3d_fb<T, kSwPre>(h, fb, cpt, chiN, S, tsrc, x, y, out, inflow, s);
+  } else {
+    if (mode == kSwKap) return sweep3d_fb<T, kSwKap>(h, fb, cpt, chiN, S, tsrc, x, y, out, inflow, s);
   }
-  if (fb == 2) return sweep3d_cpt<T, 2>(h, cpt, chiN, S, tsrc, x, y, out, inflow, s);
-  return sweep3d_cpt<T, 1>(h, cpt, chiN, S, tsrc, x, y, out, inflow, s);
+  return sweep3d_fb<T, kSwChi>(h, fb, cpt, chiN, S, tsrc, x, y, out, inflow, s);
 }
 
 template <typename T, typename TX>
@@ -718,6 +785,40 @@ int box_prepare(rt_handle *h, const double *chi) {
   if (e == cudaSuccess) e = cudaMalloc(&h->chi32, c32.size() * 4);
   if (e == cudaSuccess) e = cudaMemcpy(h->chi32, c32.data(), c32.size() * 4, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return (int)e;
+  // separable opacity chi(p, nu) = kappa(p) phi(nu) (to 1e-14): the float32
+  // sweep then keeps one kappa per cell; phi from the point of largest
+  // opacity, kappa(p) = chi(p, f*) / phi(f*) at that point's largest frequency
+  {
+    int64_t pr = 0;
+    int fr = 0;
+    double cmax = -1.0;
+    for (int64_t p = 0; p < npts; ++p)
+      for (int f = 0; f < nn; ++f)
+        if (chi[(size_t)p * nn + f] > cmax) {
+          cmax = chi[(size_t)p * nn + f];
+          pr = p;
+          fr = f;
+        }
+    bool sep = cmax > 0.0;
+    std::vector<double> phi(nn), kap(npts);
+    for (int f = 0; f < nn && sep; ++f) phi[f] = chi[(size_t)pr * nn + f];
+    for (int64_t p = 0; p < npts && sep; ++p) {
+      kap[p] = chi[(size_t)p * nn + fr] / cmax;
+      for (int f = 0; f < nn; ++f) {
+        const double c = chi[(size_t)p * nn + f];
+        if (std::fabs(kap[p] * phi[f] - c) > 1e-14 * std::fabs(c) + 1e-300) { sep = false; break; }
+      }
+    }
+    if (sep) {
+      std::vector<float> k32(kap.begin(), kap.end()), p32((size_t)npad, 0.f);
+      for (int f = 0; f < nn; ++f) p32[f] = (float)phi[f];
+      e = cudaMalloc(&h->box_kap32, k32.size() * 4);
+      if (e == cudaSuccess) e = cudaMemcpy(h->box_kap32, k32.data(), k32.size() * 4, cudaMemcpyHostToDevice);
+      if (e == cudaSuccess) e = cudaMalloc(&h->box_phi32, p32.size() * 4);
+      if (e == cudaSuccess) e = cudaMemcpy(h->box_phi32, p32.data(), p32.size() * 4, cudaMemcpyHostToDevice);
+      if (e != cudaSuccess) return (int)e;
+    }
+  }
   // float64 step weights, when they take at most a quarter of the free memory
   const int64_t ncoef = (int64_t)h->box.nd * npts * ((nn + 1) / 2) * 2;
   size_t free_b = 0, total_b = 0;

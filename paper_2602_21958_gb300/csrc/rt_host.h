@@ -110,6 +110,7 @@ struct rt_handle {
   double lr_tol = 0.0;
   std::vector<double> h_rw, h_wnu;   // host copies: R w (as RwT) and w_nu per column
   double *box_w064 = nullptr, *box_bt64 = nullptr;  // 3D: float64 step weights, or null
+  float *box_kap32 = nullptr, *box_phi32 = nullptr; // 3D: separable opacity kappa [n_pts], phi [npad], or null
   double *g_part = nullptr, *g_red = nullptr, *g_coef = nullptr, *g_r = nullptr;
   int64_t stage_len = 0;
   bool has_dense = false;
