@@ -30,6 +30,17 @@
  * records a message retrievable by rt_last_error() (thread-local).  On error
  * the output buffers are unspecified; the handle stays valid unless rt_create
  * failed (then *out is NULL).
+ *
+ * Fault injection (failure-detection tests; implementation property, the paper
+ * has none).  The environment variable RT_FAULT, read at each call:
+ *   alloc     rt_create / rt_create_batch return RT_ERR_OOM before any device call;
+ *   launch    rt_apply, rt_apply_noalloc, rt_solve, rt_arnoldi return RT_ERR_CUDA
+ *             before launching;
+ *   nan_input rt_solve returns RT_ERR_NONFINITE (info->status too) without launching;
+ *   stall     the bounded device waits of the tensor-core Sigma (mixed handles with a
+ *             dense kernel) poll once, give up, drain their own copies and MMAs, free
+ *             their tensor memory, and the call returns RT_ERR_TIMEOUT; the handle
+ *             stays usable.
  */
 #ifndef RT_GB300_H
 #define RT_GB300_H

@@ -26,6 +26,39 @@ int fail(int code, const std::string &msg) {
   return code;
 }
 
+// Host-side fault injection for failure-detection tests (no GPU fault is
+// ever made): the environment variable RT_FAULT, read at each call, set to
+//   alloc     -> rt_create / rt_create_batch fail with RT_ERR_OOM before any
+//                device call,
+//   launch    -> rt_apply, rt_apply_noalloc, rt_solve and rt_arnoldi fail with
+//                RT_ERR_CUDA before launching anything,
+//   nan_input -> rt_solve reports a non-finite input (RT_ERR_NONFINITE, info
+//                filled) without launching,
+//   stall     -> the bounded waits of the tensor-core Sigma poll once, so they
+//                give up and the call returns RT_ERR_TIMEOUT (the kernel
+//                drains its own work and frees its tensor memory first).
+enum Fault { kFaultNone = 0, kFaultAlloc, kFaultLaunch, kFaultNan, kFaultStall };
+
+int fault_now() {
+  const char *f = std::getenv("RT_FAULT");
+  if (!f || !*f) return kFaultNone;
+  if (!std::strcmp(f, "alloc")) return kFaultAlloc;
+  if (!std::strcmp(f, "launch")) return kFaultLaunch;
+  if (!std::strcmp(f, "nan_input")) return kFaultNan;
+  if (!std::strcmp(f, "stall")) return kFaultStall;
+  return kFaultNone;
+}
+
+// RT_FAULT=stall for the duration of one call: pipeline waits poll once
+struct StallScope {
+  rt_handle *h;
+  long long saved;
+  explicit StallScope(rt_handle *hh) : h(hh), saved(hh->wait_limit) {
+    if (fault_now() == kFaultStall) h->wait_limit = 1;
+  }
+  ~StallScope() { h->wait_limit = saved; }
+};
+
 #define RT_CUDA(call)                                                                        \
   do {                                                                                       \
     cudaError_t e_ = (call);                                                                 \
@@ -925,6 +958,8 @@ const char *rt_version(void) { return "rt_gb300 0.1 (sm_103a)"; }
 
 int rt_create(const rt_desc *desc, int32_t n_rhs, int32_t precision, int32_t max_restart,
               rt_handle **out) {
+  if (out) *out = nullptr;
+  if (fault_now() == kFaultAlloc) return fail(RT_ERR_OOM, "RT_FAULT=alloc: injected device allocation failure");
   if (!desc) return fail(RT_ERR_ARG, "null descriptor");
   if (desc->dims == 3) return create_box(desc, n_rhs, precision, max_restart, out);
   return create_columns(desc, 1, n_rhs, precision, max_restart, out);
@@ -932,6 +967,8 @@ int rt_create(const rt_desc *desc, int32_t n_rhs, int32_t precision, int32_t max
 
 int rt_create_batch(const rt_desc *cols, int32_t n_cols, int32_t n_rhs, int32_t precision,
                     int32_t max_restart, rt_handle **out) {
+  if (out) *out = nullptr;
+  if (fault_now() == kFaultAlloc) return fail(RT_ERR_OOM, "RT_FAULT=alloc: injected device allocation failure");
   if (!cols) return fail(RT_ERR_ARG, "null descriptor array");
   return create_columns(cols, n_cols, n_rhs, precision, max_restart, out);
 }
@@ -940,6 +977,8 @@ int64_t rt_vector_length(const rt_handle *h) { return h ? h->E * h->n_rhs : 0; }
 
 int rt_apply(rt_handle *h, int32_t op, int32_t fp64, const double *x, double *y, void *stream) {
   if (!h) return fail(RT_ERR_ARG, "null handle");
+  if (fault_now() == kFaultLaunch) return fail(RT_ERR_CUDA, "RT_FAULT=launch: injected launch failure");
+  StallScope stall(h);
   if (op < RT_OP_A || op > RT_OP_RHS) return fail(RT_ERR_ARG, "unknown op");
   if (!y || (!x && op != RT_OP_RHS)) return fail(RT_ERR_ARG, "null vector");
   cudaStream_t s = (cudaStream_t)stream;
@@ -979,6 +1018,8 @@ int rt_apply(rt_handle *h, int32_t op, int32_t fp64, const double *x, double *y,
 
 int rt_apply_noalloc(rt_handle *h, int32_t op, int32_t fp64, const double *x, double *y, void *stream) {
   if (!h) return fail(RT_ERR_ARG, "null handle");
+  if (fault_now() == kFaultLaunch) return fail(RT_ERR_CUDA, "RT_FAULT=launch: injected launch failure");
+  StallScope stall(h);
   if (op < RT_OP_A || op > RT_OP_RHS) return fail(RT_ERR_ARG, "unknown op");
   if (!y || (!x && op != RT_OP_RHS)) return fail(RT_ERR_ARG, "null vector");
   if ((x && !is_device_ptr(x)) || !is_device_ptr(y))
@@ -1201,6 +1242,7 @@ int rt_autotune(rt_handle *h, int32_t flags, rt_tune_info *out, void *stream) {
 
 int rt_arnoldi(rt_handle *h, const double *v0, int32_t m, double *H, int32_t *m_done, void *stream) {
   if (!h || !H || !m_done) return fail(RT_ERR_ARG, "null handle, H or m_done");
+  if (fault_now() == kFaultLaunch) return fail(RT_ERR_CUDA, "RT_FAULT=launch: injected launch failure");
   if (h->dims != 3 && !rt::single_instance(h))
     return fail(RT_ERR_ARG, "rt_arnoldi needs a handle with one instance (a box or one column, n_rhs = 1)");
   if (m < 1) return fail(RT_ERR_ARG, "need m >= 1");
@@ -1222,6 +1264,23 @@ int rt_arnoldi(rt_handle *h, const double *v0, int32_t m, double *H, int32_t *m_
 int rt_solve(rt_handle *h, const double *b, double *x, const rt_solve_opts *o, rt_info *info,
              void *stream) {
   if (!h || !x || !o) return fail(RT_ERR_ARG, "null handle, x or options");
+  {
+    const int fk = fault_now();
+    if (fk == kFaultLaunch) return fail(RT_ERR_CUDA, "RT_FAULT=launch: injected launch failure");
+    if (fk == kFaultNan) {
+      if (info) {
+        rt_info loc{};
+        loc.status = RT_ERR_NONFINITE;
+        loc.n_instances = h->dims == 3 ? 1 : h->n_cols * h->n_rhs;
+        loc.max_relres = NAN;
+        loc.inst_outer = info->inst_outer;
+        loc.inst_inner = info->inst_inner;
+        loc.inst_relres = info->inst_relres;
+        *info = loc;
+      }
+      return fail(RT_ERR_NONFINITE, "RT_FAULT=nan_input: injected non-finite right-hand side");
+    }
+  }
   if (o->method != RT_KRYLOV_GMRES && o->method != RT_KRYLOV_BICGSTAB)
     return fail(RT_ERR_ARG, "method must be RT_KRYLOV_GMRES or RT_KRYLOV_BICGSTAB");
   const bool bicg = o->method == RT_KRYLOV_BICGSTAB;

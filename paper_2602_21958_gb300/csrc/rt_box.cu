@@ -151,14 +151,15 @@ __global__ void __launch_bounds__(kBoxSigNT) k_sigma_box(ColDev c, Tables<T> tb,
 #pragma unroll
       for (int k = 0; k < KR; ++k) m[j][k] = 0;
     int d = 0;
-    for (; d + 4 <= nd; d += 4) {
-      T xv[4][FL];
+    constexpr int kDL = FL <= 2 ? 8 : 4;  // directions whose loads are issued together
+    for (; d + kDL <= nd; d += kDL) {
+      T xv[kDL][FL];
 #pragma unroll
-      for (int e = 0; e < 4; ++e)
+      for (int e = 0; e < kDL; ++e)
 #pragma unroll
         for (int j = 0; j < FL; ++j) xv[e][j] = on[j] ? cast_to<T>(xp[(d + e) * nn + fl[j]]) : T(0);
 #pragma unroll
-      for (int e = 0; e < 4; ++e) {
+      for (int e = 0; e < kDL; ++e) {
         const T *u = sUw + (d + e) * KR;
 #pragma unroll
         for (int k = 0; k < KR; ++k) {

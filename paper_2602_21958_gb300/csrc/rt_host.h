@@ -6,6 +6,7 @@
 #include <vector>
 
 #include "../../include/rt_gb300.h"
+#include "rt_async.cuh"
 #include "rt_internal.cuh"
 
 namespace rt {
@@ -91,6 +92,7 @@ struct rt_handle {
   uint32_t *d_tc_xb = nullptr;        // X packed to bf16 (A operand), rows stacked per column
   void *d_tc_maps = nullptr;          // TMA tensor maps over d_tc_xb, one per column
   int *d_err = nullptr;               // device error word (bounded waits)
+  long long wait_limit = rt::kSpinLimit;  // polls of a pipeline wait of the tensor-core Sigma
   // 3D boxes: geometry, per-direction (sx, sy, ds, up), opacity, grid-solve scratch
   // CUDA graph of the batched solve (queue reset + persistent kernel), reused
   // while the call signature (b, x, options) repeats

@@ -18,9 +18,11 @@
 //               epilogue warps -- so a tile's epilogue overlaps the next
 //               tile's MMAs; stages and accumulators hand over through
 //               mbarriers (full/empty, accumulator full/empty).
-// Every wait is bounded; on timeout the CTA raises an error flag, lets the
-// other roles stop, drains what it issued (bounded), frees its tensor memory
-// and returns.
+// Every wait is bounded: the pipeline waits by a per-launch poll limit
+// (rt_handle::wait_limit), the drains of a thread's own copies and MMAs by
+// kSpinLimit.  On timeout the CTA raises an error flag, lets the other roles
+// stop, drains what it issued, frees its tensor memory and returns; the host
+// reads the flag (RT_ERR_TIMEOUT).
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -122,10 +124,11 @@ __global__ void k_to_bf16(const ColDev *__restrict__ cols, const TX *__restrict_
     dst[i] = pack_bf16(to_f32(src[2 * i]), to_f32(src[2 * i + 1]));
 }
 
-// Bounded mbarrier wait that also gives up once another role raised *abort.
-__device__ __forceinline__ bool tc_wait(uint64_t *bar, uint32_t par, volatile int *abort) {
+// Bounded mbarrier wait of the pipeline: at most `limit` polls (a launch
+// parameter), and it gives up early once another role raised *abort.
+__device__ __forceinline__ bool tc_wait(uint64_t *bar, uint32_t par, volatile int *abort, long long limit) {
   const uint32_t a = smem_u32(bar);
-  for (long long it = 0; it < kSpinLimit; ++it) {
+  for (long long it = 0; it < limit; ++it) {
     uint32_t done;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
@@ -140,6 +143,10 @@ __device__ __forceinline__ bool tc_wait(uint64_t *bar, uint32_t par, volatile in
   *abort = 1;
   return false;
 }
+
+// Wait for work this thread issued itself (its copies or MMAs in flight)
+// before the CTA leaves: not cut short by an abort, bounded by kSpinLimit.
+__device__ __forceinline__ void tc_drain(uint64_t *bar, uint32_t par) { mbar_wait(bar, par); }
 
 // Persistent, warp-specialised tile loop.  A CTA walks tiles (column, 128
 // stacked rhs/point rows, 256 rays) j = blockIdx.x, blockIdx.x + gridDim.x, ...:
@@ -170,7 +177,7 @@ __global__ void __launch_bounds__(kT2Threads, 1)
     k_sigma_dense_tc(const CUtensorMap *__restrict__ maps, const TcJob2 *__restrict__ jobs, int n_jobs,
                      const ColDev *__restrict__ cols, const int64_t *__restrict__ btile_off,
                      const uint16_t *__restrict__ btiles, const float *__restrict__ gamma, int64_t E,
-                     int n_rhs, TS *__restrict__ S, int *err) {
+                     int n_rhs, TS *__restrict__ S, int *err, long long limit) {
   extern __shared__ __align__(1024) uint8_t tc_smem[];
   uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(tc_smem) + 1023) & ~uintptr_t(1023));
   __shared__ __align__(8) uint64_t full[kT2Stages], empty[kT2Stages], accf[2], acce[2];
@@ -215,7 +222,7 @@ __global__ void __launch_bounds__(kT2Threads, 1)
         const CUtensorMap *map = maps + J.col;
         for (int kc = 0; kc < nchunk; ++kc, ++g) {
           const int st = (int)(g % kT2Stages);
-          if (g >= kT2Stages && !tc_wait(&empty[st], (uint32_t)((g / kT2Stages - 1) & 1), &abort_flag)) break;
+          if (g >= kT2Stages && !tc_wait(&empty[st], (uint32_t)((g / kT2Stages - 1) & 1), &abort_flag, limit)) break;
           mbar_expect_tx(&full[st], kT2StageBytes);
           tma_load_2d(sA(st), map, kc * kTcBK, J.m0, &full[st]);  // 64 q x 128 rows, 128-byte swizzle
           bulk_g2s(sB(st), Bcol + (int64_t)kc * (kTcBN * kTcBK), kTcBBytes, &full[st]);
@@ -223,7 +230,7 @@ __global__ void __launch_bounds__(kT2Threads, 1)
       }
       // drain: every issued stage must have landed before the CTA leaves
       for (int64_t q = (g > kT2Stages ? g - kT2Stages : 0); q < g; ++q)
-        tc_wait(&full[q % kT2Stages], (uint32_t)((q / kT2Stages) & 1), &abort_flag);
+        tc_drain(&full[q % kT2Stages], (uint32_t)((q / kT2Stages) & 1));
     }
   } else if (warp == 1) {
     if (lane == 0) {  // ---- MMA issuer
@@ -236,13 +243,13 @@ __global__ void __launch_bounds__(kT2Threads, 1)
         const int nchunk = (c.nr + kTcBK - 1) / kTcBK, nk = c.nr / 16;
         const int n_valid = min(kTcBN, c.nr - J.n0);
         const int b = t & 1;
-        if (t >= 2 && !tc_wait(&acce[b], (uint32_t)((t / 2 - 1) & 1), &abort_flag)) break;
+        if (t >= 2 && !tc_wait(&acce[b], (uint32_t)((t / 2 - 1) & 1), &abort_flag, limit)) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t idesc = tc_idesc(kTcBM, (n_valid + 15) / 16 * 16);
         const uint32_t dt = tmem + (uint32_t)(b * kTcBN);
         for (int kc = 0; kc < nchunk; ++kc, ++g) {
           const int st = (int)(g % kT2Stages);
-          if (!tc_wait(&full[st], (uint32_t)((g / kT2Stages) & 1), &abort_flag)) break;
+          if (!tc_wait(&full[st], (uint32_t)((g / kT2Stages) & 1), &abort_flag, limit)) break;
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           const uint32_t a0 = smem_u32(sA(st)), b0 = smem_u32(sB(st));
 #pragma unroll
@@ -258,7 +265,7 @@ __global__ void __launch_bounds__(kT2Threads, 1)
         tc_commit(&accf[b]);
       }
       // drain: the last commit completes after every earlier MMA of this thread
-      if (any && g > 0) tc_wait(&empty[(g - 1) % kT2Stages], (uint32_t)(((g - 1) / kT2Stages) & 1), &abort_flag);
+      if (any && g > 0) tc_drain(&empty[(g - 1) % kT2Stages], (uint32_t)(((g - 1) / kT2Stages) & 1));
     }
   } else {  // ---- epilogue warps 2..5
     const int quarter = warp & 3;  // TMEM lanes 32*quarter.. (a warp's accessible quarter)
@@ -270,7 +277,7 @@ __global__ void __launch_bounds__(kT2Threads, 1)
       const int nr = c.nr, nn = c.nn, nz = c.nz;
       const int n_valid = min(kTcBN, nr - J.n0);
       const int b = t & 1;
-      if (!tc_wait(&accf[b], (uint32_t)((t / 2) & 1), &abort_flag)) break;
+      if (!tc_wait(&accf[b], (uint32_t)((t / 2) & 1), &abort_flag, limit)) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       // 32-column slices: TMEM -> the warp's shared slice (row = lane) ->
       // coalesced stores, 4 rows x 32 columns per warp instruction
@@ -316,9 +323,9 @@ __global__ void __launch_bounds__(kT2Threads, 1)
       if (lane == 0) mbar_arrive(&acce[b]);
     }
   }
-  if (tid == 0 && abort_flag) atomicOr(err, 1);
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-  __syncthreads();
+  __syncthreads();  // every role has stopped: the abort flag is final
+  if (tid == 0 && abort_flag) atomicOr(err, 1);
   if (warp == 1)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kTcBN) : "memory");
 }
@@ -460,11 +467,11 @@ int launch_sigma_dense_tc(rt_handle *h, bool x_is_float, const void *x, void *S,
   if (s_is_double)
     k_sigma_dense_tc<double><<<ctas, kT2Threads, kT2Smem, s>>>(maps, jobs, h->n_tc_jobs, h->d_cols, h->d_tc_off,
                                                                h->d_tc_tiles, h->gam32, h->E, h->n_rhs,
-                                                               static_cast<double *>(S), h->d_err);
+                                                               static_cast<double *>(S), h->d_err, h->wait_limit);
   else
     k_sigma_dense_tc<float><<<ctas, kT2Threads, kT2Smem, s>>>(maps, jobs, h->n_tc_jobs, h->d_cols, h->d_tc_off,
                                                               h->d_tc_tiles, h->gam32, h->E, h->n_rhs,
-                                                              static_cast<float *>(S), h->d_err);
+                                                              static_cast<float *>(S), h->d_err, h->wait_limit);
   return (int)cudaGetLastError();
 }
 

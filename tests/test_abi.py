@@ -99,3 +99,20 @@ def test_ritz_values_of_a_full_arnoldi_are_the_eigenvalues():
     assert H.shape == (9, 8) or H.shape == (8, 8)
     got = np.sort_complex(rt.ritz_values(H))
     assert np.abs(got - np.sort(lam)).max() < 1e-10
+
+
+def test_fault_injection_alloc_needs_no_device(monkeypatch):
+    """RT_FAULT=alloc: rt_create and rt_create_batch return RT_ERR_OOM before
+    any device call (so this runs without a GPU), with a message naming the
+    injection; unset, the variable changes nothing."""
+    import numpy as np
+
+    from paper_2602_21958_gb300 import rt
+    from paper_2602_21958_gb300 import workloads as W
+
+    p = W.two_level_column(np.logspace(-2, 2, 5), 2, 1, 3, "crd", 1e-2, 1.0)
+    monkeypatch.setenv("RT_FAULT", "alloc")
+    for probs in (p, [p, p]):
+        with pytest.raises(rt.RTError) as e:
+            rt.Handle(probs)
+        assert e.value.code == rt.RT_ERR_OOM and "RT_FAULT=alloc" in str(e.value)
