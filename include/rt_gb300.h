@@ -41,6 +41,10 @@
  *             dense kernel) poll once, give up, drain their own copies and MMAs, free
  *             their tensor memory, and the call returns RT_ERR_TIMEOUT; the handle
  *             stays usable.
+ *
+ * Memory option.  RT_BOX_COEF64=0, read by rt_create for 3D boxes, keeps the
+ * float64 sweep's step weights on the fly instead of precomputing them (16
+ * bytes per dof, taken only when they fit in a quarter of the free memory).
  */
 #ifndef RT_GB300_H
 #define RT_GB300_H

@@ -613,7 +613,6 @@ int create_box(const rt_desc *d, int n_rhs, int precision, int max_restart, rt_h
   if (!d->Psi && (!d->P || !d->R)) return fail(RT_ERR_ARG, "box: need Psi or both P and R");
   if (d->formal_solver != RT_FS_SCL && d->formal_solver != RT_FS_IE) return fail(RT_ERR_ARG, "unknown formal_solver");
   const int64_t npts = (int64_t)d->nx * d->ny * d->nz;
-  const int64_t plane = (int64_t)d->nx * d->ny;
   if (!rt::box_plane_fits(d->nx, d->ny)) return fail(RT_ERR_ARG, "box: nx*ny must be at most 4096 (a z-plane in shared memory)");
   for (int k = 0; k < d->n_dir; ++k)
     if (!(std::fabs(d->dir[3 * k + 2]) > 0.0)) return fail(RT_ERR_ARG, "box: direction with Omega_z = 0");

@@ -26,6 +26,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <vector>
 
 #include "rt_host.h"
@@ -821,9 +822,12 @@ int box_prepare(rt_handle *h, const double *chi) {
     }
   }
   // float64 step weights, when they take at most a quarter of the free memory
+  // and RT_BOX_COEF64 is not "0" (then the float64 sweep forms them on the fly)
   const int64_t ncoef = (int64_t)h->box.nd * npts * ((nn + 1) / 2) * 2;
+  const char *env = std::getenv("RT_BOX_COEF64");
+  const bool allow = !(env && env[0] == '0' && env[1] == 0);
   size_t free_b = 0, total_b = 0;
-  if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess && (double)ncoef * 16.0 <= 0.25 * (double)free_b) {
+  if (allow && cudaMemGetInfo(&free_b, &total_b) == cudaSuccess && (double)ncoef * 16.0 <= 0.25 * (double)free_b) {
     e = cudaMalloc(&h->box_w064, (size_t)ncoef * 8);
     if (e == cudaSuccess) e = cudaMalloc(&h->box_bt64, (size_t)ncoef * 8);
     if (e != cudaSuccess) return (int)e;

@@ -114,6 +114,60 @@ def test_c3_physics_reduced_grid(rt):
     assert rel(x.cpu().numpy(), xref) < 1e-10
 
 
+def nonseparable_box(seed=3, **kw):
+    """small_box with chi(p, nu) = kappa(p) phi(nu) times an independent factor
+    in [0.5, 1.5] per (point, frequency): the sweeps then read the full opacity
+    instead of one kappa per cell."""
+    p = small_box(seed=seed, **kw)
+    rng = np.random.Generator(np.random.PCG64(seed + 100))
+    return dataclasses.replace(p, chi=p.chi * rng.uniform(0.5, 1.5, p.chi.shape))
+
+
+@pytest.mark.parametrize("coef64", ["precomputed", "on_the_fly"])
+@pytest.mark.parametrize("separable", [True, False])
+@pytest.mark.parametrize("op", [0, 1, 3])
+def test_box_step_weight_modes_fp64(rt, monkeypatch, coef64, separable, op):
+    """Every float64 step-weight mode of the plane sweep (precomputed per
+    (direction, point, nu), or formed from the opacity) on separable and
+    non-separable opacities, against the oracle."""
+    if coef64 == "on_the_fly":
+        monkeypatch.setenv("RT_BOX_COEF64", "0")
+    kw = dict(nx=6, ny=7, nz=5, n_nu=7, kernel="r2")
+    p = nonseparable_box(**kw) if not separable else small_box(seed=3, **kw)
+    h = rt.Handle(p, precision=rt.RT_P_FP64, max_restart=4)
+    x = W.random_vectors(p.n, 1, 50 + op)[0]
+    y = torch.empty(p.n, dtype=torch.float64, device="cuda:0")
+    h.rt_apply(op, dev(x), y)
+    torch.cuda.synchronize()
+    ref = oracle_op(p, op, x)
+    assert rel(y.cpu().numpy(), ref) < 1e-12
+    assert np.abs(y.cpu().numpy() - ref).max() < 1e-12 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("op", [0, 1])
+def test_box_nonseparable_opacity_mixed(rt, op):
+    """The float32 sweep with the full (blocked) opacity: apply within the
+    mixed-apply bar."""
+    p = nonseparable_box(nx=9, ny=8, nz=7, order=6, n_nu=10, kernel="r2")
+    h = rt.Handle(p, precision=rt.RT_P_MIXED, max_restart=8)
+    x = W.random_vectors(p.n, 1, 60 + op, "uniform")[0]
+    y = torch.empty(p.n, dtype=torch.float64, device="cuda:0")
+    h.rt_apply(op, dev(x), y)
+    torch.cuda.synchronize()
+    assert rel(y.cpu().numpy(), oracle_op(p, op, x)) < 2e-5
+
+
+def test_box_nonseparable_opacity_mixed_solve(rt):
+    p = nonseparable_box(nx=6, ny=5, nz=6, order=4, n_nu=5, kernel="r2", eps=1e-3)
+    xref = O.solve_gmres(p, tol=1e-14, restart=300, max_iter=600).x
+    h = rt.Handle(p, precision=rt.RT_P_MIXED, max_restart=120)
+    x = torch.zeros(p.n, dtype=torch.float64, device="cuda:0")
+    info = h.rt_solve(None, x, tol=1e-13, tol_inner=1e-5, restart=120, max_outer=30)
+    torch.cuda.synchronize()
+    assert info["status"] == 0, info
+    assert rel(x.cpu().numpy(), xref) < 1e-10
+
+
 def test_quadratic_formal_solver_is_rejected_for_boxes(rt):
     # quadratic short characteristics are built for 1D columns only
     p = dataclasses.replace(small_box(), formal_solver=W.FS_QSC)
