@@ -257,6 +257,19 @@ int rt_apply_noalloc(rt_handle *h, int32_t op, int32_t fp64, const double *x, do
  * Synchronous (host eigen-decompositions, one upload). */
 int rt_set_sigma_rank(rt_handle *h, double tol, int32_t *max_rank);
 
+/* Device time of the tensor-core Sigma kernel alone, for roofline
+ * measurements (implementation property; the paper has none).  on = 1 starts a
+ * timing session on this handle: every later launch of that kernel (rt_apply
+ * with fp64 = 0 and op RT_OP_A or RT_OP_SIGMA on a handle with dense-Psi
+ * columns) is bracketed by two CUDA events on its stream, up to 4096 launches
+ * per session (later ones are not timed).  on = 0 ends the session, waits for
+ * the recorded events and writes the summed device time in milliseconds to
+ * *ms and the number of timed launches to *launches (either may be NULL); the
+ * bf16 packing of x that precedes each launch is not included.  The events
+ * are created when the session starts and destroyed when it ends.  Errors:
+ * RT_ERR_ARG for a NULL handle or on = 0 without a session, RT_ERR_CUDA. */
+int rt_tc_timer(rt_handle *h, int32_t on, double *ms, int64_t *launches);
+
 /* Solve A_N x = b for all instances (eq. RT_sys_algebraic; the Krylov solvers
  * of Sec. 5, GMRES and BiCGStab, unpreconditioned).  b == NULL uses the
  * internal right-hand side Lambda t + I_in for every rhs.

@@ -156,6 +156,7 @@ void free_handle(rt_handle *h) {
     if (p) cudaFree(p);
   if (h->solve_graph) cudaGraphExecDestroy(h->solve_graph);
   if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
+  for (cudaEvent_t e : h->tc_ev) cudaEventDestroy(e);
   delete h;
 }
 
@@ -1122,6 +1123,44 @@ int rt_set_sigma_rank(rt_handle *h, double tol, int32_t *max_rank) {
   }
   if (max_rank) *max_rank = rmax;
   return RT_OK;
+}
+
+int rt_tc_timer(rt_handle *h, int32_t on, double *ms, int64_t *launches) {
+  if (!h) return fail(RT_ERR_ARG, "null handle");
+  if (on) {
+    constexpr int kPairs = 4096;
+    for (cudaEvent_t e : h->tc_ev) cudaEventDestroy(e);
+    h->tc_ev.clear();
+    h->tc_ev_used = 0;
+    for (int i = 0; i < 2 * kPairs; ++i) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) {
+        for (cudaEvent_t f : h->tc_ev) cudaEventDestroy(f);
+        h->tc_ev.clear();
+        return fail(RT_ERR_CUDA, "rt_tc_timer: event creation failed");
+      }
+      h->tc_ev.push_back(e);
+    }
+    return RT_OK;
+  }
+  if (h->tc_ev.empty()) return fail(RT_ERR_ARG, "rt_tc_timer: no timing session");
+  double total = 0.0;
+  int rc = RT_OK;
+  for (int i = 0; i + 1 < h->tc_ev_used; i += 2) {
+    float t = 0.f;
+    if (cudaEventSynchronize(h->tc_ev[i + 1]) != cudaSuccess ||
+        cudaEventElapsedTime(&t, h->tc_ev[i], h->tc_ev[i + 1]) != cudaSuccess) {
+      rc = fail(RT_ERR_CUDA, "rt_tc_timer: event read failed");
+      break;
+    }
+    total += t;
+  }
+  if (ms) *ms = total;
+  if (launches) *launches = h->tc_ev_used / 2;
+  for (cudaEvent_t e : h->tc_ev) cudaEventDestroy(e);
+  h->tc_ev.clear();
+  h->tc_ev_used = 0;
+  return rc;
 }
 
 int rt_autotune(rt_handle *h, int32_t flags, rt_tune_info *out, void *stream) {

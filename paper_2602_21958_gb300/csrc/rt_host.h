@@ -93,6 +93,9 @@ struct rt_handle {
   void *d_tc_maps = nullptr;          // TMA tensor maps over d_tc_xb, one per column
   int *d_err = nullptr;               // device error word (bounded waits)
   long long wait_limit = rt::kSpinLimit;  // polls of a pipeline wait of the tensor-core Sigma
+  // rt_tc_timer session: event pairs around launches of the tensor-core Sigma
+  std::vector<cudaEvent_t> tc_ev;
+  int tc_ev_used = 0;
   // 3D boxes: geometry, per-direction (sx, sy, ds, up), opacity, grid-solve scratch
   // CUDA graph of the batched solve (queue reset + persistent kernel), reused
   // while the call signature (b, x, options) repeats

@@ -14,7 +14,7 @@
 //   accumulate: fp32 in tensor memory, two 128 x 256 accumulators, read back
 //               with tcgen05.ld and scaled by Gamma in the epilogue.
 //   schedule  : persistent CTAs (one per SM) walk the tile list with
-//               specialised warps -- a TMA producer, an MMA issuer and four
+//               specialised warps -- a TMA producer, an MMA issuer and eight
 //               epilogue warps -- so a tile's epilogue overlaps the next
 //               tile's MMAs; stages and accumulators hand over through
 //               mbarriers (full/empty, accumulator full/empty).
@@ -107,6 +107,19 @@ __device__ __forceinline__ float to_f32(double v) { return narrow_f32(v); }
 __device__ __forceinline__ float to_f32(float v) { return v; }
 
 // ----------------------------------------------------------------- kernel
+// eight consecutive values of X as float32 (16-byte vector loads)
+__device__ __forceinline__ void load8(const double *p, float (&f)[8]) {
+  const double2 *q = reinterpret_cast<const double2 *>(p);
+  const double2 a = q[0], b = q[1], c = q[2], d = q[3];
+  f[0] = to_f32(a.x), f[1] = to_f32(a.y), f[2] = to_f32(b.x), f[3] = to_f32(b.y);
+  f[4] = to_f32(c.x), f[5] = to_f32(c.y), f[6] = to_f32(d.x), f[7] = to_f32(d.y);
+}
+__device__ __forceinline__ void load8(const float *p, float (&f)[8]) {
+  const float4 *q = reinterpret_cast<const float4 *>(p);
+  const float4 a = q[0], b = q[1];
+  f[0] = a.x, f[1] = a.y, f[2] = a.z, f[3] = a.w, f[4] = b.x, f[5] = b.y, f[6] = b.z, f[7] = b.w;
+}
+
 // X -> bf16, the A operand of the GEMM.  Column c's rows of all right-hand
 // sides are stacked: row m = rhs * nz + p at n_rhs * x_off + m * nr, so one 2D
 // TMA map per column covers every (rhs, point) row and a 128-row tile can
@@ -117,11 +130,17 @@ __global__ void k_to_bf16(const ColDev *__restrict__ cols, const TX *__restrict_
   const ColDev c = cols[blockIdx.y];
   if (c.psi_off < 0 || c.nr % 16) return;
   const int rhs = blockIdx.z;
-  const int64_t n2 = (int64_t)c.nz * c.nr / 2;
+  // nz * nr is a multiple of 16 and x_off, E multiples of 8 (tc_prepare), so
+  // every group of eight values starts on a 64-byte (source) and 16-byte
+  // (destination) boundary
+  const int64_t n8 = (int64_t)c.nz * c.nr / 8;
   const TX *src = X + rhs * E + c.x_off;
-  uint32_t *dst = Xb + ((int64_t)n_rhs * c.x_off + (int64_t)rhs * c.nz * c.nr) / 2;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n2; i += (int64_t)gridDim.x * blockDim.x)
-    dst[i] = pack_bf16(to_f32(src[2 * i]), to_f32(src[2 * i + 1]));
+  uint4 *dst = reinterpret_cast<uint4 *>(Xb + ((int64_t)n_rhs * c.x_off + (int64_t)rhs * c.nz * c.nr) / 2);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n8; i += (int64_t)gridDim.x * blockDim.x) {
+    float f[8];
+    load8(src + 8 * i, f);
+    dst[i] = make_uint4(pack_bf16(f[0], f[1]), pack_bf16(f[2], f[3]), pack_bf16(f[4], f[5]), pack_bf16(f[6], f[7]));
+  }
 }
 
 // Bounded mbarrier wait of the pipeline: at most `limit` polls (a launch
@@ -158,14 +177,16 @@ __device__ __forceinline__ void tc_drain(uint64_t *bar, uint32_t par) { mbar_wai
 //   warp 1 (one thread): tcgen05.mma (M=128, N<=256, K=16) into one of two
 //     TMEM accumulators (2 x 256 columns), releases each stage by
 //     tcgen05.commit, and the accumulator when the tile is complete;
-//   warps 2-5: epilogue of the previous tile while the next one is
-//     multiplied: TMEM (their 32-lane quarter) -> shared tile -> Gamma-scaled
-//     coalesced 16-byte stores, then the accumulator is handed back.
+//   warps 2-9: epilogue of the previous tile while the next one is
+//     multiplied: TMEM (a warp's 32-lane quarter, half of the columns) ->
+//     shared slice -> Gamma-scaled coalesced 16-byte stores, then the
+//     accumulator is handed back (all eight warps arrive).
 constexpr int kT2Stages = 4;
-constexpr int kT2Threads = 192;
-constexpr int kT2Ld = 36;  // floats per row of a warp's epilogue slice (32 columns + 4)
+constexpr int kT2EpiWarps = 8;
+constexpr int kT2Threads = 64 + 32 * kT2EpiWarps;
+constexpr int kT2Ld = 16;  // floats per row of a warp's epilogue slice (16 columns, chunks rotated)
 constexpr int kT2StageBytes = kTcABytes + kTcBBytes;
-constexpr int kT2EpiBytes = 4 * 32 * kT2Ld * 4;
+constexpr int kT2EpiBytes = kT2EpiWarps * 32 * kT2Ld * 4;
 constexpr int kT2Smem = kT2Stages * kT2StageBytes + kT2EpiBytes + 1024;
 
 struct TcJob2 {
@@ -195,7 +216,7 @@ __global__ void __launch_bounds__(kT2Threads, 1)
     }
     for (int i = 0; i < 2; ++i) {
       mbar_init(&accf[i], 1);
-      mbar_init(&acce[i], 4);
+      mbar_init(&acce[i], kT2EpiWarps);
     }
     abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -267,9 +288,17 @@ __global__ void __launch_bounds__(kT2Threads, 1)
       // drain: the last commit completes after every earlier MMA of this thread
       if (any && g > 0) tc_drain(&empty[(g - 1) % kT2Stages], (uint32_t)(((g - 1) / kT2Stages) & 1));
     }
-  } else {  // ---- epilogue warps 2..5
-    const int quarter = warp & 3;  // TMEM lanes 32*quarter.. (a warp's accessible quarter)
+  } else {  // ---- epilogue warps 2..9
+    // Warp w reads the TMEM lanes of its accessible quarter (32 * (w % 4)..)
+    // and the tile columns [128 * half, 128 * half + 128), half = (w - 2) / 4.
+    // Per 16-column slice: TMEM -> the warp's shared slice (row = lane, the
+    // four 16-byte chunks of a row rotated by (row / 2) % 4, so the
+    // row-per-lane writes are free of bank conflicts) -> Gamma-scaled stores
+    // in which 8 lanes write one row's 16 values: whole 128-byte lines (64
+    // bytes for float32) per row, 4 rows per instruction.
+    const int quarter = warp & 3, half = (warp - 2) >> 2;
     float *tile = epi + (warp - 2) * 32 * kT2Ld;
+    const int sub = lane >> 3, c2 = 2 * (lane & 7);  // store layout: row it * 4 + sub, columns c2, c2 + 1
     int t = 0;
     for (int j = blockIdx.x; j < n_jobs && !abort_flag; j += gridDim.x, ++t) {
       const TcJob2 J = jobs[j];
@@ -277,45 +306,57 @@ __global__ void __launch_bounds__(kT2Threads, 1)
       const int nr = c.nr, nn = c.nn, nz = c.nz;
       const int n_valid = min(kTcBN, nr - J.n0);
       const int b = t & 1;
+      // the eight rows this lane stores in every slice of the tile, resolved
+      // to (right-hand side, point) once per tile: offsets of the Gamma row
+      // and of the output row (below 2^31: the batch vector's length)
+      int goff[8], soff[8];
+#pragma unroll
+      for (int it = 0; it < 8; ++it) {
+        const int m = J.m0 + quarter * 32 + it * 4 + sub;
+        const bool ok = m < n_rhs * nz;
+        const int rhs = ok ? m / nz : 0, p = ok ? m - rhs * nz : 0;
+        goff[it] = ok ? (int)(c.g_off + (int64_t)p * nn) : -1;
+        soff[it] = (int)(rhs * E + c.x_off + (int64_t)p * nr + J.n0);
+      }
       if (!tc_wait(&accf[b], (uint32_t)((t / 2) & 1), &abort_flag, limit)) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      // 32-column slices: TMEM -> the warp's shared slice (row = lane) ->
-      // coalesced stores, 4 rows x 32 columns per warp instruction
-      for (int cs = 0; cs < n_valid; cs += 32) {
-        const int w = min(32, n_valid - cs);  // 16 or 32
-        const uint32_t taddr = tmem + (uint32_t)(b * kTcBN) + ((uint32_t)(quarter * 32) << 16) + (uint32_t)cs;
-        for (int h16 = 0; h16 < w; h16 += 16) {
+      const int c_hi = min(n_valid, half * 128 + 128);
+      for (int cs = half * 128; cs < c_hi; cs += 16) {
+        {
           float v[16];
-          tc_ld16(taddr + (uint32_t)h16, v);
-          float4 *dst = reinterpret_cast<float4 *>(tile + lane * kT2Ld + h16);
+          tc_ld16(tmem + (uint32_t)(b * kTcBN) + ((uint32_t)(quarter * 32) << 16) + (uint32_t)cs, v);
+          float4 *dst = reinterpret_cast<float4 *>(tile + lane * kT2Ld);
+          const int rot = (lane >> 1) & 3;
 #pragma unroll
-          for (int q = 0; q < 4; ++q) dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+          for (int q = 0; q < 4; ++q)
+            dst[q ^ rot] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
         }
         __syncwarp();
-#pragma unroll 2
-        for (int it = 0; it < 8; ++it) {
-          const int rr = it * 4 + (lane >> 3), ci = 4 * (lane & 7);
-          const int m = J.m0 + quarter * 32 + rr;
-          if (m < n_rhs * nz && ci < w) {
-            const int rhs = m / nz, p = m - rhs * nz;
-            const float4 v = *reinterpret_cast<const float4 *>(tile + rr * kT2Ld + ci);
-            const float *gp = gamma + c.g_off + (int64_t)p * nn;
-            const int r0 = J.n0 + cs + ci;
-            // frequency of ray r0 (ray = direction * nn + frequency), then the
-            // next three with wrap-around instead of a division each
-            int f0 = r0 - (r0 / nn) * nn;
-            const int f1 = f0 + 1 == nn ? 0 : f0 + 1, f2 = f1 + 1 == nn ? 0 : f1 + 1, f3 = f2 + 1 == nn ? 0 : f2 + 1;
-            const float a0 = gp[f0] * v.x, a1 = gp[f1] * v.y;
-            const float a2 = gp[f2] * v.z, a3 = gp[f3] * v.w;
-            TS *dst = S + rhs * E + c.x_off + (int64_t)p * nr + r0;
-            if (sizeof(TS) == 4) {
-              *reinterpret_cast<float4 *>(dst) = make_float4(a0, a1, a2, a3);
-            } else {
-              reinterpret_cast<double2 *>(dst)[0] = make_double2(widen_f64(a0), widen_f64(a1));
-              reinterpret_cast<double2 *>(dst)[1] = make_double2(widen_f64(a2), widen_f64(a3));
-            }
+        // frequencies of this lane's two rays (ray = direction * nn +
+        // frequency): one division per slice
+        const int r0 = J.n0 + cs + c2;
+        const int f0 = r0 - (r0 / nn) * nn;
+        const int f1 = f0 + 1 == nn ? 0 : f0 + 1;
+        float g0[8], g1[8];
+#pragma unroll
+        for (int it = 0; it < 8; ++it)
+          if (goff[it] >= 0) {
+            g0[it] = gamma[goff[it] + f0];
+            g1[it] = gamma[goff[it] + f1];
           }
-        }
+#pragma unroll
+        for (int it = 0; it < 8; ++it)
+          if (goff[it] >= 0) {
+            const int row = it * 4 + sub;
+            const float2 v = *reinterpret_cast<const float2 *>(
+                tile + row * kT2Ld + 4 * ((c2 >> 2) ^ ((row >> 1) & 3)) + (c2 & 3));
+            const float a0 = g0[it] * v.x, a1 = g1[it] * v.y;
+            TS *dst = S + (int64_t)soff[it] + cs + c2;
+            if (sizeof(TS) == 4)
+              *reinterpret_cast<float2 *>(dst) = make_float2(a0, a1);
+            else
+              *reinterpret_cast<double2 *>(dst) = make_double2(widen_f64(a0), widen_f64(a1));
+          }
         __syncwarp();
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -420,8 +461,9 @@ int tc_prepare(rt_handle *h, const std::vector<double> &psiwT) {
   std::vector<TcJob2> jobs;
   tc_build_tiles(h->h_cols, psiwT, tiles, offs);
   tc_build_jobs(h->h_cols, h->n_rhs, jobs);
-  // 16-byte vector accesses of the epilogue need x_off and E multiples of 8
-  bool aligned = h->E % 8 == 0;
+  // 16-byte vector accesses of the epilogue need x_off and E multiples of 8;
+  // its 32-bit row offsets need the batch vector below 2^31 values
+  bool aligned = h->E % 8 == 0 && (int64_t)h->E * h->n_rhs < (int64_t(1) << 31);
   for (const ColDev &c : h->h_cols) aligned = aligned && c.x_off % 8 == 0;
   h->n_tc_jobs = aligned ? (int)jobs.size() : 0;
   if (h->n_tc_jobs == 0) return 0;
@@ -455,7 +497,7 @@ int launch_sigma_dense_tc(rt_handle *h, bool x_is_float, const void *x, void *S,
   cudaError_t ae = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kT2Smem);
   if (ae != cudaSuccess) return (int)ae;
   int64_t most = 1;
-  for (const ColDev &c : h->h_cols) most = std::max<int64_t>(most, (int64_t)c.nz * c.nr / 2);
+  for (const ColDev &c : h->h_cols) most = std::max<int64_t>(most, (int64_t)c.nz * c.nr / 8);
   const dim3 pg((unsigned)std::min<int64_t>((most + 255) / 256, 64), (unsigned)h->n_cols, (unsigned)h->n_rhs);
   if (x_is_float)
     k_to_bf16<float><<<pg, 256, 0, s>>>(h->d_cols, static_cast<const float *>(x), h->d_tc_xb, h->E, h->n_rhs);
@@ -464,6 +506,9 @@ int launch_sigma_dense_tc(rt_handle *h, bool x_is_float, const void *x, void *S,
   const TcJob2 *jobs = static_cast<const TcJob2 *>(h->d_tc_jobs);
   const CUtensorMap *maps = static_cast<const CUtensorMap *>(h->d_tc_maps);
   const int ctas = std::min(h->n_tc_jobs, h->n_sm > 0 ? h->n_sm : 152);
+  // rt_tc_timer session: bracket this launch with the next event pair
+  const bool timed = h->tc_ev_used + 2 <= (int)h->tc_ev.size();
+  if (timed) cudaEventRecord(h->tc_ev[h->tc_ev_used], s);
   if (s_is_double)
     k_sigma_dense_tc<double><<<ctas, kT2Threads, kT2Smem, s>>>(maps, jobs, h->n_tc_jobs, h->d_cols, h->d_tc_off,
                                                                h->d_tc_tiles, h->gam32, h->E, h->n_rhs,
@@ -472,6 +517,10 @@ int launch_sigma_dense_tc(rt_handle *h, bool x_is_float, const void *x, void *S,
     k_sigma_dense_tc<float><<<ctas, kT2Threads, kT2Smem, s>>>(maps, jobs, h->n_tc_jobs, h->d_cols, h->d_tc_off,
                                                               h->d_tc_tiles, h->gam32, h->E, h->n_rhs,
                                                               static_cast<float *>(S), h->d_err, h->wait_limit);
+  if (timed) {
+    cudaEventRecord(h->tc_ev[h->tc_ev_used + 1], s);
+    h->tc_ev_used += 2;
+  }
   return (int)cudaGetLastError();
 }
 

@@ -49,8 +49,8 @@ class rt_info(C.Structure):
 
 
 EXPORTS = ("rt_create", "rt_create_batch", "rt_vector_length", "rt_apply", "rt_apply_noalloc",
-           "rt_autotune", "rt_set_sigma_rank", "rt_solve", "rt_arnoldi", "rt_destroy", "rt_last_error",
-           "rt_version")
+           "rt_autotune", "rt_set_sigma_rank", "rt_tc_timer", "rt_solve", "rt_arnoldi", "rt_destroy",
+           "rt_last_error", "rt_version")
 
 
 class rt_tune_info(C.Structure):
@@ -83,6 +83,8 @@ def load(path: Optional[str] = None) -> C.CDLL:
     lib.rt_autotune.restype = C.c_int
     lib.rt_set_sigma_rank.argtypes = [vp, C.c_double, C.POINTER(C.c_int32)]
     lib.rt_set_sigma_rank.restype = C.c_int
+    lib.rt_tc_timer.argtypes = [vp, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
+    lib.rt_tc_timer.restype = C.c_int
     lib.rt_solve.argtypes = [vp, vp, vp, C.POINTER(rt_solve_opts), C.POINTER(rt_info), vp]
     lib.rt_arnoldi.argtypes = [vp, vp, C.c_int32, vp, C.POINTER(C.c_int32), vp]
     lib.rt_destroy.argtypes = [vp]
@@ -223,6 +225,13 @@ class Handle:
         r = C.c_int32(0)
         _check(load().rt_set_sigma_rank(self._h, float(tol), C.byref(r)))
         return r.value
+
+    def rt_tc_timer(self, on: bool):
+        """Start (on) or end a timing session of the tensor-core Sigma kernel;
+        ending returns (summed device ms, launches timed)."""
+        ms, n = C.c_double(0.0), C.c_int64(0)
+        _check(load().rt_tc_timer(self._h, int(bool(on)), C.byref(ms), C.byref(n)))
+        return None if on else (ms.value, n.value)
 
     def rt_solve(self, b, x, tol: float = 1e-11, tol_inner: float = 0.1, restart: Optional[int] = None,
                  max_outer: int = 50, use_x0: bool = False, stream=None, per_instance: bool = False,

@@ -97,3 +97,32 @@ def test_dense_mixed_solve_refines_to_fp64_accuracy(rt):
     xref = O.solve_dense(p)
     assert info["status"] == 0
     assert np.linalg.norm(x.cpu().numpy() - xref) / np.linalg.norm(xref) < 1e-10
+
+
+def test_tc_timer_counts_and_times_only_the_gemm(rt):
+    """rt_tc_timer brackets each tensor-core launch with CUDA events: three
+    Sigma applies give three timed launches whose summed time is positive and
+    below the applies' own (which also pack x to bf16); the output is the same
+    as without a session, and ending a session that was never started is an
+    argument error."""
+    p = CASES["nr1280"]().with_dense_kernel()
+    h = rt.Handle(p, n_rhs=2, precision=rt.RT_P_MIXED, max_restart=4)
+    x = torch.tensor(W.random_vectors(2 * p.n, 1, 23)[0], device="cuda:0")
+    y0 = torch.empty_like(x)
+    y1 = torch.empty_like(x)
+    h.rt_apply(rt.RT_OP_SIGMA, x, y0)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    h.rt_tc_timer(True)
+    e0.record()
+    for _ in range(3):
+        h.rt_apply(rt.RT_OP_SIGMA, x, y1)
+    e1.record()
+    torch.cuda.synchronize()
+    ms, n = h.rt_tc_timer(False)
+    assert n == 3
+    assert 0.0 < ms < e0.elapsed_time(e1)
+    assert torch.equal(y0, y1)
+    with pytest.raises(rt.RTError) as e:
+        h.rt_tc_timer(False)
+    assert e.value.code == rt.RT_ERR_ARG
