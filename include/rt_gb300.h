@@ -45,6 +45,9 @@
  * Memory option.  RT_BOX_COEF64=0, read by rt_create for 3D boxes, keeps the
  * float64 sweep's step weights on the fly instead of precomputing them (16
  * bytes per dof, taken only when they fit in a quarter of the free memory).
+ * Shape option.  RT_BOX_FB=1, 2 or 4, read by rt_create for 3D boxes, fixes
+ * the frequencies per plane-sweep CTA (capped at 2 for the float64 sweep and
+ * by shared memory) until rt_autotune picks one by timing.
  */
 #ifndef RT_GB300_H
 #define RT_GB300_H

@@ -237,6 +237,176 @@ __global__ void __launch_bounds__(kBoxSigNT) k_sigma_box(ColDev c, Tables<T> tb,
   }
 }
 
+// Four consecutive values of a float32 / float64 array (16-byte aligned).
+template <typename T> struct Vec4;
+template <> struct Vec4<float> {
+  static __device__ __forceinline__ void ld(const float *p, float (&v)[4]) {
+    const float4 a = *reinterpret_cast<const float4 *>(p);
+    v[0] = a.x, v[1] = a.y, v[2] = a.z, v[3] = a.w;
+  }
+  static __device__ __forceinline__ void st(float *p, const float (&v)[4]) {
+    *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  }
+};
+template <> struct Vec4<double> {
+  static __device__ __forceinline__ void ld(const double *p, double (&v)[4]) {
+    const double2 a = reinterpret_cast<const double2 *>(p)[0], b = reinterpret_cast<const double2 *>(p)[1];
+    v[0] = a.x, v[1] = a.y, v[2] = b.x, v[3] = b.y;
+  }
+  static __device__ __forceinline__ void st(double *p, const double (&v)[4]) {
+    reinterpret_cast<double2 *>(p)[0] = make_double2(v[0], v[1]);
+    reinterpret_cast<double2 *>(p)[1] = make_double2(v[2], v[3]);
+  }
+};
+
+// Separable kernel, sweep-layout output with FBO in {1, 2, 4} frequencies per
+// block and nn a multiple of 4: LP lanes per point, each owning 4 consecutive
+// frequencies (16- or 32-byte loads of X, one vector load of the frequency
+// kernel row per q), 32 / LP consecutive points per warp, so the points'
+// FBO-value runs of one (direction, block) are adjacent in the output and a
+// warp's store fills whole sectors.  Output offsets are formed once per point
+// (no division per store).  Same stages and shared memory as k_sigma_box.
+template <typename T, typename TX, int KR, int LP, int FBO>
+__global__ void __launch_bounds__(kBoxSigNT) k_sigma_box4(ColDev c, Tables<T> tb, int64_t npts,
+                                                          const TX *__restrict__ X, T *__restrict__ S) {
+  extern __shared__ __align__(16) unsigned char sig_smem[];
+  constexpr int PPW = 32 / LP;
+  const int nd = c.nd, nn = c.nn, nr = c.nr, rp = c.rp;
+  const int nfb = nn / FBO;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int ps = lane / LP, f0 = 4 * (lane % LP);
+  const bool on = f0 < nn;
+  T *sUw = reinterpret_cast<T *>(sig_smem);
+  T *sUl = sUw + nd * KR;
+  T *sRw = sUl + nd * KR;
+  const bool rw_cached = !c.rdiag && (int64_t)nn * nn * sizeof(T) <= kBoxRwCache;
+  const int rw_len = c.rdiag ? nn : (rw_cached ? nn * nn : 0);
+  const int wstride = KR * nn + 4;  // per point of a warp: moments, offset so points hit other banks
+  T *wm = sRw + ((rw_len + 3) & ~3) + (int64_t)warp * PPW * wstride + ps * wstride;
+  for (int i = threadIdx.x; i < nd * KR; i += blockDim.x) {
+    const int d = i / KR, k = i - d * KR;
+    sUw[i] = k < rp ? tb.Uw[c.u_off + d * rp + k] : T(0);
+    sUl[i] = k < rp ? tb.Ul[c.u_off + d * rp + k] : T(0);
+  }
+  for (int i = threadIdx.x; i < rw_len; i += blockDim.x) sRw[i] = tb.RwT[c.r_off + i];
+  __syncthreads();
+  const T *Rw = (c.rdiag || rw_cached) ? sRw : tb.RwT + c.r_off;
+  const T *gam = tb.gamma + c.g_off;
+  const int64_t dstride = (int64_t)nfb * npts * FBO;  // output stride of one direction
+  for (int64_t p0 = ((int64_t)blockIdx.x * nw + warp) * PPW; p0 < npts; p0 += (int64_t)gridDim.x * nw * PPW) {
+    const int64_t p = p0 + ps;
+    const bool act = on && p < npts;
+    const TX *xp = X + p * nr + f0;
+    // 1. moments m_k(f) = sum_d Uw[d][k] X(d, f)
+    T m[4][KR];
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int k = 0; k < KR; ++k) m[j][k] = 0;
+    constexpr int kDL = 4;  // directions whose loads are issued together
+    int d = 0;
+    for (; d + kDL <= nd; d += kDL) {
+      TX xv[kDL][4];
+#pragma unroll
+      for (int e = 0; e < kDL; ++e) {
+        if (act) {
+          Vec4<TX>::ld(xp + (int64_t)(d + e) * nn, xv[e]);
+        } else {
+#pragma unroll
+          for (int j = 0; j < 4; ++j) xv[e][j] = TX(0);
+        }
+      }
+#pragma unroll
+      for (int e = 0; e < kDL; ++e) {
+        const T *u = sUw + (d + e) * KR;
+        T xt[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) xt[j] = cast_to<T>(xv[e][j]);
+#pragma unroll
+        for (int k = 0; k < KR; ++k) {
+          const T uk = u[k];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) m[j][k] = fma(uk, xt[j], m[j][k]);
+        }
+      }
+    }
+    for (; d < nd; ++d) {
+      TX xv[4] = {TX(0), TX(0), TX(0), TX(0)};
+      if (act) Vec4<TX>::ld(xp + (int64_t)d * nn, xv);
+      const T *u = sUw + d * KR;
+#pragma unroll
+      for (int k = 0; k < KR; ++k)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) m[j][k] = fma(u[k], cast_to<T>(xv[j]), m[j][k]);
+    }
+    // 2. frequency kernel z_k(f) = sum_q RwT[q][f] m_k(q)
+    T z[4][KR];
+    if (c.rdiag) {
+      T r[4] = {T(0), T(0), T(0), T(0)};
+      if (on) Vec4<T>::ld(Rw + f0, r);
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int k = 0; k < KR; ++k) z[j][k] = r[j] * m[j][k];
+    } else {
+      if (on) {
+#pragma unroll
+        for (int k = 0; k < KR; ++k) {
+          const T v[4] = {m[0][k], m[1][k], m[2][k], m[3][k]};
+          Vec4<T>::st(wm + k * nn + f0, v);
+        }
+      }
+      __syncwarp();
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int k = 0; k < KR; ++k) z[j][k] = 0;
+      if (on) {
+        for (int q = 0; q < nn; ++q) {
+          T r[4];
+          Vec4<T>::ld(Rw + (int64_t)q * nn + f0, r);
+#pragma unroll
+          for (int k = 0; k < KR; ++k) {
+            const T mq = wm[k * nn + q];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) z[j][k] = fma(r[j], mq, z[j][k]);
+          }
+        }
+      }
+      __syncwarp();
+    }
+    if (!act) continue;
+    // 3. expansion S(d, f) = gamma(f) sum_k Ul[d][k] z_k(f), into the blocks
+    //    of FBO frequencies: f0 / FBO .. (f0 + 3) / FBO
+    T g[4];
+    Vec4<T>::ld(gam + p * nn + f0, g);
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int k = 0; k < KR; ++k) z[j][k] *= g[j];
+    T *out = S + ((int64_t)(f0 / FBO) * npts + p) * FBO;  // direction 0, first block of this lane
+    const int64_t bstride = npts * FBO;                  // next frequency block
+    for (int dd = 0; dd < nd; ++dd, out += dstride) {
+      const T *u = sUl + dd * KR;
+      T acc[4] = {T(0), T(0), T(0), T(0)};
+#pragma unroll
+      for (int k = 0; k < KR; ++k) {
+        const T uk = u[k];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[j] = fma(uk, z[j][k], acc[j]);
+      }
+      if (FBO == 4) {
+        Vec4<T>::st(out, acc);
+      } else if (FBO == 2) {
+        out[0] = acc[0], out[1] = acc[1];
+        out[bstride] = acc[2], out[bstride + 1] = acc[3];
+      } else {
+        out[0] = acc[0], out[bstride] = acc[1], out[2 * bstride] = acc[2], out[3 * bstride] = acc[3];
+      }
+    }
+  }
+}
+
 // Dense kernel Psi (n_r x n_r): S(p, r) = gamma sum_q PsiwT[q][r] X(p, q),
 // lanes over r, one warp per point (small problems only).
 template <typename T, typename TX>
@@ -695,6 +865,40 @@ static int sigma_box(rt_handle *h, const Tables<T> &tb, const TX *x, T *S, int f
     kern<<<grid, kBoxSigNT, smem, s>>>(c, tb, npts, x, S, fb_out);
     return (int)cudaGetLastError();
   };
+  // four frequencies per lane into sweep blocks of 1, 2 or 4 (nn a multiple
+  // of 4, at most 128; Gamma rows 16-byte aligned)
+  if (fb_out > 0 && 4 % fb_out == 0 && c.nn % 4 == 0 && c.nn <= 128 && c.g_off % 4 == 0) {
+    const int lp = c.nn <= 32 ? 8 : (c.nn <= 64 ? 16 : 32);
+    const int pts_per_cta = nw * (32 / lp);
+    const int grid4 = (int)std::min<int64_t>((npts + pts_per_cta - 1) / pts_per_cta, (int64_t)h->n_sm * 16);
+    auto launch4 = [&](auto kern, int kr) -> int {
+      const size_t smem = sizeof(T) * ((size_t)2 * c.nd * kr + ((rw_len + 3) & ~3) +
+                                       (size_t)nw * (32 / lp) * (kr * c.nn + 4));
+      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return (int)e;
+      kern<<<grid4, kBoxSigNT, smem, s>>>(c, tb, npts, x, S);
+      return (int)cudaGetLastError();
+    };
+#define RT_SIGMA_BOX4(KR)                                                                        \
+  {                                                                                              \
+    if (lp == 8) {                                                                               \
+      if (fb_out == 4) return launch4(k_sigma_box4<T, TX, KR, 8, 4>, KR);                        \
+      if (fb_out == 2) return launch4(k_sigma_box4<T, TX, KR, 8, 2>, KR);                        \
+      return launch4(k_sigma_box4<T, TX, KR, 8, 1>, KR);                                         \
+    }                                                                                            \
+    if (lp == 16) {                                                                              \
+      if (fb_out == 4) return launch4(k_sigma_box4<T, TX, KR, 16, 4>, KR);                       \
+      if (fb_out == 2) return launch4(k_sigma_box4<T, TX, KR, 16, 2>, KR);                       \
+      return launch4(k_sigma_box4<T, TX, KR, 16, 1>, KR);                                        \
+    }                                                                                            \
+    if (fb_out == 4) return launch4(k_sigma_box4<T, TX, KR, 32, 4>, KR);                         \
+    if (fb_out == 2) return launch4(k_sigma_box4<T, TX, KR, 32, 2>, KR);                         \
+    return launch4(k_sigma_box4<T, TX, KR, 32, 1>, KR);                                          \
+  }
+    if (c.rp <= 2) RT_SIGMA_BOX4(2)
+    RT_SIGMA_BOX4(6)
+#undef RT_SIGMA_BOX4
+  }
   const int fl = (c.nn + 31) / 32;
   if (c.rp <= 2) {
     if (fl <= 1) return launch(k_sigma_box<T, TX, 2, 1>, 2);
@@ -770,6 +974,10 @@ int box_apply(rt_handle *h, int op, bool fp64, const void *x, bool xf, void *y, 
 
 // Opacity in the sweep's padded per-point layout, both precisions.
 int box_prepare(rt_handle *h, const double *chi) {
+  // RT_BOX_FB = 1, 2 or 4 fixes the plane sweep's frequencies per CTA (the
+  // choice rt_autotune makes by timing; it may override it later)
+  const char *efb = std::getenv("RT_BOX_FB");
+  if (efb && (efb[0] == '1' || efb[0] == '2' || efb[0] == '4') && efb[1] == 0) h->tune.box_fb = efb[0] - '0';
   const int nn = h->box.nn;
   const int npad = (nn + 3) / 4 * 4;
   const int64_t npts = (int64_t)h->box.nx * h->box.ny * h->box.nz;

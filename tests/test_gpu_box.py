@@ -168,6 +168,26 @@ def test_box_nonseparable_opacity_mixed_solve(rt):
     assert rel(x.cpu().numpy(), xref) < 1e-10
 
 
+@pytest.mark.parametrize("fb", ["1", "2", "4"])
+@pytest.mark.parametrize("n_nu,kernel", [(8, "r2"), (12, "crd")])
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_box_sigma_four_frequencies_per_lane(rt, monkeypatch, fb, n_nu, kernel, prec):
+    """Frequency counts that are multiples of 4 take the Sigma kernel with four
+    consecutive frequencies per lane and several points per warp; every sweep
+    block width (RT_BOX_FB) and both precisions, all four operators."""
+    monkeypatch.setenv("RT_BOX_FB", fb)
+    p = small_box(nx=7, ny=6, nz=5, order=4, n_nu=n_nu, kernel=kernel, seed=9)
+    h = rt.Handle(p, precision=rt.RT_P_FP64 if prec == "fp64" else rt.RT_P_MIXED, max_restart=4)
+    for op in (0, 1, 2, 3):
+        x = W.random_vectors(p.n, 1, 70 + op, "uniform")[0]
+        y = torch.empty(p.n, dtype=torch.float64, device="cuda:0")
+        h.rt_apply(op, dev(x), y)
+        torch.cuda.synchronize()
+        ref = oracle_op(p, op, x)
+        bar = 1e-12 if prec == "fp64" else 2e-5
+        assert rel(y.cpu().numpy(), ref) < bar, (op, fb)
+
+
 def test_quadratic_formal_solver_is_rejected_for_boxes(rt):
     # quadratic short characteristics are built for 1D columns only
     p = dataclasses.replace(small_box(), formal_solver=W.FS_QSC)
