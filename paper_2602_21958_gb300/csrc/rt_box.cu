@@ -57,16 +57,22 @@ __device__ __forceinline__ void step_coef<float>(float d, int ie, float &e, floa
     return;
   }
   e = __expf(-d);
-  // series below 0.5: 1 - e^-d = d (1 - d/2 (1 - d/3 (...))) and
-  // w1/d = (d/2)(1 - (d/3)(1 - (d/4)(...))), 10 factors each
-  float s0 = 1.f, s1 = 1.f;
+  float w0, beta;
+  if (d < 0.5f) {
+    // series, no cancellation: 1 - e^-d = d (1 - d/2 (1 - d/3 (...))) and
+    // w1/d = (d/2)(1 - (d/3)(1 - (d/4)(...))), 8 factors each (the first
+    // dropped terms, d^8/9! and 2 d^8/10!, stay below 1.1e-8 for d < 0.5)
+    float s0 = 1.f, s1 = 1.f;
 #pragma unroll
-  for (int j = 11; j >= 2; --j) s0 = 1.f - d * (1.f / (float)j) * s0;
+    for (int j = 9; j >= 2; --j) s0 = 1.f - d * (1.f / (float)j) * s0;
 #pragma unroll
-  for (int j = 12; j >= 3; --j) s1 = 1.f - d * (1.f / (float)j) * s1;
-  const bool small = d < 0.5f;
-  const float w0 = small ? d * s0 : 1.f - e;
-  const float beta = small ? 0.5f * d * s1 : 1.f - __fdividef(w0, d);
+    for (int j = 10; j >= 3; --j) s1 = 1.f - d * (1.f / (float)j) * s1;
+    w0 = d * s0;
+    beta = 0.5f * d * s1;
+  } else {
+    w0 = 1.f - e;
+    beta = 1.f - __fdividef(w0, d);
+  }
   b = beta;
   a = w0 - beta;
 }

@@ -129,14 +129,18 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double *red, double *
 // operations instead; values outside the float32 normal range (and zeros,
 // subnormals, inf, nan) take the conversion instruction.
 // narrow_f32: round to nearest even, as the cvt.rn.f32.f64 it replaces.
+// In the normal float32 range the top 32 bits of (bits << 3) hold the low 9
+// exponent bits and the 23 leading mantissa bits; subtracting 896 << 23
+// rebiases the exponent (modulo 2^9 it is exact for biased exponents
+// 897..1150); the 29 dropped bits round the result, a carry moving into the
+// exponent as it should.  Zero and subnormal doubles give a signed zero.
 __device__ __forceinline__ float narrow_f32(double v) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(v);
   const uint32_t hi = (uint32_t)(b >> 32), lo = (uint32_t)b;
   const uint32_t e = (hi >> 20) & 0x7ffu;
-  if (e - 897u > 253u) return (float)v;  // biased exponent outside [897, 1150]
-  uint32_t r = ((e - 896u) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
-  const uint32_t rem = lo & 0x1fffffffu;
-  r += (rem > 0x10000000u || (rem == 0x10000000u && (r & 1u))) ? 1u : 0u;
+  if (e - 897u > 253u) return e == 0u ? __uint_as_float(hi & 0x80000000u) : (float)v;
+  uint32_t r = __funnelshift_l(lo, hi, 3) - (896u << 23);
+  r += ((lo & 0x1fffffffu) + 0x0fffffffu + (r & 1u)) >> 29;
   return __uint_as_float(r | (hi & 0x80000000u));
 }
 // widen_f64: exact, as cvt.f64.f32.
