@@ -274,7 +274,8 @@ template <> struct Vec4<double> {
 // (no division per store).  Same stages and shared memory as k_sigma_box.
 template <typename T, typename TX, int KR, int LP, int FBO>
 __global__ void __launch_bounds__(kBoxSigNT) k_sigma_box4(ColDev c, Tables<T> tb, int64_t npts,
-                                                          const TX *__restrict__ X, T *__restrict__ S) {
+                                                          const TX *__restrict__ X, T *__restrict__ S,
+                                                          T *__restrict__ XS) {
   extern __shared__ __align__(16) unsigned char sig_smem[];
   constexpr int PPW = 32 / LP;
   const int nd = c.nd, nn = c.nn, nr = c.nr, rp = c.rp;
@@ -303,6 +304,23 @@ __global__ void __launch_bounds__(kBoxSigNT) k_sigma_box4(ColDev c, Tables<T> tb
     const int64_t p = p0 + ps;
     const bool act = on && p < npts;
     const TX *xp = X + p * nr + f0;
+    const int64_t obase = ((int64_t)(f0 / FBO) * npts + p) * FBO;  // direction 0, first block of this lane
+    const int64_t bstride = npts * FBO;                            // next frequency block
+    // X in the sweep's layout and precision, for the sweep's y = x - I
+    auto put_x = [&](int dd, const TX (&v)[4]) {
+      T t[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) t[j] = cast_to<T>(v[j]);
+      T *o = XS + obase + (int64_t)dd * dstride;
+      if (FBO == 4) {
+        Vec4<T>::st(o, t);
+      } else if (FBO == 2) {
+        o[0] = t[0], o[1] = t[1];
+        o[bstride] = t[2], o[bstride + 1] = t[3];
+      } else {
+        o[0] = t[0], o[bstride] = t[1], o[2 * bstride] = t[2], o[3 * bstride] = t[3];
+      }
+    };
     // 1. moments m_k(f) = sum_d Uw[d][k] X(d, f)
     T m[4][KR];
 #pragma unroll
@@ -322,6 +340,10 @@ __global__ void __launch_bounds__(kBoxSigNT) k_sigma_box4(ColDev c, Tables<T> tb
           for (int j = 0; j < 4; ++j) xv[e][j] = TX(0);
         }
       }
+      if (XS && act) {
+#pragma unroll
+        for (int e = 0; e < kDL; ++e) put_x(d + e, xv[e]);
+      }
 #pragma unroll
       for (int e = 0; e < kDL; ++e) {
         const T *u = sUw + (d + e) * KR;
@@ -339,6 +361,7 @@ __global__ void __launch_bounds__(kBoxSigNT) k_sigma_box4(ColDev c, Tables<T> tb
     for (; d < nd; ++d) {
       TX xv[4] = {TX(0), TX(0), TX(0), TX(0)};
       if (act) Vec4<TX>::ld(xp + (int64_t)d * nn, xv);
+      if (XS && act) put_x(d, xv);
       const T *u = sUw + d * KR;
 #pragma unroll
       for (int k = 0; k < KR; ++k)
@@ -390,8 +413,7 @@ __global__ void __launch_bounds__(kBoxSigNT) k_sigma_box4(ColDev c, Tables<T> tb
     for (int j = 0; j < 4; ++j)
 #pragma unroll
       for (int k = 0; k < KR; ++k) z[j][k] *= g[j];
-    T *out = S + ((int64_t)(f0 / FBO) * npts + p) * FBO;  // direction 0, first block of this lane
-    const int64_t bstride = npts * FBO;                  // next frequency block
+    T *out = S + obase;
     for (int dd = 0; dd < nd; ++dd, out += dstride) {
       const T *u = sUl + dd * KR;
       T acc[4] = {T(0), T(0), T(0), T(0)};
@@ -485,7 +507,8 @@ __global__ void __launch_bounds__(512) k_sweep3d(BoxDev bx, const double *__rest
                                                  const double *__restrict__ I_top,
                                                  const double *__restrict__ I_bot,
                                                  const T *__restrict__ cW0, const T *__restrict__ cB,
-                                                 const T *__restrict__ kap, const T *__restrict__ phi) {
+                                                 const T *__restrict__ kap, const T *__restrict__ phi,
+                                                 const T *__restrict__ xs) {
   using P = Pack<T, FB>;
   extern __shared__ __align__(16) unsigned char sw_smem[];
   const int nx = bx.nx, ny = bx.ny, nz = bx.nz, nn = bx.nn, nd = bx.nd;
@@ -510,6 +533,9 @@ __global__ void __launch_bounds__(512) k_sweep3d(BoxDev bx, const double *__rest
   const T w00 = ((T)1 - ay) * ((T)1 - ax), w01 = ((T)1 - ay) * ax, w10 = ay * ((T)1 - ax), w11 = ay * ax;
   const int step = up ? -1 : 1, k0 = up ? nz - 1 : 0;
   const P *Sd = SL ? SL + ((int64_t)d * nfb + fb) * npts : nullptr;
+  // x already cast to T in the sweep layout (written by the Sigma kernel),
+  // or null: x read in the space-based layout
+  const P *Xd = xs ? reinterpret_cast<const P *>(xs) + ((int64_t)d * nfb + fb) * npts : nullptr;
   const int ie = bx.ie;
   // this thread's cells and their four upwind neighbours (the shift is the
   // same for every plane), packed two 16-bit cell indices per word
@@ -583,7 +609,7 @@ __global__ void __launch_bounds__(512) k_sweep3d(BoxDev bx, const double *__rest
       // loads of CB cells issued together
       P Sc[CB], Cc[CB];
       T Kc[CB];
-      TX xv[CB][FB];
+      T xv[CB][FB];
 #pragma unroll
       for (int u = 0; u < CB; ++u) {
         const int c = threadIdx.x + (i0 + u) * blockDim.x;
@@ -598,13 +624,17 @@ __global__ void __launch_bounds__(512) k_sweep3d(BoxDev bx, const double *__rest
         }
         if (out != kOutI) {
           const int64_t k = (pk + cc) * nr + (int64_t)d * nn + f0;
-          if (vec) {
-            const PX v = *reinterpret_cast<const PX *>(x + k);
+          if (Xd) {
+            const P v = Xd[pk + cc];
 #pragma unroll
             for (int j = 0; j < FB; ++j) xv[u][j] = v.v[j];
+          } else if (vec) {
+            const PX v = *reinterpret_cast<const PX *>(x + k);
+#pragma unroll
+            for (int j = 0; j < FB; ++j) xv[u][j] = cast_to<T>(v.v[j]);
           } else {
 #pragma unroll
-            for (int j = 0; j < FB; ++j) xv[u][j] = f0 + j < nn ? x[k + j] : TX(0);
+            for (int j = 0; j < FB; ++j) xv[u][j] = f0 + j < nn ? cast_to<T>(x[k + j]) : T(0);
           }
         }
       }
@@ -645,7 +675,7 @@ __global__ void __launch_bounds__(512) k_sweep3d(BoxDev bx, const double *__rest
           }
           const T I = fma(e, Iu, fma(a, Su, b * Sc[u].v[j]));
           In[dbl ? 0 : i].v[j] = I;
-          yv.v[j] = out == kOutI ? cast_to<TY>(I) : cast_to<TY>(cast_to<T>(xv[u][j]) - I);
+          yv.v[j] = out == kOutI ? cast_to<TY>(I) : cast_to<TY>(xv[u][j] - I);
         }
         if (vec) {
           *reinterpret_cast<PY *>(y + k) = yv;
@@ -787,7 +817,7 @@ int64_t box_scratch_elems(const rt_handle *h, bool fp64) {
 
 template <typename T, int FB, int CPT, int MODE, typename TX, typename TY>
 static int sweep3d_run(rt_handle *h, const T *chiN, const void *S, const double *tsrc, const TX *x, TY *y, int out,
-                       bool inflow, cudaStream_t s) {
+                       bool inflow, cudaStream_t s, const T *xs) {
   const BoxDev &bx = h->box;
   const int plane = bx.nx * bx.ny;
   const int nfb = (bx.nn + FB - 1) / FB;
@@ -808,57 +838,61 @@ static int sweep3d_run(rt_handle *h, const T *chiN, const void *S, const double 
     phi = reinterpret_cast<const T *>(h->box_phi32);
   }
   kern<<<bx.nd * nfb, nt, smem, s>>>(bx, h->d_geo, chiN, h->box_npad, static_cast<const Pack<T, FB> *>(S), tsrc, x,
-                                     y, out, inflow ? 1 : 0, h->d_Itop, h->d_Ibot, cw, cb, kap, phi);
+                                     y, out, inflow ? 1 : 0, h->d_Itop, h->d_Ibot, cw, cb, kap, phi, xs);
   return (int)cudaGetLastError();
 }
 
 template <typename T, int FB, int MODE, typename TX, typename TY>
 static int sweep3d_cpt(rt_handle *h, int cpt, const T *chiN, const void *S, const double *tsrc, const TX *x, TY *y,
-                       int out, bool inflow, cudaStream_t s) {
+                       int out, bool inflow, cudaStream_t s, const T *xs) {
   constexpr bool f64 = sizeof(T) == 8;
   constexpr int cmax = f64 ? (FB == 2 && MODE != kSwPre ? 2 : 8) : (FB == 4 && MODE != kSwKap ? 4 : 8);
-  if (cpt <= 1) return sweep3d_run<T, FB, 1, MODE>(h, chiN, S, tsrc, x, y, out, inflow, s);
-  if (cpt == 2 || cmax == 2) return sweep3d_run<T, FB, 2, MODE>(h, chiN, S, tsrc, x, y, out, inflow, s);
+  if (cpt <= 1) return sweep3d_run<T, FB, 1, MODE>(h, chiN, S, tsrc, x, y, out, inflow, s, xs);
+  if (cpt == 2 || cmax == 2) return sweep3d_run<T, FB, 2, MODE>(h, chiN, S, tsrc, x, y, out, inflow, s, xs);
   if constexpr (cmax >= 4) {
-    if (cpt == 4 || cmax == 4) return sweep3d_run<T, FB, 4, MODE>(h, chiN, S, tsrc, x, y, out, inflow, s);
+    if (cpt == 4 || cmax == 4) return sweep3d_run<T, FB, 4, MODE>(h, chiN, S, tsrc, x, y, out, inflow, s, xs);
   }
-  if constexpr (cmax >= 8) return sweep3d_run<T, FB, 8, MODE>(h, chiN, S, tsrc, x, y, out, inflow, s);
+  if constexpr (cmax >= 8) return sweep3d_run<T, FB, 8, MODE>(h, chiN, S, tsrc, x, y, out, inflow, s, xs);
   return (int)cudaErrorInvalidConfiguration;
 }
 
 template <typename T, int MODE, typename TX, typename TY>
 static int sweep3d_fb(rt_handle *h, int fb, int cpt, const T *chiN, const void *S, const double *tsrc, const TX *x,
-                      TY *y, int out, bool inflow, cudaStream_t s) {
+                      TY *y, int out, bool inflow, cudaStream_t s, const T *xs) {
   if constexpr (sizeof(T) == 4) {
-    if (fb == 4) return sweep3d_cpt<T, 4, MODE>(h, cpt, chiN, S, tsrc, x, y, out, inflow, s);
+    if (fb == 4) return sweep3d_cpt<T, 4, MODE>(h, cpt, chiN, S, tsrc, x, y, out, inflow, s, xs);
   }
-  if (fb == 2) return sweep3d_cpt<T, 2, MODE>(h, cpt, chiN, S, tsrc, x, y, out, inflow, s);
-  return sweep3d_cpt<T, 1, MODE>(h, cpt, chiN, S, tsrc, x, y, out, inflow, s);
+  if (fb == 2) return sweep3d_cpt<T, 2, MODE>(h, cpt, chiN, S, tsrc, x, y, out, inflow, s, xs);
+  return sweep3d_cpt<T, 1, MODE>(h, cpt, chiN, S, tsrc, x, y, out, inflow, s, xs);
 }
 
 template <typename T, typename TX, typename TY>
 static int sweep3d(rt_handle *h, const void *S, const double *tsrc, const TX *x, TY *y, int out, bool inflow,
-                   cudaStream_t s) {
+                   cudaStream_t s, const T *xs = nullptr) {
   constexpr bool f64 = sizeof(T) == 8;
   const T *chiN = reinterpret_cast<const T *>(f64 ? (const void *)h->chi64 : (const void *)h->chi32);
   int fb, cpt;
   box_shape(h, f64, fb, cpt);
   const int mode = box_mode(h, f64);
   if constexpr (f64) {
-    if (mode == kSwPre) return sweep3d_fb<T, kSwPre>(h, fb, cpt, chiN, S, tsrc, x, y, out, inflow, s);
+    if (mode == kSwPre) return sweep3d_fb<T, kSwPre>(h, fb, cpt, chiN, S, tsrc, x, y, out, inflow, s, xs);
   } else {
-    if (mode == kSwKap) return sweep3d_fb<T, kSwKap>(h, fb, cpt, chiN, S, tsrc, x, y, out, inflow, s);
+    if (mode == kSwKap) return sweep3d_fb<T, kSwKap>(h, fb, cpt, chiN, S, tsrc, x, y, out, inflow, s, xs);
   }
-  return sweep3d_fb<T, kSwChi>(h, fb, cpt, chiN, S, tsrc, x, y, out, inflow, s);
+  return sweep3d_fb<T, kSwChi>(h, fb, cpt, chiN, S, tsrc, x, y, out, inflow, s, xs);
 }
 
+// XS (may be null): also write x, cast to T, in the sweep layout there; set
+// to null when the kernel taken does not (the sweep then reads x itself).
 template <typename T, typename TX>
-static int sigma_box(rt_handle *h, const Tables<T> &tb, const TX *x, T *S, int fb_out, cudaStream_t s) {
+static int sigma_box(rt_handle *h, const Tables<T> &tb, const TX *x, T *S, int fb_out, cudaStream_t s,
+                     T *&XS) {
   const ColDev &c = h->h_cols[0];
   const int64_t npts = (int64_t)h->box.nx * h->box.ny * h->box.nz;
   const int nw = kBoxSigNT / 32;
   const int grid = (int)std::min<int64_t>((npts + nw - 1) / nw, (int64_t)h->n_sm * 16);
   if (c.psi_off >= 0) {
+    XS = nullptr;
     k_sigma_box_dense<T, TX><<<grid, kBoxSigNT, 0, s>>>(c, tb, npts, x, S, fb_out);
     return (int)cudaGetLastError();
   }
@@ -882,7 +916,7 @@ static int sigma_box(rt_handle *h, const Tables<T> &tb, const TX *x, T *S, int f
                                        (size_t)nw * (32 / lp) * (kr * c.nn + 4));
       cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e != cudaSuccess) return (int)e;
-      kern<<<grid4, kBoxSigNT, smem, s>>>(c, tb, npts, x, S);
+      kern<<<grid4, kBoxSigNT, smem, s>>>(c, tb, npts, x, S, XS);
       return (int)cudaGetLastError();
     };
 #define RT_SIGMA_BOX4(KR)                                                                        \
@@ -905,6 +939,7 @@ static int sigma_box(rt_handle *h, const Tables<T> &tb, const TX *x, T *S, int f
     RT_SIGMA_BOX4(6)
 #undef RT_SIGMA_BOX4
   }
+  XS = nullptr;
   const int fl = (c.nn + 31) / 32;
   if (c.rp <= 2) {
     if (fl <= 1) return launch(k_sigma_box<T, TX, 2, 1>, 2);
@@ -935,9 +970,13 @@ static int box_apply_t(rt_handle *h, const Tables<T> &tb, int op, const TX *x, T
   T *St = static_cast<T *>(S);
   int e = 0;
   switch (op) {
-    case 0:  // y = x - Lambda Sigma x
-      if ((e = sigma_box<T, TX>(h, tb, x, St, fb, s))) return e;
-      return sweep3d<T, TX, TY>(h, St, nullptr, x, y, kOutAminus, false, s);
+    case 0: {  // y = x - Lambda Sigma x
+      // float32 operator on the handle's scratch (room for two float32
+      // arrays): Sigma also writes x in the sweep layout behind S
+      T *XS = sizeof(T) == 4 && S == h->apply_S ? St + npts * h->box.nd * h->box_npad : nullptr;
+      if ((e = sigma_box<T, TX>(h, tb, x, St, fb, s, XS))) return e;
+      return sweep3d<T, TX, TY>(h, St, nullptr, x, y, kOutAminus, false, s, XS);
+    }
     case 1:  // y = Lambda x
       if constexpr (sizeof(TX) != 8) return (int)cudaErrorInvalidValue;
       else {
@@ -947,7 +986,8 @@ static int box_apply_t(rt_handle *h, const Tables<T> &tb, int op, const TX *x, T
     case 2:  // y = Sigma x (space-based layout, float64 out)
       if constexpr (sizeof(TY) != 8) return (int)cudaErrorInvalidValue;
       else {
-        if ((e = sigma_box<T, TX>(h, tb, x, St, fb, s))) return e;
+        T *no_xs = nullptr;
+        if ((e = sigma_box<T, TX>(h, tb, x, St, fb, s, no_xs))) return e;
         k_box_from_sweep<T><<<(int)std::min<int64_t>(npts, 65535), 256, 0, s>>>(St, y, npts, h->box.nd, h->box.nn, fb);
         return (int)cudaGetLastError();
       }
