@@ -270,6 +270,13 @@ def lambda_3d(prob: Problem, S: np.ndarray, with_inflow: bool = False) -> np.nda
     units); with Omega_z < 0 it is in plane k-1.  Along the segment
     ds = dz/|Omega_z| the optical depth is 0.5 (chi_u + chi_c) ds and the step
     is the 1D recurrence.  Inflow planes are 0 unless ``with_inflow``.
+
+    Quadratic short characteristics (FS_QSC, the Sec. 5.3 integrator): the
+    downwind point continues the ray one segment past the cell, into the next
+    plane at the opposite shift +(Omega_x, Omega_y) dz/|Omega_z|; S and chi
+    there are interpolated the same way, the downwind optical depth is
+    0.5 (chi_c + chi_d) ds, and the step takes qsc_coefficients.  The last
+    plane a ray reaches has no downwind point and takes the linear step.
     """
     nx, ny, nz, nd, nn = prob.nx, prob.ny, prob.nz, prob.n_dir, prob.n_nu
     dx, dy, dz = (float(v) for v in prob.z)
@@ -299,8 +306,16 @@ def lambda_3d(prob: Problem, S: np.ndarray, with_inflow: bool = False) -> np.nda
             Sc = np.moveaxis(S[k, :, :, d, :], -1, 0)
             cc = np.moveaxis(chi[k], -1, 0)
             dtau = 0.5 * (cu + cc) * ds
-            e, al, be = step_coefficients(dtau, prob.formal_solver)
-            Iplane = e * Iu + al * Su + be * Sc
+            kd = k - prev                                  # downwind plane
+            if prob.formal_solver == FS_QSC and 0 <= kd < nz:
+                Sd = _bilinear_periodic(np.moveaxis(S[kd, :, :, d, :], -1, 0), -sx, -sy)
+                cd = _bilinear_periodic(np.moveaxis(chi[kd], -1, 0), -sx, -sy)
+                e, pu, pc, pd = qsc_coefficients(dtau, 0.5 * (cc + cd) * ds)
+                Iplane = e * Iu + pu * Su + pc * Sc + pd * Sd
+            else:
+                fs = FS_SCL if prob.formal_solver == FS_QSC else prob.formal_solver
+                e, al, be = step_coefficients(dtau, fs)
+                Iplane = e * Iu + al * Su + be * Sc
             I[k, :, :, d, :] = np.moveaxis(Iplane, 0, -1)
     return I.reshape(-1)
 

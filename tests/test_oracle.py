@@ -527,6 +527,77 @@ def test_3d_integer_offset_follows_the_diagonal():
             assert I[0, y, x0] == 0.0
 
 
+def _diagonal_qsc(chi_line, S_line, ds):
+    """1D quadratic short characteristics along one ray through the cells
+    chi_line[k], S_line[k] (k in sweep order, unit segments of length ds): the
+    upwind, current and downwind cells of step k are k-1, k, k+1; the last
+    step is linear.  Inflow 0."""
+    nz = len(S_line)
+    out = np.zeros(nz)
+    for k in range(1, nz):
+        du = 0.5 * (chi_line[k - 1] + chi_line[k]) * ds
+        if k < nz - 1:
+            dd = 0.5 * (chi_line[k] + chi_line[k + 1]) * ds
+            e, pu, pc, pd = O.qsc_coefficients(np.array(du), np.array(dd))
+            src = pu * S_line[k - 1] + pc * S_line[k] + pd * S_line[k + 1]
+        else:
+            e, al, be = O.step_coefficients(np.array(du), W.FS_SCL)
+            src = al * S_line[k - 1] + be * S_line[k]
+        out[k] = e * out[k - 1] + src
+    return out
+
+
+@pytest.mark.parametrize("sgn", [-1.0, 1.0])
+def test_3d_qsc_integer_offset_follows_the_diagonal(sgn):
+    """Quadratic short characteristics in 3D with Omega = (1, 0, sgn)/sqrt(2),
+    unit cells: upwind and downwind points are exactly the cells (x -+ 1) of
+    the neighbouring planes, so every diagonal line is an independent 1D QSC
+    ray (a downwind shift taken with the wrong sign, or a wrong downwind
+    plane, breaks it)."""
+    rng = np.random.default_rng(14)
+    n, nz = 6, 7
+    dirs = np.array([[1 / math.sqrt(2), 0.0, sgn / math.sqrt(2)]])
+    box = W.Problem(dims=3, nx=n, ny=n, nz=nz, z=np.array([1.0, 1.0, 1.0]), dirs=dirs,
+                    w_dir=np.ones(1), w_nu=np.ones(1), chi=rng.uniform(0.05, 3, (n * n * nz, 1)),
+                    gamma=np.zeros((n * n * nz, 1)), I_top=np.zeros(1), I_bot=np.zeros(1),
+                    formal_solver=W.FS_QSC)
+    S = rng.standard_normal(box.n)
+    I = O.lambda_3d(box, S).reshape(nz, n, n)
+    Sg = S.reshape(nz, n, n)
+    chi = box.chi.reshape(nz, n, n)
+    planes = list(range(nz)) if sgn < 0 else list(range(nz - 1, -1, -1))  # sweep order
+    for y in range(n):
+        for x0 in range(n):
+            xs = [(x0 + i) % n for i in range(nz)]         # the ray moves +1 in x per plane
+            ref = _diagonal_qsc(np.array([chi[k, y, x] for k, x in zip(planes, xs)]),
+                                np.array([Sg[k, y, x] for k, x in zip(planes, xs)]), math.sqrt(2.0))
+            got = np.array([I[k, y, x] for k, x in zip(planes, xs)])
+            assert np.abs(got - ref).max() < 1e-13
+
+
+def test_3d_qsc_homogeneous_box_is_the_1d_column():
+    """A box whose opacity and source vary only with z: with QSC every
+    direction of every cell reproduces the 1D QSC column (Sec. 3.2 recurrence
+    with the quadratic integrator) for mu = Omega_z, with inflow."""
+    rng = np.random.default_rng(15)
+    nx, ny, nz, nn = 4, 3, 8, 3
+    dirs, wd = W.level_symmetric(4)
+    chi1 = rng.uniform(0.05, 4.0, (nz, nn))
+    S1 = rng.standard_normal((nz, len(dirs), nn))
+    dz = 0.7
+    box = W.Problem(dims=3, nx=nx, ny=ny, nz=nz, z=np.array([1.1, 0.9, dz]), dirs=dirs, w_dir=wd,
+                    w_nu=np.ones(nn), chi=np.repeat(chi1, nx * ny, axis=0),
+                    gamma=np.zeros((nx * ny * nz, nn)), I_top=rng.uniform(0, 1, nn),
+                    I_bot=rng.uniform(0, 1, nn), formal_solver=W.FS_QSC)
+    col = W.Problem(dims=1, nx=1, ny=1, nz=nz, z=dz * np.arange(nz), dirs=dirs, w_dir=wd,
+                    w_nu=np.ones(nn), chi=chi1, gamma=np.zeros((nz, nn)), I_top=box.I_top,
+                    I_bot=box.I_bot, formal_solver=W.FS_QSC)
+    S3 = np.broadcast_to(S1[:, None, None], (nz, ny, nx, len(dirs), nn)).reshape(-1)
+    I3 = O.lambda_3d(box, S3, with_inflow=True).reshape(nz, ny, nx, len(dirs), nn)
+    I1 = O.lambda_op(col, S1.reshape(-1), with_inflow=True).reshape(nz, len(dirs), nn)
+    assert np.abs(I3 - I1[:, None, None]).max() < 1e-13 * np.abs(I1).max()
+
+
 def test_3d_half_offset_interpolates_two_cells():
     """Upwind offset of half a cell in y: the upwind value is the mean of the
     two neighbouring cells of the upwind plane."""
