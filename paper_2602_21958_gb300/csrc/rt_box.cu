@@ -101,6 +101,77 @@ __device__ __forceinline__ void step_coef<double>(double d, int ie, double &e, d
   a = w0 - beta;
 }
 
+// Quadratic short-characteristics step (Sec. 5.3 integrator): S is the
+// parabola through the upwind, current and downwind points, at optical path
+// -du, 0 and +dd from the current point, integrated exactly against the
+// attenuation:  I_c = e I_u + pu S_u + pc S_c + pd S_d  with the moments
+// W1 = du - w0 and W2 = du^2 - 2 W1 taken as a = W1 / du^2 and
+// m = a - W2 / du^3 = (W1 (du + 2) - du^2) / du^3:
+//   pc = du a + du^2 m / dd,  pd = -du^3 m / (dd (du + dd)),
+//   pu = w0 - du a - du^2 m / (du + dd)      (the three sum to w0).
+// Below the cut a and m come from their series, a = sum (-du)^k / (k+2)! and
+// m = sum (-du)^k (k+1) / (k+3)!, which do not cancel.
+template <typename T>
+__device__ __forceinline__ void qsc_coef(T du, T dd, T &e, T &pu, T &pc, T &pd);
+
+template <>
+__device__ __forceinline__ void qsc_coef<float>(float du, float dd, float &e, float &pu, float &pc, float &pd) {
+  e = __expf(-du);
+  float w0, a, m;
+  if (du < 0.5f) {
+    // 8 terms each: the first dropped ones, du^8/10! and 9 du^8/11!, stay below 1.2e-9
+    float s0 = 1.f;
+#pragma unroll
+    for (int j = 9; j >= 2; --j) s0 = 1.f - du * (1.f / (float)j) * s0;
+    w0 = du * s0;
+    a = 0.f, m = 0.f;
+    float ik = 1.f / 362880.f;  // 1/(k+2)! at k = 7
+#pragma unroll
+    for (int k = 7; k >= 0; --k) {
+      a = fmaf(-du, a, ik);
+      m = fmaf(-du, m, ik * (float)(k + 1) / (float)(k + 3));
+      ik *= (float)(k + 2);
+    }
+  } else {
+    w0 = 1.f - e;
+    const float w1 = du - w0;
+    const float r = 1.f / du;
+    a = w1 * r * r;
+    m = (w1 * (du + 2.f) - du * du) * r * r * r;
+  }
+  const float q = du * du * m;
+  pc = du * a + q / dd;
+  pd = -q * du / (dd * (du + dd));
+  pu = w0 - du * a - q / (du + dd);
+}
+
+template <>
+__device__ __forceinline__ void qsc_coef<double>(double du, double dd, double &e, double &pu, double &pc,
+                                                 double &pd) {
+  e = exp(-du);
+  const double w0 = -expm1(-du);
+  double a, m;
+  if (du < 0.1) {
+    // 18 terms each
+    a = 0.0, m = 0.0;
+    double ik = 1.0 / 121645100408832000.0;  // 1/(k+2)! at k = 17 (1/19!)
+#pragma unroll
+    for (int k = 17; k >= 0; --k) {
+      a = fma(-du, a, ik);
+      m = fma(-du, m, ik * (double)(k + 1) / (double)(k + 3));  // (k+1)/(k+3)!
+      ik *= (double)(k + 2);
+    }
+  } else {
+    const double w1 = du - w0;
+    a = w1 / (du * du);
+    m = (w1 * (du + 2.0) - du * du) / (du * du * du);
+  }
+  const double q = du * du * m;
+  pc = du * a + q / dd;
+  pd = -q * du / (dd * (du + dd));
+  pu = w0 - du * a - q / (du + dd);
+}
+
 // ------------------------------------------------------------------ Sigma
 constexpr int kBoxSigNT = 256;     // threads per Sigma CTA (8 warps, one point each)
 constexpr int kBoxRwCache = 32768;  // bytes of frequency kernel staged in shared memory (else global)
@@ -495,8 +566,12 @@ __global__ void k_box_from_sweep(const T *__restrict__ S, double *__restrict__ y
 // (interpolated at the upwind point); kSwPre: precomputed (1 - e^-d, w1/d)
 // in cW0, cB (float64 boxes); kSwKap: the opacity is kappa(p) phi(nu)
 // (detected at creation), so shared memory holds one kappa per cell (kap)
-// instead of FB opacities and d = ds/2 phi (kappa_u + kappa_c).
-enum { kSwChi = 0, kSwPre = 1, kSwKap = 2 };
+// instead of FB opacities and d = ds/2 phi (kappa_u + kappa_c); kSwQsc:
+// quadratic short characteristics, the opacity as kSwChi, plus S and chi
+// at the downwind point (the upwind stencil mirrored, in the next plane,
+// gathered from global memory: that plane is not in shared memory) and the
+// qsc_coef weights; the last plane of the sweep takes the linear step.
+enum { kSwChi = 0, kSwPre = 1, kSwKap = 2, kSwQsc = 3 };
 
 template <typename T, int FB, int CPT, int CB, typename TX, typename TY, int MODE>
 __global__ void __launch_bounds__(512) k_sweep3d(BoxDev bx, const double *__restrict__ geo,
@@ -539,11 +614,14 @@ __global__ void __launch_bounds__(512) k_sweep3d(BoxDev bx, const double *__rest
   const int ie = bx.ie;
   // this thread's cells and their four upwind neighbours (the shift is the
   // same for every plane), packed two 16-bit cell indices per word
+  constexpr bool qsc = MODE == kSwQsc;
   uint32_t nb0[CPT], nb1[CPT];
+  uint32_t nd0[qsc ? CPT : 1], nd1[qsc ? CPT : 1];  // kSwQsc: the downwind stencil
 #pragma unroll
   for (int i = 0; i < CPT; ++i) {
     const int c = threadIdx.x + i * blockDim.x;
     nb0[i] = nb1[i] = 0;
+    if (qsc) nd0[i] = nd1[i] = 0;
     if (c < plane) {
       const int yy = c / nx, xx = c - yy * nx;
       int x0 = xx - fx, y0 = yy - fy;
@@ -553,6 +631,16 @@ __global__ void __launch_bounds__(512) k_sweep3d(BoxDev bx, const double *__rest
       const int y1 = y0 == 0 ? ny - 1 : y0 - 1;
       nb0[i] = (uint32_t)(y0 * nx + x0) | ((uint32_t)(y0 * nx + x1) << 16);
       nb1[i] = (uint32_t)(y1 * nx + x0) | ((uint32_t)(y1 * nx + x1) << 16);
+      if (qsc) {
+        // the point (xx + fx + ax, yy + fy + ay): cells +0 / +1, same weights
+        int u0 = xx + fx, v0 = yy + fy;
+        if (u0 >= nx) u0 -= nx;
+        if (v0 >= ny) v0 -= ny;
+        const int u1 = u0 + 1 == nx ? 0 : u0 + 1;
+        const int v1 = v0 + 1 == ny ? 0 : v0 + 1;
+        nd0[qsc ? i : 0] = (uint32_t)(v0 * nx + u0) | ((uint32_t)(v0 * nx + u1) << 16);
+        nd1[qsc ? i : 0] = (uint32_t)(v1 * nx + u0) | ((uint32_t)(v1 * nx + u1) << 16);
+      }
     }
   }
   auto load_src = [&](int64_t p) -> P {
@@ -588,7 +676,7 @@ __global__ void __launch_bounds__(512) k_sweep3d(BoxDev bx, const double *__rest
       if (c >= plane) continue;
       sI[c] = I0;
       sS[c] = load_src(pk + c);
-      if (MODE == kSwChi) sC[c] = load_chi(pk + c);
+      if (MODE == kSwChi || qsc) sC[c] = load_chi(pk + c);
       if (MODE == kSwKap) sK[c] = kap[pk + c];
       const int64_t k = (pk + c) * nr + (int64_t)d * nn + f0;
 #pragma unroll
@@ -656,12 +744,29 @@ __global__ void __launch_bounds__(512) k_sweep3d(BoxDev bx, const double *__rest
           C00 = sC[c00], C01 = sC[c01], C10 = sC[c10], C11 = sC[c11];
         }
         const int64_t k = (pk + c) * nr + (int64_t)d * nn + f0;
+        // kSwQsc away from the last plane: S and chi at the downwind point
+        P Sdw, Cdw;
+        const bool quad = qsc && s + 1 < nz;
+        if (quad) {
+          const int64_t pd = pk + (int64_t)step * plane;
+          const int e00 = nd0[qsc ? i : 0] & 0xffff, e01 = nd0[qsc ? i : 0] >> 16;
+          const int e10 = nd1[qsc ? i : 0] & 0xffff, e11 = nd1[qsc ? i : 0] >> 16;
+          const P A00 = load_src(pd + e00), A01 = load_src(pd + e01), A10 = load_src(pd + e10),
+                  A11 = load_src(pd + e11);
+          const P B00 = load_chi(pd + e00), B01 = load_chi(pd + e01), B10 = load_chi(pd + e10),
+                  B11 = load_chi(pd + e11);
+#pragma unroll
+          for (int j = 0; j < FB; ++j) {
+            Sdw.v[j] = w00 * A00.v[j] + w01 * A01.v[j] + w10 * A10.v[j] + w11 * A11.v[j];
+            Cdw.v[j] = w00 * B00.v[j] + w01 * B01.v[j] + w10 * B10.v[j] + w11 * B11.v[j];
+          }
+        }
         PY yv;
 #pragma unroll
         for (int j = 0; j < FB; ++j) {
           const T Iu = w00 * I00.v[j] + w01 * I01.v[j] + w10 * I10.v[j] + w11 * I11.v[j];
           const T Su = w00 * S00.v[j] + w01 * S01.v[j] + w10 * S10.v[j] + w11 * S11.v[j];
-          T e, a, b;
+          T e, a, b, pdS = T(0);
           if (MODE == kSwPre) {
             const T w0 = Cc[u].v[j];
             e = (T)1 - w0;
@@ -671,9 +776,15 @@ __global__ void __launch_bounds__(512) k_sweep3d(BoxDev bx, const double *__rest
             step_coef<T>(hphi[j] * Ku, ie, e, a, b);
           } else {
             const T Cu = w00 * C00.v[j] + w01 * C01.v[j] + w10 * C10.v[j] + w11 * C11.v[j];
-            step_coef<T>(hds * (Cu + Cc[u].v[j]), ie, e, a, b);
+            if (quad) {  // weights of the upwind, current and downwind source
+              T wd;
+              qsc_coef<T>(hds * (Cu + Cc[u].v[j]), hds * (Cc[u].v[j] + Cdw.v[j]), e, a, b, wd);
+              pdS = wd * Sdw.v[j];
+            } else {
+              step_coef<T>(hds * (Cu + Cc[u].v[j]), qsc ? 0 : ie, e, a, b);
+            }
           }
-          const T I = fma(e, Iu, fma(a, Su, b * Sc[u].v[j]));
+          const T I = quad ? fma(e, Iu, fma(a, Su, fma(b, Sc[u].v[j], pdS))) : fma(e, Iu, fma(a, Su, b * Sc[u].v[j]));
           In[dbl ? 0 : i].v[j] = I;
           yv.v[j] = out == kOutI ? cast_to<TY>(I) : cast_to<TY>(xv[u][j] - I);
         }
@@ -694,7 +805,7 @@ __global__ void __launch_bounds__(512) k_sweep3d(BoxDev bx, const double *__rest
       if (c >= plane) continue;
       if (!dbl) sI[c] = In[i];
       sS[c] = load_src(pk + c);
-      if (MODE == kSwChi) sC[c] = load_chi(pk + c);
+      if (MODE == kSwChi || qsc) sC[c] = load_chi(pk + c);
       if (MODE == kSwKap) sK[c] = kap[pk + c];
     }
     __syncthreads();
@@ -757,6 +868,7 @@ __global__ void k_box_coef64(BoxDev bx, const double *__restrict__ geo, const do
 // ------------------------------------------------------------ host side
 // Step-weight mode of the sweep for one precision (see k_sweep3d).
 static int box_mode(const rt_handle *h, bool fp64) {
+  if (h->box.qsc) return kSwQsc;
   if (fp64) return h->box_w064 ? kSwPre : kSwChi;
   return h->box_kap32 ? kSwKap : kSwChi;
 }
@@ -766,7 +878,7 @@ static int box_mode(const rt_handle *h, bool fp64) {
 static size_t box_smem(const rt_handle *h, bool fp64, int fb) {
   const size_t plane = (size_t)h->box.nx * h->box.ny, esz = fp64 ? 8 : 4;
   const int mode = box_mode(h, fp64);
-  return plane * esz * (2 * fb + (mode == kSwChi ? fb : mode == kSwKap ? fb + 1 : 0));
+  return plane * esz * (2 * fb + ((mode == kSwChi || mode == kSwQsc) ? fb : mode == kSwKap ? fb + 1 : 0));
 }
 
 // Launch shape of the sweep for one precision: FB frequencies per CTA and
@@ -778,6 +890,7 @@ static size_t box_smem(const rt_handle *h, bool fp64, int fb) {
 // 512 threads, not wider than the frequencies need; rt_autotune may cap FB
 // and raise CPT.
 static int box_cpt_max(bool fp64, int fb, int mode) {
+  if (mode == kSwQsc) return fb == 1 ? 4 : 2;
   if (fp64) return fb == 2 && mode != kSwPre ? 2 : 8;
   return fb == 4 && mode != kSwKap ? 4 : 8;
 }
@@ -846,7 +959,8 @@ template <typename T, int FB, int MODE, typename TX, typename TY>
 static int sweep3d_cpt(rt_handle *h, int cpt, const T *chiN, const void *S, const double *tsrc, const TX *x, TY *y,
                        int out, bool inflow, cudaStream_t s, const T *xs) {
   constexpr bool f64 = sizeof(T) == 8;
-  constexpr int cmax = f64 ? (FB == 2 && MODE != kSwPre ? 2 : 8) : (FB == 4 && MODE != kSwKap ? 4 : 8);
+  constexpr int cmax = MODE == kSwQsc ? (FB == 1 ? 4 : 2)
+                                      : f64 ? (FB == 2 && MODE != kSwPre ? 2 : 8) : (FB == 4 && MODE != kSwKap ? 4 : 8);
   if (cpt <= 1) return sweep3d_run<T, FB, 1, MODE>(h, chiN, S, tsrc, x, y, out, inflow, s, xs);
   if (cpt == 2 || cmax == 2) return sweep3d_run<T, FB, 2, MODE>(h, chiN, S, tsrc, x, y, out, inflow, s, xs);
   if constexpr (cmax >= 4) {
@@ -874,6 +988,7 @@ static int sweep3d(rt_handle *h, const void *S, const double *tsrc, const TX *x,
   int fb, cpt;
   box_shape(h, f64, fb, cpt);
   const int mode = box_mode(h, f64);
+  if (mode == kSwQsc) return sweep3d_fb<T, kSwQsc>(h, fb, cpt, chiN, S, tsrc, x, y, out, inflow, s, xs);
   if constexpr (f64) {
     if (mode == kSwPre) return sweep3d_fb<T, kSwPre>(h, fb, cpt, chiN, S, tsrc, x, y, out, inflow, s, xs);
   } else {
@@ -1055,7 +1170,7 @@ int box_prepare(rt_handle *h, const double *chi) {
           pr = p;
           fr = f;
         }
-    bool sep = cmax > 0.0;
+    bool sep = cmax > 0.0 && !h->box.qsc;  // the quadratic sweep reads the full opacity
     std::vector<double> phi(nn), kap(npts);
     for (int f = 0; f < nn && sep; ++f) phi[f] = chi[(size_t)pr * nn + f];
     for (int64_t p = 0; p < npts && sep; ++p) {
@@ -1079,7 +1194,7 @@ int box_prepare(rt_handle *h, const double *chi) {
   // and RT_BOX_COEF64 is not "0" (then the float64 sweep forms them on the fly)
   const int64_t ncoef = (int64_t)h->box.nd * npts * ((nn + 1) / 2) * 2;
   const char *env = std::getenv("RT_BOX_COEF64");
-  const bool allow = !(env && env[0] == '0' && env[1] == 0);
+  const bool allow = !(env && env[0] == '0' && env[1] == 0) && !h->box.qsc;
   size_t free_b = 0, total_b = 0;
   if (allow && cudaMemGetInfo(&free_b, &total_b) == cudaSuccess && (double)ncoef * 16.0 <= 0.25 * (double)free_b) {
     e = cudaMalloc(&h->box_w064, (size_t)ncoef * 8);

@@ -188,9 +188,65 @@ def test_box_sigma_four_frequencies_per_lane(rt, monkeypatch, fb, n_nu, kernel, 
         assert rel(y.cpu().numpy(), ref) < bar, (op, fb)
 
 
-def test_quadratic_formal_solver_is_rejected_for_boxes(rt):
-    # quadratic short characteristics are built for 1D columns only
-    p = dataclasses.replace(small_box(), formal_solver=W.FS_QSC)
-    with pytest.raises(rt.RTError) as e:
-        rt.Handle(p)
-    assert e.value.code == rt.RT_ERR_ARG
+def qsc_box(separable=True, **kw):
+    p = small_box(**kw) if separable else nonseparable_box(**kw)
+    return dataclasses.replace(p, formal_solver=W.FS_QSC)
+
+
+@pytest.mark.parametrize("fb", ["1", "2"])
+@pytest.mark.parametrize("separable", [True, False])
+@pytest.mark.parametrize("op", [0, 1, 2, 3])
+def test_box_qsc_fp64(rt, monkeypatch, fb, separable, op):
+    """Quadratic short characteristics in 3D (downwind point mirrored into
+    the next plane, linear last step) against the oracle, float64, every
+    operator, both sweep block widths."""
+    monkeypatch.setenv("RT_BOX_FB", fb)
+    p = qsc_box(separable, nx=6, ny=7, nz=6, n_nu=5, kernel="r2", seed=11)
+    h = rt.Handle(p, precision=rt.RT_P_FP64, max_restart=4)
+    x = W.random_vectors(p.n, 1, 80 + op)[0]
+    y = torch.empty(p.n, dtype=torch.float64, device="cuda:0")
+    h.rt_apply(op, dev(x), y)
+    torch.cuda.synchronize()
+    ref = oracle_op(p, op, x)
+    assert rel(y.cpu().numpy(), ref) < 1e-12
+    assert np.abs(y.cpu().numpy() - ref).max() < 1e-12 * np.abs(ref).max()
+
+
+def test_box_qsc_integer_offset_direction(rt):
+    """Diagonal directions whose upwind and downwind points are exact cells,
+    both sweep senses."""
+    p = qsc_box(nx=6, ny=6, nz=6, spacing=(1.0, 1.0, 1.0))
+    d = np.array([[1 / math.sqrt(2), 0.0, -1 / math.sqrt(2)], [0.0, -1 / math.sqrt(2), 1 / math.sqrt(2)]])
+    p = dataclasses.replace(p, dirs=d, w_dir=np.array([0.5, 0.5]), P=np.ones((2, 2)))
+    h = rt.Handle(p, precision=rt.RT_P_FP64, max_restart=8)
+    x = W.random_vectors(p.n, 1, 91)[0]
+    y = torch.empty(p.n, dtype=torch.float64, device="cuda:0")
+    h.rt_apply(1, dev(x), y)
+    torch.cuda.synchronize()
+    assert rel(y.cpu().numpy(), O.lambda_op(p, x)) < 1e-13
+
+
+@pytest.mark.parametrize("separable", [True, False])
+@pytest.mark.parametrize("op", [0, 1])
+def test_box_qsc_mixed(rt, separable, op):
+    """The float32 quadratic sweep (series below an optical depth of 0.5)
+    within the mixed-apply bar."""
+    p = qsc_box(separable, nx=9, ny=8, nz=7, order=6, n_nu=8, kernel="r2", seed=12)
+    h = rt.Handle(p, precision=rt.RT_P_MIXED, max_restart=8)
+    x = W.random_vectors(p.n, 1, 95 + op, "uniform")[0]
+    y = torch.empty(p.n, dtype=torch.float64, device="cuda:0")
+    h.rt_apply(op, dev(x), y)
+    torch.cuda.synchronize()
+    assert rel(y.cpu().numpy(), oracle_op(p, op, x)) < 2e-5
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_box_qsc_solve(rt, prec):
+    p = qsc_box(nx=6, ny=5, nz=6, order=4, n_nu=5, kernel="r2", eps=1e-3)
+    xref = O.solve_gmres(p, tol=1e-14, restart=300, max_iter=600).x
+    h = rt.Handle(p, precision=rt.RT_P_FP64 if prec == "fp64" else rt.RT_P_MIXED, max_restart=120)
+    x = torch.zeros(p.n, dtype=torch.float64, device="cuda:0")
+    info = h.rt_solve(None, x, tol=1e-13, tol_inner=1e-5, restart=120, max_outer=30)
+    torch.cuda.synchronize()
+    assert info["status"] == 0, info
+    assert rel(x.cpu().numpy(), xref) < 1e-10
