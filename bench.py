@@ -440,7 +440,8 @@ def configs_sweep(rank: int = 0) -> dict:
     vector) and the float64 BiCGStab (all four).  The mixed solve is the
     nested float64 FGMRES(32) + float32 GMRES cycles for the 1D columns (C2
     also with a 60-step inner cycle) and, for the boxes, restarted float32
-    GMRES(m) with float64 residuals and refinement (C4: m = 12)."""
+    GMRES(m) with float64 residuals and refinement (C4: m = 12).  C3 also
+    with quadratic short characteristics (applies, mixed solve)."""
     import torch
 
     from paper_2602_21958_gb300 import workloads as W
@@ -459,7 +460,7 @@ def config_entry(name, p) -> dict:
     """The figures of one configuration (see configs_sweep)."""
     import torch
 
-    from paper_2602_21958_gb300 import rt
+    from paper_2602_21958_gb300 import rt, workloads as W
 
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     stream = torch.cuda.current_stream()
@@ -520,6 +521,37 @@ def config_entry(name, p) -> dict:
         h.close()
         del x, y, b
         torch.cuda.empty_cache()
+    if name == "C3":
+        # the same box with quadratic short characteristics (RT_FS_QSC):
+        # apply times in both precisions, mixed solve to 1e-10
+        import dataclasses
+
+        pq = dataclasses.replace(p, formal_solver=W.FS_QSC)
+        entry["qsc"] = {"applies_ms": {}}
+        for label, prec in (("mixed", rt.RT_P_MIXED), ("fp64", rt.RT_P_FP64)):
+            h = rt.Handle(pq, n_rhs=1, precision=prec, max_restart=24)
+            h.rt_autotune()
+            x = torch.rand(p.n, dtype=torch.float64, device=dev)
+            y = torch.empty_like(x)
+            for _ in range(3):
+                h.rt_apply(rt.RT_OP_A, x, y)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(20):
+                h.rt_apply(rt.RT_OP_A, x, y)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            entry["qsc"]["applies_ms"][label] = e0.elapsed_time(e1) / 20
+            if label == "mixed":
+                b = y
+                h.rt_apply(rt.RT_OP_RHS, None, b, fp64=True)
+                kw = dict(tol=1e-10, restart=24, max_outer=MAX_OUTER, tol_inner=TOL_INNER, inner_restart=0)
+                timed_solve(h, b, x, **kw)
+                entry["qsc"]["solve_ms_mixed"], entry["qsc"]["iterations_mixed"] = timed_solve(h, b, x, **kw)
+            h.close()
+            del x, y
+            torch.cuda.empty_cache()
     return entry
 
 
