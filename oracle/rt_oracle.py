@@ -26,7 +26,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from paper_2602_21958_gb300.workloads import FS_IE, FS_QSC, FS_SCL, Problem
+from paper_2602_21958_gb300.workloads import FS_IE, FS_LC, FS_QSC, FS_SCL, Problem
 
 SERIES_CUT = 0.1
 
@@ -320,10 +320,54 @@ def lambda_3d(prob: Problem, S: np.ndarray, with_inflow: bool = False) -> np.nda
     return I.reshape(-1)
 
 
+def lambda_3d_lc(prob: Problem, S: np.ndarray, with_inflow: bool = False) -> np.ndarray:
+    """Long characteristics in a box periodic in x, y (the rays of Sec. 3.4
+    followed from boundary to point, TRIP's treatment of the 3D transfer named
+    in Sec. 5.3): the value at cell (k, y, x) in direction Omega comes from the
+    straight ray through that cell traced back to the inflow plane.  That ray
+    crosses plane k' (between the inflow plane and k) at the cell position
+    shifted back by (k - k') (Omega_x, Omega_y) dz/|Omega_z|; S and chi there
+    are interpolated bilinearly (periodic), the intensity never is.  Along the
+    ray the linear SC-L step of eqs. ie_1/ie_2's recurrence is taken from
+    crossing to crossing, optical depth 0.5 (chi_a + chi_b) ds per segment,
+    starting from the inflow (0 unless ``with_inflow``)."""
+    nx, ny, nz, nd, nn = prob.nx, prob.ny, prob.nz, prob.n_dir, prob.n_nu
+    dx, dy, dz = (float(v) for v in prob.z)
+    S = np.asarray(S, dtype=float).reshape(nz, ny, nx, nd, nn)
+    chi = prob.chi.reshape(nz, ny, nx, nn)
+    I = np.zeros_like(S)
+    for d in range(nd):
+        ox, oy, oz = prob.dirs[d]
+        ds = dz / abs(oz)
+        sx, sy = ox * ds / dx, oy * ds / dy
+        first, step = (nz - 1, -1) if oz > 0 else (0, 1)
+        inflow = prob.I_bot if oz > 0 else prob.I_top
+        I0 = np.zeros((nn, ny, nx))
+        if with_inflow:
+            I0[:] = inflow[:, None, None]
+        I[first, :, :, d, :] = np.moveaxis(I0, 0, -1)
+        for s in range(1, nz):                      # target plane first + s * step
+            Iray = I0.copy()
+            Sa = ca = None
+            for m in range(s + 1):                  # crossing m: plane first + m * step
+                km = first + m * step
+                t = s - m                           # segments between the crossing and the target
+                Sm = _bilinear_periodic(np.moveaxis(S[km, :, :, d, :], -1, 0), t * sx, t * sy)
+                cm = _bilinear_periodic(np.moveaxis(chi[km], -1, 0), t * sx, t * sy)
+                if m > 0:
+                    e, al, be = step_coefficients(0.5 * (ca + cm) * ds, FS_SCL)
+                    Iray = e * Iray + al * Sa + be * Sm
+                Sa, ca = Sm, cm
+            I[first + s * step, :, :, d, :] = np.moveaxis(Iray, 0, -1)
+    return I.reshape(-1)
+
+
 def lambda_op(prob: Problem, S: np.ndarray, with_inflow: bool = False) -> np.ndarray:
     """Lambda_N S (+ I_in) for a 1D column or a 3D box (Sec. 3.2, Sec. 3.4)."""
     if prob.dims == 1:
         return lambda_1d(prob, S, with_inflow)
+    if prob.formal_solver == FS_LC:
+        return lambda_3d_lc(prob, S, with_inflow)
     return lambda_3d(prob, S, with_inflow)
 
 

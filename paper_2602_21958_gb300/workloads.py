@@ -38,7 +38,8 @@ SEED_BASE = 20262195
 
 FS_SCL = "scl"  # linear short-characteristics exponential integrator
 FS_IE = "ie"    # implicit Euler (eqs. ie_1, ie_2)
-FS_QSC = "qsc"  # quadratic short-characteristics exponential integrator (1D)
+FS_QSC = "qsc"  # quadratic short-characteristics exponential integrator
+FS_LC = "lc"    # long characteristics (3D boxes): linear steps along each point's own ray
 
 
 @dataclasses.dataclass

@@ -598,6 +598,98 @@ def test_3d_qsc_homogeneous_box_is_the_1d_column():
     assert np.abs(I3 - I1[:, None, None]).max() < 1e-13 * np.abs(I1).max()
 
 
+def _lc_box(rng, dirs, n=(5, 4, 6), nn=2, fs=None):
+    nx, ny, nz = n
+    return W.Problem(dims=3, nx=nx, ny=ny, nz=nz, z=np.array([1.0, 1.3, 0.8]), dirs=dirs,
+                     w_dir=np.ones(len(dirs)) / len(dirs), w_nu=np.ones(nn),
+                     chi=rng.uniform(0.05, 3.0, (nx * ny * nz, nn)), gamma=np.zeros((nx * ny * nz, nn)),
+                     I_top=rng.uniform(0, 1, nn), I_bot=rng.uniform(0, 1, nn),
+                     formal_solver=fs or W.FS_LC)
+
+
+def test_3d_lc_integer_offsets_equal_short_characteristics():
+    """With integer cell offsets per plane the ray of every point passes
+    through cell centres only, so long characteristics and the SC-L plane
+    sweep compute the same recurrence (both senses, with inflow)."""
+    rng = np.random.default_rng(21)
+    # with dx = 1, dy = 1.3, dz = 0.8: Omega ~ (1, 1.3, -0.8) moves (1, 1) cells per
+    # plane downwards, Omega ~ (-1, 0, 0.8) moves (-1, 0) cells per plane upwards
+    dirs = np.array([[1.0, 1.3, -0.8], [-1.0, 0.0, 0.8]])
+    dirs /= np.linalg.norm(dirs, axis=1)[:, None]
+    box = _lc_box(rng, dirs)
+    S = rng.standard_normal(box.n)
+    lc = O.lambda_op(box, S, with_inflow=True)
+    sc = O.lambda_op(dataclasses.replace(box, formal_solver=W.FS_SCL), S, with_inflow=True)
+    assert np.abs(lc - sc).max() < 1e-13 * np.abs(sc).max()
+
+
+def test_3d_lc_homogeneous_box_is_the_1d_column():
+    """Fields that vary only with z: every long characteristic sees the 1D
+    column, whatever the horizontal offsets (level-symmetric S_4)."""
+    rng = np.random.default_rng(22)
+    nx, ny, nz, nn = 4, 3, 7, 2
+    dirs, wd = W.level_symmetric(4)
+    chi1 = rng.uniform(0.05, 4.0, (nz, nn))
+    S1 = rng.standard_normal((nz, len(dirs), nn))
+    box = W.Problem(dims=3, nx=nx, ny=ny, nz=nz, z=np.array([1.1, 0.9, 0.7]), dirs=dirs, w_dir=wd,
+                    w_nu=np.ones(nn), chi=np.repeat(chi1, nx * ny, axis=0), gamma=np.zeros((nx * ny * nz, nn)),
+                    I_top=rng.uniform(0, 1, nn), I_bot=rng.uniform(0, 1, nn), formal_solver=W.FS_LC)
+    col = W.Problem(dims=1, nx=1, ny=1, nz=nz, z=0.7 * np.arange(nz), dirs=dirs, w_dir=wd, w_nu=np.ones(nn),
+                    chi=chi1, gamma=np.zeros((nz, nn)), I_top=box.I_top, I_bot=box.I_bot)
+    S3 = np.broadcast_to(S1[:, None, None], (nz, ny, nx, len(dirs), nn)).reshape(-1)
+    I3 = O.lambda_op(box, S3, with_inflow=True).reshape(nz, ny, nx, len(dirs), nn)
+    I1 = O.lambda_op(col, S1.reshape(-1), with_inflow=True).reshape(nz, len(dirs), nn)
+    assert np.abs(I3 - I1[:, None, None]).max() < 1e-13 * np.abs(I1).max()
+
+
+def test_3d_lc_single_rays_by_hand():
+    """Fractional offsets: a few points recomputed one scalar at a time (the
+    ray's crossing of every plane, bilinear weights from the floor and the
+    fraction of the offset, periodic wrap), and the long characteristics
+    differ from the short ones there (the intensity is not interpolated)."""
+    rng = np.random.default_rng(23)
+    v = np.array([[0.37, -0.52, -0.6], [-0.21, 0.44, 0.7]])
+    dirs = v / np.linalg.norm(v, axis=1)[:, None]
+    box = _lc_box(rng, dirs, n=(5, 4, 6), nn=1)
+    nx, ny, nz = box.nx, box.ny, box.nz
+    S = rng.standard_normal(box.n)
+    I = O.lambda_op(box, S, with_inflow=True).reshape(nz, ny, nx, 2)
+    Sg = S.reshape(nz, ny, nx, 2)
+    chi = box.chi.reshape(nz, ny, nx)
+    dx, dy, dz = box.z
+
+    def interp(F, k, yy, xx, sx, sy):
+        px, py = xx - sx, yy - sy
+        x0, y0 = math.floor(px), math.floor(py)
+        ax, ay = px - x0, py - y0
+        g = lambda j, i: F[k, j % ny, i % nx]
+        return ((1 - ay) * ((1 - ax) * g(y0, x0) + ax * g(y0, x0 + 1))
+                + ay * ((1 - ax) * g(y0 + 1, x0) + ax * g(y0 + 1, x0 + 1)))
+
+    for d in range(2):
+        ox, oy, oz = dirs[d]
+        ds = dz / abs(oz)
+        sx, sy = ox * ds / dx, oy * ds / dy
+        first, step = (nz - 1, -1) if oz > 0 else (0, 1)
+        inflow = box.I_bot[0] if oz > 0 else box.I_top[0]
+        for (k, yy, xx) in ((first + 5 * step, 1, 2), (first + 3 * step, 3, 0), (first + 1 * step, 0, 4)):
+            s = abs(k - first)
+            val, Sa, ca = inflow, None, None
+            for m in range(s + 1):
+                km, t = first + m * step, s - m
+                Sm = interp(Sg[..., d], km, yy, xx, t * sx, t * sy)
+                cm = interp(chi, km, yy, xx, t * sx, t * sy)
+                if m > 0:
+                    tau = 0.5 * (ca + cm) * ds
+                    e = math.exp(-tau)
+                    beta = (tau + math.expm1(-tau)) / tau
+                    val = e * val + (1 - e - beta) * Sa + beta * Sm
+                Sa, ca = Sm, cm
+            assert abs(I[k, yy, xx, d] - val) < 1e-13 * max(1.0, abs(val))
+    sc = O.lambda_op(dataclasses.replace(box, formal_solver=W.FS_SCL), S, with_inflow=True)
+    assert np.abs(sc.reshape(I.shape) - I).max() > 1e-3
+
+
 def test_3d_half_offset_interpolates_two_cells():
     """Upwind offset of half a cell in y: the upwind value is the mean of the
     two neighbouring cells of the upwind plane."""
