@@ -73,12 +73,17 @@ enum {
 /* ---- enumerations ---------------------------------------------------- */
 enum { RT_FS_SCL = 0,    /* linear short-characteristics exponential step       */
        RT_FS_IE = 1,     /* implicit Euler, eqs. ie_1, ie_2                      */
-       RT_FS_QSC = 2 };  /* quadratic short characteristics (upwind, current and
+       RT_FS_QSC = 2,    /* quadratic short characteristics (upwind, current and
                             downwind points; the last step of a ray is linear) --
                             the quadratic exponential integrator of the paper's 3D
                             runs (Sec. 5.3), restated; in 3D boxes the downwind
                             point is the upwind stencil mirrored into the next
                             plane                                                */
+       RT_FS_LC = 3 };   /* 3D boxes only: long characteristics (Sec. 3.4 rays,
+                            TRIP's choice named in Sec. 5.3) -- each point's ray
+                            traced back to the inflow plane, S and chi interpolated
+                            at every plane crossing, linear steps; O(nz) steps per
+                            point                                                */
 enum { RT_P_FP64 = 0,    /* every stage in float64                              */
        RT_P_MIXED = 1 }; /* Sigma and sweep in float32 (bf16 tensor cores for the
                             dense kernel), Krylov and refinement in float64     */
@@ -113,7 +118,7 @@ typedef struct rt_desc {
   const double *t_src;   /* [n_pts*n_nu] thermal term t = eps_t/chi, or NULL (= 0)    */
   const double *I_top;   /* [n_nu] inflow for mu < 0 at the top, or NULL (= 0)        */
   const double *I_bot;   /* [n_nu] inflow for mu > 0 at the bottom, or NULL (= 0)     */
-  int32_t formal_solver; /* RT_FS_SCL, RT_FS_IE, or RT_FS_QSC                         */
+  int32_t formal_solver; /* RT_FS_SCL, RT_FS_IE, RT_FS_QSC, or RT_FS_LC (boxes)        */
 } rt_desc;
 
 /* ---- solve options and report ----------------------------------------- */

@@ -179,6 +179,8 @@ int check_desc(const rt_desc *d, int idx) {
   if (!d->z || !d->dir || !d->w_dir || !d->w_nu || !d->chi || !d->gamma)
     return fail(RT_ERR_ARG, std::string(pre) + "missing z, dir, w_dir, w_nu, chi or gamma");
   if (!d->Psi && (!d->P || !d->R)) return fail(RT_ERR_ARG, std::string(pre) + "need Psi or both P and R");
+  if (d->formal_solver == RT_FS_LC)
+    return fail(RT_ERR_ARG, std::string(pre) + "long characteristics (RT_FS_LC) are for 3D boxes");
   if (d->formal_solver != RT_FS_SCL && d->formal_solver != RT_FS_IE && d->formal_solver != RT_FS_QSC)
     return fail(RT_ERR_ARG, std::string(pre) + "unknown formal_solver");
   for (int i = 0; i + 1 < d->nz; ++i)
@@ -610,7 +612,8 @@ int create_box(const rt_desc *d, int n_rhs, int precision, int max_restart, rt_h
     return fail(RT_ERR_ARG, "box: missing z (spacings), dir, w_dir, w_nu, chi or gamma");
   if (!(d->z[0] > 0 && d->z[1] > 0 && d->z[2] > 0)) return fail(RT_ERR_ARG, "box: spacings must be positive");
   if (!d->Psi && (!d->P || !d->R)) return fail(RT_ERR_ARG, "box: need Psi or both P and R");
-  if (d->formal_solver != RT_FS_SCL && d->formal_solver != RT_FS_IE && d->formal_solver != RT_FS_QSC)
+  if (d->formal_solver != RT_FS_SCL && d->formal_solver != RT_FS_IE && d->formal_solver != RT_FS_QSC &&
+      d->formal_solver != RT_FS_LC)
     return fail(RT_ERR_ARG, "unknown formal_solver");
   const int64_t npts = (int64_t)d->nx * d->ny * d->nz;
   if (!rt::box_plane_fits(d->nx, d->ny)) return fail(RT_ERR_ARG, "box: nx*ny must be at most 4096 (a z-plane in shared memory)");
@@ -641,7 +644,7 @@ int create_box(const rt_desc *d, int n_rhs, int precision, int max_restart, rt_h
   h->E = npts * c.nr;
   h->nmax = h->E;
   h->box = rt::BoxDev{d->nx, d->ny, d->nz, d->n_dir, d->n_nu, d->formal_solver == RT_FS_IE ? 1 : 0,
-                      d->formal_solver == RT_FS_QSC ? 1 : 0};
+                      d->formal_solver == RT_FS_QSC ? 1 : 0, d->formal_solver == RT_FS_LC ? 1 : 0};
   // per direction: integer upwind shift reduced modulo the periodic plane,
   // its fractional part, the path length between planes, the sweep sense
   std::vector<double> geo(6 * (size_t)d->n_dir);

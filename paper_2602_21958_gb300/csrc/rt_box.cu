@@ -571,7 +571,7 @@ __global__ void k_box_from_sweep(const T *__restrict__ S, double *__restrict__ y
 // at the downwind point (the upwind stencil mirrored, in the next plane,
 // gathered from global memory: that plane is not in shared memory) and the
 // qsc_coef weights; the last plane of the sweep takes the linear step.
-enum { kSwChi = 0, kSwPre = 1, kSwKap = 2, kSwQsc = 3 };
+enum { kSwChi = 0, kSwPre = 1, kSwKap = 2, kSwQsc = 3, kSwLc = 4 };
 
 template <typename T, int FB, int CPT, int CB, typename TX, typename TY, int MODE>
 __global__ void __launch_bounds__(512) k_sweep3d(BoxDev bx, const double *__restrict__ geo,
@@ -817,6 +817,85 @@ __global__ void __launch_bounds__(512) k_sweep3d(BoxDev bx, const double *__rest
   }
 }
 
+// Long characteristics (RT_FS_LC, kSwLc): every point's value from its own
+// straight ray traced back to the inflow plane.  The ray through cell c of
+// plane k crosses plane k' at c shifted back by (k - k') (sx, sy) cells; S and
+// chi are interpolated there (bilinear, periodic) and the linear step of
+// eqs. ie_1/ie_2 is taken from crossing to crossing; the intensity is never
+// interpolated.  One thread per (direction, frequency, cell of a plane), all
+// target planes in sweep order, O(nz) steps per point; no shared memory, no
+// barriers.  SL: the source in the sweep layout with one frequency per block,
+// [d][f][p], or null for the thermal term tsrc.
+template <typename T, typename TX, typename TY>
+__global__ void __launch_bounds__(256) k_box_lc(BoxDev bx, const double *__restrict__ geo,
+                                                const T *__restrict__ chiN, const T *__restrict__ SL,
+                                                const double *__restrict__ tsrc, const TX *__restrict__ x,
+                                                TY *__restrict__ y, int out, int inflow,
+                                                const double *__restrict__ I_top,
+                                                const double *__restrict__ I_bot) {
+  const int nx = bx.nx, ny = bx.ny, nz = bx.nz, nn = bx.nn, nd = bx.nd;
+  const int plane = nx * ny;
+  const int64_t npts = (int64_t)plane * nz, nr = (int64_t)nd * nn;
+  const int64_t total = (int64_t)nd * nn * plane;
+  for (int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; gid < total;
+       gid += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(gid % plane);
+    const int64_t df = gid / plane;
+    const int f = (int)(df % nn), d = (int)(df / nn);
+    const double *g = geo + 6 * d;
+    const int fx = (int)g[0], fy = (int)g[1];
+    const T ax = (T)g[2], ay = (T)g[3], hds = (T)(0.5 * g[4]);
+    const bool up = g[5] > 0.5;
+    const int k0 = up ? nz - 1 : 0, step = up ? -1 : 1;
+    const int yy = c / nx, xx = c - yy * nx;
+    const T *Sd = SL ? SL + ((int64_t)d * nn + f) * npts : nullptr;
+    const T *chiB = chiN + (int64_t)(f >> 2) * npts * 4 + (f & 3);
+    // S and chi of plane km at cell c shifted back by t segments
+    auto at = [&](int km, int t, T &sv, T &cv) {
+      const T tx = (T)t * ax, ty = (T)t * ay;
+      const T flx = floor(tx), fly = floor(ty);
+      const T wx = tx - flx, wy = ty - fly;
+      const int shx = (int)(((int64_t)t * fx + (int64_t)flx) % nx);
+      const int shy = (int)(((int64_t)t * fy + (int64_t)fly) % ny);
+      int x0 = xx - shx, y0 = yy - shy;
+      if (x0 < 0) x0 += nx;
+      if (y0 < 0) y0 += ny;
+      const int x1 = x0 == 0 ? nx - 1 : x0 - 1;
+      const int y1 = y0 == 0 ? ny - 1 : y0 - 1;
+      const int64_t b = (int64_t)km * plane;
+      const int64_t p00 = b + y0 * nx + x0, p01 = b + y0 * nx + x1, p10 = b + y1 * nx + x0, p11 = b + y1 * nx + x1;
+      const T w00 = ((T)1 - wy) * ((T)1 - wx), w01 = ((T)1 - wy) * wx, w10 = wy * ((T)1 - wx), w11 = wy * wx;
+      if (Sd) {
+        sv = w00 * Sd[p00] + w01 * Sd[p01] + w10 * Sd[p10] + w11 * Sd[p11];
+      } else {
+        sv = w00 * cast_to<T>(tsrc[p00 * nn + f]) + w01 * cast_to<T>(tsrc[p01 * nn + f]) +
+             w10 * cast_to<T>(tsrc[p10 * nn + f]) + w11 * cast_to<T>(tsrc[p11 * nn + f]);
+      }
+      cv = w00 * chiB[p00 * 4] + w01 * chiB[p01 * 4] + w10 * chiB[p10 * 4] + w11 * chiB[p11 * 4];
+    };
+    auto put = [&](int k, T I) {
+      const int64_t q = ((int64_t)k * plane + c) * nr + (int64_t)d * nn + f;
+      y[q] = out == kOutI ? cast_to<TY>(I) : cast_to<TY>(cast_to<T>(x[q]) - I);
+    };
+    const T I0 = inflow ? (T)(up ? I_bot[f] : I_top[f]) : T(0);
+    put(k0, I0);
+    for (int s = 1; s < nz; ++s) {
+      T I = I0, Sa, ca;
+      at(k0, s, Sa, ca);
+      for (int m = 1; m <= s; ++m) {
+        T Sm, cm, e, a, b;
+        at(k0 + m * step, s - m, Sm, cm);
+        step_coef<T>(hds * (ca + cm), 0, e, a, b);
+        I = fma(e, I, fma(a, Sa, b * Sm));
+        Sa = Sm;
+        ca = cm;
+      }
+      put(k0 + s * step, I);
+    }
+  }
+}
+
+
 // Step weights of the float64 sweep, once per handle: for every (direction,
 // point, frequency) the optical depth of the step from the upwind plane,
 // 0.5 (chi_u + chi_c) ds with chi_u bilinear at the upwind point, and from it
@@ -868,6 +947,7 @@ __global__ void k_box_coef64(BoxDev bx, const double *__restrict__ geo, const do
 // ------------------------------------------------------------ host side
 // Step-weight mode of the sweep for one precision (see k_sweep3d).
 static int box_mode(const rt_handle *h, bool fp64) {
+  if (h->box.lc) return kSwLc;
   if (h->box.qsc) return kSwQsc;
   if (fp64) return h->box_w064 ? kSwPre : kSwChi;
   return h->box_kap32 ? kSwKap : kSwChi;
@@ -898,6 +978,10 @@ static int box_cpt_max(bool fp64, int fb, int mode) {
 static void box_shape(const rt_handle *h, bool fp64, int &fb, int &cpt) {
   const int plane = h->box.nx * h->box.ny;
   const int mode = box_mode(h, fp64);
+  if (mode == kSwLc) {  // one frequency per source block, no plane sweep
+    fb = cpt = 1;
+    return;
+  }
   const int fbmax = fp64 ? 2 : 4;
   fb = h->tune.box_fb > 0 ? std::min(fbmax, h->tune.box_fb) : fbmax;
   while (fb > 1 && (fb / 2 >= h->box.nn || box_smem(h, fp64, fb) > (size_t)kBoxSmemMax ||
@@ -988,6 +1072,13 @@ static int sweep3d(rt_handle *h, const void *S, const double *tsrc, const TX *x,
   int fb, cpt;
   box_shape(h, f64, fb, cpt);
   const int mode = box_mode(h, f64);
+  if (mode == kSwLc) {
+    const int64_t total = (int64_t)h->box.nd * h->box.nn * h->box.nx * h->box.ny;
+    const int grid = (int)std::min<int64_t>((total + 255) / 256, (int64_t)(h->n_sm > 0 ? h->n_sm : 152) * 32);
+    k_box_lc<T, TX, TY><<<grid, 256, 0, s>>>(h->box, h->d_geo, chiN, static_cast<const T *>(S), tsrc, x, y, out,
+                                             inflow ? 1 : 0, h->d_Itop, h->d_Ibot);
+    return (int)cudaGetLastError();
+  }
   if (mode == kSwQsc) return sweep3d_fb<T, kSwQsc>(h, fb, cpt, chiN, S, tsrc, x, y, out, inflow, s, xs);
   if constexpr (f64) {
     if (mode == kSwPre) return sweep3d_fb<T, kSwPre>(h, fb, cpt, chiN, S, tsrc, x, y, out, inflow, s, xs);
@@ -1170,7 +1261,7 @@ int box_prepare(rt_handle *h, const double *chi) {
           pr = p;
           fr = f;
         }
-    bool sep = cmax > 0.0 && !h->box.qsc;  // the quadratic sweep reads the full opacity
+    bool sep = cmax > 0.0 && !h->box.qsc && !h->box.lc;  // these two read the full opacity
     std::vector<double> phi(nn), kap(npts);
     for (int f = 0; f < nn && sep; ++f) phi[f] = chi[(size_t)pr * nn + f];
     for (int64_t p = 0; p < npts && sep; ++p) {
@@ -1194,7 +1285,7 @@ int box_prepare(rt_handle *h, const double *chi) {
   // and RT_BOX_COEF64 is not "0" (then the float64 sweep forms them on the fly)
   const int64_t ncoef = (int64_t)h->box.nd * npts * ((nn + 1) / 2) * 2;
   const char *env = std::getenv("RT_BOX_COEF64");
-  const bool allow = !(env && env[0] == '0' && env[1] == 0) && !h->box.qsc;
+  const bool allow = !(env && env[0] == '0' && env[1] == 0) && !h->box.qsc && !h->box.lc;
   size_t free_b = 0, total_b = 0;
   if (allow && cudaMemGetInfo(&free_b, &total_b) == cudaSuccess && (double)ncoef * 16.0 <= 0.25 * (double)free_b) {
     e = cudaMalloc(&h->box_w064, (size_t)ncoef * 8);

@@ -45,7 +45,7 @@ constexpr int kBoxSmemMax = 220 * 1024;  // shared-memory budget of one 3D sweep
 
 // 3D box geometry (device-side copy of the scalars)
 struct BoxDev {
-  int nx, ny, nz, nd, nn, ie, qsc;  // qsc: quadratic short characteristics
+  int nx, ny, nz, nd, nn, ie, qsc, lc;  // qsc: quadratic short characteristics, lc: long characteristics
 };
 
 }  // namespace rt

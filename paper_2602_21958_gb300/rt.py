@@ -13,13 +13,13 @@ from typing import Optional, Sequence
 
 import numpy as np
 
-from .workloads import FS_IE, FS_QSC, FS_SCL, Problem
+from .workloads import FS_IE, FS_LC, FS_QSC, FS_SCL, Problem
 
 _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "librt_gb300.so")
 
 RT_OK, RT_ERR_ARG, RT_ERR_CUDA, RT_ERR_OOM, RT_ERR_NOCONV, RT_ERR_BREAKDOWN, RT_ERR_NONFINITE, \
     RT_ERR_TIMEOUT = range(8)
-RT_FS_SCL, RT_FS_IE, RT_FS_QSC = 0, 1, 2
+RT_FS_SCL, RT_FS_IE, RT_FS_QSC, RT_FS_LC = 0, 1, 2, 3
 RT_P_FP64, RT_P_MIXED = 0, 1
 RT_OP_A, RT_OP_LAMBDA, RT_OP_SIGMA, RT_OP_RHS = 0, 1, 2, 3
 RT_KRYLOV_GMRES, RT_KRYLOV_BICGSTAB = 0, 1
@@ -158,7 +158,7 @@ def make_desc(p: Problem, keep: list) -> rt_desc:
     d.n_dir, d.n_nu = p.n_dir, p.n_nu
     for k, v in arrs.items():
         setattr(d, k, v.ctypes.data_as(_dp) if v is not None else _dp())
-    fs = {FS_SCL: RT_FS_SCL, FS_IE: RT_FS_IE, FS_QSC: RT_FS_QSC}.get(p.formal_solver)
+    fs = {FS_SCL: RT_FS_SCL, FS_IE: RT_FS_IE, FS_QSC: RT_FS_QSC, FS_LC: RT_FS_LC}.get(p.formal_solver)
     if fs is None:
         raise ValueError("unknown formal solver %r" % (p.formal_solver,))
     d.formal_solver = fs

@@ -67,7 +67,8 @@ def test_descriptor_marshalling():
     from paper_2602_21958_gb300 import workloads as W
 
     p = W.two_level_column(np.logspace(-2, 2, 7), 4, 2, 5, "r2", 1e-3, 1.0)
-    for fs, code in ((W.FS_SCL, rt.RT_FS_SCL), (W.FS_IE, rt.RT_FS_IE), (W.FS_QSC, rt.RT_FS_QSC)):
+    for fs, code in ((W.FS_SCL, rt.RT_FS_SCL), (W.FS_IE, rt.RT_FS_IE), (W.FS_QSC, rt.RT_FS_QSC),
+                     (W.FS_LC, rt.RT_FS_LC)):
         keep = []
         d = rt.make_desc(dataclasses.replace(p, formal_solver=fs), keep)
         assert (d.dims, d.nx, d.ny, d.nz, d.n_dir, d.n_nu) == (1, 1, 1, 7, 8, 5)

@@ -250,3 +250,54 @@ def test_box_qsc_solve(rt, prec):
     torch.cuda.synchronize()
     assert info["status"] == 0, info
     assert rel(x.cpu().numpy(), xref) < 1e-10
+
+
+def lc_box(separable=True, **kw):
+    p = small_box(**kw) if separable else nonseparable_box(**kw)
+    return dataclasses.replace(p, formal_solver=W.FS_LC)
+
+
+@pytest.mark.parametrize("separable", [True, False])
+@pytest.mark.parametrize("op", [0, 1, 2, 3])
+def test_box_lc_fp64(rt, separable, op):
+    """Long characteristics (each point's ray traced back to the inflow plane)
+    against the oracle, float64, every operator."""
+    p = lc_box(separable, nx=6, ny=7, nz=6, n_nu=5, kernel="r2", seed=13)
+    h = rt.Handle(p, precision=rt.RT_P_FP64, max_restart=4)
+    x = W.random_vectors(p.n, 1, 100 + op)[0]
+    y = torch.empty(p.n, dtype=torch.float64, device="cuda:0")
+    h.rt_apply(op, dev(x), y)
+    torch.cuda.synchronize()
+    ref = oracle_op(p, op, x)
+    assert rel(y.cpu().numpy(), ref) < 1e-12
+    assert np.abs(y.cpu().numpy() - ref).max() < 1e-12 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("op", [0, 1])
+def test_box_lc_mixed(rt, op):
+    p = lc_box(False, nx=9, ny=8, nz=7, order=6, n_nu=8, kernel="r2", seed=14)
+    h = rt.Handle(p, precision=rt.RT_P_MIXED, max_restart=8)
+    x = W.random_vectors(p.n, 1, 110 + op, "uniform")[0]
+    y = torch.empty(p.n, dtype=torch.float64, device="cuda:0")
+    h.rt_apply(op, dev(x), y)
+    torch.cuda.synchronize()
+    assert rel(y.cpu().numpy(), oracle_op(p, op, x)) < 2e-5
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_box_lc_solve(rt, prec):
+    p = lc_box(nx=6, ny=5, nz=6, order=4, n_nu=5, kernel="r2", eps=1e-3)
+    xref = O.solve_gmres(p, tol=1e-14, restart=300, max_iter=600).x
+    h = rt.Handle(p, precision=rt.RT_P_FP64 if prec == "fp64" else rt.RT_P_MIXED, max_restart=120)
+    x = torch.zeros(p.n, dtype=torch.float64, device="cuda:0")
+    info = h.rt_solve(None, x, tol=1e-13, tol_inner=1e-5, restart=120, max_outer=30)
+    torch.cuda.synchronize()
+    assert info["status"] == 0, info
+    assert rel(x.cpu().numpy(), xref) < 1e-10
+
+
+def test_long_characteristics_are_refused_for_columns(rt):
+    col = W.two_level_column(np.logspace(-2, 2, 7), 4, 2, 5, "r2", 1e-3, 1.0, formal_solver=W.FS_LC)
+    with pytest.raises(rt.RTError) as e:
+        rt.Handle(col)
+    assert e.value.code == rt.RT_ERR_ARG
