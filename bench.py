@@ -522,37 +522,49 @@ def config_entry(name, p) -> dict:
         del x, y, b
         torch.cuda.empty_cache()
     if name == "C3":
-        # the same box with quadratic short characteristics (RT_FS_QSC):
-        # apply times in both precisions, mixed solve to 1e-10
-        import dataclasses
-
-        pq = dataclasses.replace(p, formal_solver=W.FS_QSC)
-        entry["qsc"] = {"applies_ms": {}}
-        for label, prec in (("mixed", rt.RT_P_MIXED), ("fp64", rt.RT_P_FP64)):
-            h = rt.Handle(pq, n_rhs=1, precision=prec, max_restart=24)
-            h.rt_autotune()
-            x = torch.rand(p.n, dtype=torch.float64, device=dev)
-            y = torch.empty_like(x)
-            for _ in range(3):
-                h.rt_apply(rt.RT_OP_A, x, y)
-            torch.cuda.synchronize()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            for _ in range(20):
-                h.rt_apply(rt.RT_OP_A, x, y)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            entry["qsc"]["applies_ms"][label] = e0.elapsed_time(e1) / 20
-            if label == "mixed":
-                b = y
-                h.rt_apply(rt.RT_OP_RHS, None, b, fp64=True)
-                kw = dict(tol=1e-10, restart=24, max_outer=MAX_OUTER, tol_inner=TOL_INNER, inner_restart=0)
-                timed_solve(h, b, x, **kw)
-                entry["qsc"]["solve_ms_mixed"], entry["qsc"]["iterations_mixed"] = timed_solve(h, b, x, **kw)
-            h.close()
-            del x, y
-            torch.cuda.empty_cache()
+        # the same box with quadratic short characteristics (RT_FS_QSC) and
+        # with long characteristics (RT_FS_LC): apply times in both
+        # precisions, mixed solve to 1e-10
+        for key, fs in (("qsc", W.FS_QSC), ("lc", W.FS_LC)):
+            entry[key] = formal_solver_leg(p, fs, dev, stream, timed_solve)
     return entry
+
+
+def formal_solver_leg(p, fs, dev, stream, timed_solve) -> dict:
+    """Applies (both precisions) and the mixed solve of box p with formal solver fs."""
+    import dataclasses
+
+    import torch
+
+    from paper_2602_21958_gb300 import rt
+
+    pq = dataclasses.replace(p, formal_solver=fs)
+    out = {"applies_ms": {}}
+    for label, prec in (("mixed", rt.RT_P_MIXED), ("fp64", rt.RT_P_FP64)):
+        h = rt.Handle(pq, n_rhs=1, precision=prec, max_restart=24)
+        h.rt_autotune()
+        x = torch.rand(p.n, dtype=torch.float64, device=dev)
+        y = torch.empty_like(x)
+        for _ in range(3):
+            h.rt_apply(rt.RT_OP_A, x, y)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(20):
+            h.rt_apply(rt.RT_OP_A, x, y)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out["applies_ms"][label] = e0.elapsed_time(e1) / 20
+        if label == "mixed":
+            b = y
+            h.rt_apply(rt.RT_OP_RHS, None, b, fp64=True)
+            kw = dict(tol=1e-10, restart=24, max_outer=MAX_OUTER, tol_inner=TOL_INNER, inner_restart=0)
+            timed_solve(h, b, x, **kw)
+            out["solve_ms_mixed"], out["iterations_mixed"] = timed_solve(h, b, x, **kw)
+        h.close()
+        del x, y
+        torch.cuda.empty_cache()
+    return out
 
 
 def spectral_sweep(rank: int = 0) -> dict:
