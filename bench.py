@@ -527,7 +527,40 @@ def config_entry(name, p) -> dict:
         # precisions, mixed solve to 1e-10
         for key, fs in (("qsc", W.FS_QSC), ("lc", W.FS_LC)):
             entry[key] = formal_solver_leg(p, fs, dev, stream, timed_solve)
+    if name == "C2":
+        entry["dense_psi"] = dense_psi_leg(p, dev, timed_solve)
     return entry
+
+
+def dense_psi_leg(p, dev, timed_solve) -> dict:
+    """C2's kernel written out as a dense Psi (n_r = 1024): the mixed solve
+    (grid-wide nested FGMRES whose float32 inner operator runs Sigma on the
+    tensor cores; their launches and summed device time from rt_tc_timer) and
+    the float64 GMRES (dense Sigma on CUDA cores), both to 1e-10."""
+    import torch
+
+    from paper_2602_21958_gb300 import rt
+
+    pd = p.with_dense_kernel()
+    out = {}
+    for label, prec in (("mixed", rt.RT_P_MIXED), ("fp64", rt.RT_P_FP64)):
+        h = rt.Handle(pd, n_rhs=1, precision=prec, max_restart=RESTART_MIXED if label == "mixed" else RESTART)
+        b = torch.empty(pd.n, dtype=torch.float64, device=dev)
+        x = torch.zeros_like(b)
+        h.rt_apply(rt.RT_OP_RHS, None, b, fp64=True)
+        kw = dict(tol=1e-10, restart=RESTART_MIXED if label == "mixed" else RESTART, max_outer=MAX_OUTER,
+                  tol_inner=TOL_INNER)
+        timed_solve(h, b, x, **kw)
+        if label == "mixed":
+            h.rt_tc_timer(True)
+        out[f"solve_ms_{label}"], out[f"iterations_{label}"] = timed_solve(h, b, x, **kw)
+        if label == "mixed":
+            tc_ms, n = h.rt_tc_timer(False)
+            out["tensor_core_sigma"] = {"launches": n, "device_ms": tc_ms}
+        h.close()
+        del b, x
+        torch.cuda.empty_cache()
+    return out
 
 
 def formal_solver_leg(p, fs, dev, stream, timed_solve) -> dict:

@@ -126,3 +126,23 @@ def test_tc_timer_counts_and_times_only_the_gemm(rt):
     with pytest.raises(rt.RTError) as e:
         h.rt_tc_timer(False)
     assert e.value.code == rt.RT_ERR_ARG
+
+
+def test_dense_single_column_mixed_solve_runs_sigma_on_the_tensor_cores(rt):
+    """One dense column of 192,000 dofs in mixed precision is solved by the
+    grid-wide nested solver, whose float32 inner operator takes the tcgen05
+    Sigma: the kernel timer counts at least one tensor-core launch per inner
+    iteration, and the float64 refinement still reaches the oracle's solution
+    (the float64 outer operator closes every cycle)."""
+    p = CASES["nr1280"]().with_dense_kernel()
+    h = rt.Handle(p, precision=rt.RT_P_MIXED, max_restart=32)
+    b = torch.tensor(O.rhs(p), device="cuda:0")
+    x = torch.zeros_like(b)
+    h.rt_tc_timer(True)
+    info = h.rt_solve(b, x, tol=1e-12, tol_inner=1e-2, max_outer=40)
+    torch.cuda.synchronize()
+    ms, launches = h.rt_tc_timer(False)
+    assert info["status"] == 0, info
+    assert launches >= info["total_inner"] > 0 and ms > 0.0
+    xref = O.solve_gmres(p, tol=1e-14, restart=400, max_iter=800).x
+    assert np.linalg.norm(x.cpu().numpy() - xref) / np.linalg.norm(xref) < 1e-10
