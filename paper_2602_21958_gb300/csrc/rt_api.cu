@@ -586,8 +586,8 @@ int create_columns(const rt_desc *descs, int n_cols, int n_rhs, int precision, i
   if (rt::single_instance(h)) {  // one (column, rhs): solved by the grid-wide kernels
     const int G = rt::grid_ctas(h);
     ce = cudaMalloc(&h->g_r, (size_t)h->ws.ld * sizeof(double));
-    if (ce == cudaSuccess) ce = cudaMalloc(&h->g_part, (size_t)G * 16 * sizeof(double));
-    if (ce == cudaSuccess) ce = cudaMalloc(&h->g_red, 64 * sizeof(double));
+    if (ce == cudaSuccess) ce = cudaMalloc(&h->g_part, (size_t)G * rt::kGridPartPerCta * sizeof(double));
+    if (ce == cudaSuccess) ce = cudaMalloc(&h->g_red, rt::kGridPartPerCta * sizeof(double));
     if (ce == cudaSuccess) ce = cudaMalloc(&h->g_coef, 1024 * sizeof(double));
     if (ce != cudaSuccess) {
       free_handle(h);
@@ -716,8 +716,8 @@ int create_box(const rt_desc *d, int n_rhs, int precision, int max_restart, rt_h
   const size_t s_bytes = (size_t)npts * d->n_dir * h->box_npad * sizeof(double);
   if (ce == cudaSuccess) ce = cudaMalloc(&h->apply_S, std::max(s_bytes, (size_t)h->E * sizeof(double)));
   if (ce == cudaSuccess) ce = cudaMalloc(&h->g_r, (size_t)h->E * sizeof(double));
-  if (ce == cudaSuccess) ce = cudaMalloc(&h->g_part, (size_t)G * 16 * sizeof(double));
-  if (ce == cudaSuccess) ce = cudaMalloc(&h->g_red, 64 * sizeof(double));
+  if (ce == cudaSuccess) ce = cudaMalloc(&h->g_part, (size_t)G * rt::kGridPartPerCta * sizeof(double));
+  if (ce == cudaSuccess) ce = cudaMalloc(&h->g_red, rt::kGridPartPerCta * sizeof(double));
   if (ce == cudaSuccess) ce = cudaMalloc(&h->g_coef, 1024 * sizeof(double));
   if (ce == cudaSuccess) ce = cudaMalloc(&h->d_err, sizeof(int));
   if (ce == cudaSuccess) ce = cudaMemset(h->d_err, 0, sizeof(int));
@@ -1286,7 +1286,7 @@ int rt_arnoldi(rt_handle *h, const double *v0, int32_t m, double *H, int32_t *m_
   if (fault_now() == kFaultLaunch) return fail(RT_ERR_CUDA, "RT_FAULT=launch: injected launch failure");
   if (h->dims != 3 && !rt::single_instance(h))
     return fail(RT_ERR_ARG, "rt_arnoldi needs a handle with one instance (a box or one column, n_rhs = 1)");
-  if (m < 1) return fail(RT_ERR_ARG, "need m >= 1");
+  if (m < 1 || m > rt::kMaxKrylov) return fail(RT_ERR_ARG, "need 1 <= m <= 512");
   const int64_t ldv = (h->E + 31) / 32 * 32;
   if ((int64_t)(m + 1) * ldv * 8 > h->ws.cap_bytes)
     return fail(RT_ERR_ARG, "workspace holds fewer than m+1 float64 vectors: create the handle with a larger max_restart");

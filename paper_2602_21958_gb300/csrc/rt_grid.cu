@@ -16,6 +16,8 @@ namespace rt {
 
 constexpr int kGT = 256;     // threads per CTA
 constexpr int kGDots = 8;    // basis vectors per pass of the projection kernel
+constexpr int kGMaxGroups = (kMaxKrylov + 2 + kGDots - 1) / kGDots;  // groups of one projection
+static_assert((kGDots + 1) * kGMaxGroups <= kGridPartPerCta, "grid partial buffer too small");
 
 int grid_ctas(const rt_handle *h) { return 2 * (h->n_sm > 0 ? h->n_sm : 152); }
 
@@ -82,6 +84,17 @@ __global__ void __launch_bounds__(kGT) k_gdots(const TL *V, int64_t ldv, int i0,
   for (int u = 0; u <= kGDots; ++u) acc[u] += (double)part[u];
   block_sum<kGDots + 1>(acc, red, outb);
   if (threadIdx.x <= kGDots) partial[(int64_t)blockIdx.x * (kGDots + 1) + threadIdx.x] = acc[threadIdx.x];
+}
+
+// out[g][u] = sum over CTAs of partial[g][cta][u], u <= kGDots: the sums of
+// several k_gdots launches (one block per group of basis rows)
+__global__ void k_greduce_groups(const double *partial, int nblk, double *out) {
+  const int g = blockIdx.x, u = threadIdx.x;
+  if (u > kGDots) return;
+  const double *p = partial + (int64_t)g * nblk * (kGDots + 1) + u;
+  double s = 0.0;
+  for (int b = 0; b < nblk; ++b) s += p[(int64_t)b * (kGDots + 1)];
+  out[g * (kGDots + 1) + u] = s;
 }
 
 __global__ void k_greduce(const double *partial, int nblk, int nv, double *out) {
@@ -223,19 +236,26 @@ static int reduce_to_host(GridCtx &g, int nv, double *dst) {
   return (int)e;
 }
 
+// h = V[0..j]^T w and ww = w.w: the groups of kGDots rows run back to back
+// into their own partial sums, one reduction and one copy to the host
 template <typename TL>
 static int dots(GridCtx &g, const TL *V, int64_t ldv, int j, const TL *w, int64_t n, std::vector<double> &h,
                 double *ww) {
   h.assign(j + 1, 0.0);
-  for (int i0 = 0; i0 <= j; i0 += kGDots) {
-    const int cnt = std::min(kGDots, j + 1 - i0);
-    k_gdots<TL><<<g.G, kGT, 0, g.s>>>(V, ldv, i0, cnt, w, n, i0 == 0 ? 1 : 0, g.part);
-    double out[kGDots + 1];
-    int e = reduce_to_host(g, kGDots + 1, out);
-    if (e) return e;
-    for (int u = 0; u < cnt; ++u) h[i0 + u] = out[u];
-    if (i0 == 0 && ww) *ww = out[kGDots];
+  const int ng = (j + kGDots) / kGDots;
+  if (ng > kGMaxGroups) return (int)cudaErrorInvalidValue;
+  for (int gi = 0; gi < ng; ++gi) {
+    const int i0 = gi * kGDots, cnt = std::min(kGDots, j + 1 - i0);
+    k_gdots<TL><<<g.G, kGT, 0, g.s>>>(V, ldv, i0, cnt, w, n, gi == 0 ? 1 : 0,
+                                      g.part + (int64_t)gi * g.G * (kGDots + 1));
   }
+  k_greduce_groups<<<ng, 32, 0, g.s>>>(g.part, g.G, g.red);
+  g.host.resize((size_t)ng * (kGDots + 1));
+  cudaError_t e = cudaMemcpyAsync(g.host.data(), g.red, g.host.size() * sizeof(double), cudaMemcpyDeviceToHost, g.s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(g.s);
+  if (e != cudaSuccess) return (int)e;
+  for (int i = 0; i <= j; ++i) h[i] = g.host[(size_t)(i / kGDots) * (kGDots + 1) + i % kGDots];
+  if (ww) *ww = g.host[kGDots];
   return 0;
 }
 

@@ -188,5 +188,8 @@ constexpr long long kNoAllocScratchBytes = 16ll << 20;
 int launch_apply_noalloc(rt_handle *h, int op, bool fp64, const double *x, double *y, cudaStream_t s);
 constexpr int kRayBlock = 128;  // default rays (threads) per sweep tile
 int max_krylov();
+constexpr int kMaxKrylov = 512;          // largest Krylov basis (max_restart, rt_arnoldi's m)
+constexpr int kGridPartPerCta = 9 * 65;  // float64 partial sums per grid-solve CTA: one projection
+                                         // over kMaxKrylov + 2 rows in groups of 8 (+ the norm)
 int apply_slots(rt_handle *h);
 }  // namespace rt
