@@ -338,8 +338,8 @@ def lambda_3d_lc(prob: Problem, S: np.ndarray, with_inflow: bool = False) -> np.
     I = np.zeros_like(S)
     for d in range(nd):
         ox, oy, oz = prob.dirs[d]
-        ds = dz / abs(oz)
-        sx, sy = ox * ds / dx, oy * ds / dy
+        seg = dz / abs(oz)                          # path length between planes
+        sx, sy = ox * seg / dx, oy * seg / dy       # cells per plane
         first, step = (nz - 1, -1) if oz > 0 else (0, 1)
         inflow = prob.I_bot if oz > 0 else prob.I_top
         I0 = np.zeros((nn, ny, nx))
@@ -355,7 +355,7 @@ def lambda_3d_lc(prob: Problem, S: np.ndarray, with_inflow: bool = False) -> np.
                 Sm = _bilinear_periodic(np.moveaxis(S[km, :, :, d, :], -1, 0), t * sx, t * sy)
                 cm = _bilinear_periodic(np.moveaxis(chi[km], -1, 0), t * sx, t * sy)
                 if m > 0:
-                    e, al, be = step_coefficients(0.5 * (ca + cm) * ds, FS_SCL)
+                    e, al, be = step_coefficients(0.5 * (ca + cm) * seg, FS_SCL)
                     Iray = e * Iray + al * Sa + be * Sm
                 Sa, ca = Sm, cm
             I[first + s * step, :, :, d, :] = np.moveaxis(Iray, 0, -1)
