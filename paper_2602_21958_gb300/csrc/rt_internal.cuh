@@ -274,14 +274,36 @@ __device__ void sigma_block_kr(const ColDev &c, const Tables<T> &tb, const TX *_
     }
   }
   __syncthreads();
-  // 3. expansion over directions, scaled by Gamma
-  for (int i = threadIdx.x; i < np * nr; i += blockDim.x) {
-    const int b = i / nr, r = i - b * nr, d = r / nn, f = r - d * nn;
-    const T *zb = zbuf + b * per_pt + f;
-    const T *u = Ul + d * rp;
-    T acc = 0;
-    for (int k = 0; k < rp; ++k) acc = fma(u[k], zb[k * nn], acc);
-    S[(int64_t)(p0 + b) * nr + r] = gam[(int64_t)(p0 + b) * nn + f] * acc;
+  // 3. expansion over directions, scaled by Gamma: one thread per (point, nu)
+  //    with its ranks' z and Gamma in registers, looping over the directions
+  //    (stores of a warp stay contiguous in nu); same sums, same order
+  if (rp <= KR) {
+    for (int i = threadIdx.x; i < np * nn; i += blockDim.x) {
+      const int b = i / nn, f = i - b * nn;
+      const T *zb = zbuf + b * per_pt + f;
+      T z[KR];
+#pragma unroll
+      for (int k = 0; k < KR; ++k) z[k] = k < rp ? zb[k * nn] : T(0);
+      const T g = gam[(int64_t)(p0 + b) * nn + f];
+      T *out = S + (int64_t)(p0 + b) * nr + f;
+      for (int d = 0; d < nd; ++d) {
+        const T *u = Ul + d * rp;
+        T acc = 0;
+#pragma unroll
+        for (int k = 0; k < KR; ++k)
+          if (k < rp) acc = fma(u[k], z[k], acc);
+        out[(int64_t)d * nn] = g * acc;
+      }
+    }
+  } else {
+    for (int i = threadIdx.x; i < np * nr; i += blockDim.x) {
+      const int b = i / nr, r = i - b * nr, d = r / nn, f = r - d * nn;
+      const T *zb = zbuf + b * per_pt + f;
+      const T *u = Ul + d * rp;
+      T acc = 0;
+      for (int k = 0; k < rp; ++k) acc = fma(u[k], zb[k * nn], acc);
+      S[(int64_t)(p0 + b) * nr + r] = gam[(int64_t)(p0 + b) * nn + f] * acc;
+    }
   }
   __syncthreads();
 }
